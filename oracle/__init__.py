@@ -1,0 +1,24 @@
+"""CPU oracle for the domain wall fermion hot path -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, FP64 numpy restatement of what the CUDA library computes.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the library never does, and this package never
+imports the library.  The two share nothing but the seeded input generators
+(``paper_2203_17119_gb300.inputs``), which hold no operator arithmetic.
+
+Modules:
+
+* ``oracle.dwf``      -- gamma matrices, Wilson hop, Shamir/Moebius 5D
+  operator and its adjoint, even-odd blocks, closed-form M_ee^-1, Schur
+  operator M_pc, CGNE solve, Dirichlet block operator D_Omega (mask form and
+  cut-link form), per-site evaluation for sampled checks.
+* ``oracle.dense``    -- dense matrices of the above on tiny lattices, for
+  brute-force inverses, determinants and the block identities of Sec. 2.1.
+* ``oracle.krylov``   -- textbook CG, mixed-precision-free reference of the
+  flexible GCR iteration.
+* ``oracle.nn``       -- the parallel-transport convolutional preconditioner
+  (forward, analytic backward, Adam).
+
+Parity pins (what fixes each function independently of its own code) are in
+``tests/test_oracle_*.py``.
+"""
