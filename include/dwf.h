@@ -1,0 +1,213 @@
+/*
+ * dwf.h -- C ABI of the GB300 (sm_103a) domain wall fermion library.
+ *
+ * The library applies the 5D domain wall operator D (Shamir and Moebius),
+ * its even-odd (red-black) blocks and Schur operator, and the Dirichlet
+ * block operator D_Omega, and solves D x = b with them on one GPU.  The paper
+ * (Boyle, Bollweg, Kelly, Yamaguchi, "Algorithms for Domain Wall Fermions",
+ * LATTICE2021) states the problem: Sec. 1 and Sec. 2.3 put the Krylov solves
+ * with D and with the local Dirichlet operator at the centre of HMC; Sec. 2.1
+ * defines D_Omega as the block of D that connects Omega with itself, and
+ * Sec. 2.4 realises it by zeroing the gauge links that cross the domain
+ * boundary.  The paper never writes D itself; the conventions used are:
+ *
+ *   Dh psi(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)
+ *   D_W       = (4 - M5) - Dh / 2
+ *   S5 psi_s  = P_- psi_{s+1} + P_+ psi_{s-1},  psi_{Ls} = -mf psi_0, psi_{-1} = -mf psi_{Ls-1}
+ *   D         = D_W (b5 + c5 S5) + (1 - S5)          (Shamir: b5 = 1, c5 = 0)
+ *   M_ee = M_oo = d + e S5,  d = b5 (4 - M5) + 1,  e = c5 (4 - M5) - 1
+ *   M_eo, M_oe  = -Dh (b5 + c5 S5) / 2 between the 4D checkerboards
+ *   M_pc        = M_oo - M_oe M_ee^-1 M_eo           (odd checkerboard)
+ *
+ * with the chiral gamma basis: g_k = [[0, -i s_k], [i s_k, 0]] (k = 1..3,
+ * directions x, y, z), g_4 = [[0, 1], [1, 0]] (t), g_5 = diag(1, 1, -1, -1),
+ * P_+ = spins {0, 1}, P_- = spins {2, 3}.  4D parity is (x + y + z + t) mod 2.
+ *
+ * ------------------------------------------------------------------------
+ * DOMAINS.  A handle is bound to a domain: either the whole periodic
+ * lattice (nbox = 0) or a list of boxes, each box an independent Dirichlet
+ * block (every link leaving the box is cut, Sec. 2.4).  Boxes may overlap in
+ * the lattice: each has its own field storage, so the handle's operator is
+ * the direct sum of the boxes' D_Omega.  A box is (origin[4], extent[4]) in
+ * (x, y, z, t) order, 1 <= extent[mu] <= L[mu], coordinates taken modulo L
+ * (boxes may wrap).  In a direction where extent == L the box is periodic.
+ *
+ * SITE ORDER.  Sites of box b are enumerated in box-local lexicographic
+ * order l = l0 + e0 (l1 + e1 (l2 + e2 l3)), global coordinate
+ * x_mu = (origin_mu + l_mu) mod L_mu.  The parity-p site list of a domain is
+ * the concatenation over boxes b = 0..nbox-1 of the sites of box b whose
+ * global parity is p, in that order.  For the whole lattice (Lx even) the
+ * parity-p index of site lex is lex / 2.
+ *
+ * FIELD LAYOUTS (all device memory, owned by the caller):
+ *   checkerboard field of parity p ("cb field"):
+ *       [i < nsites(p)][c < 12][r < nrhs][s < Ls][re, im]
+ *     c = spin * 3 + colour; element type double (DWF_FP64), float
+ *     (DWF_FP32) or bfloat16 (DWF_BF16).  nrhs right-hand sides and the
+ *     fifth dimension are the innermost axes ("lanes" l = r * Ls + s).
+ *   full field: [cb field of parity 0][cb field of parity 1].
+ *   canonical field (dwf_pack / dwf_unpack only, complex128):
+ *       [box][r][box-local site l][s][spin][colour][re, im]
+ *   canonical gauge field (dwf_set_gauge, complex128, whole lattice):
+ *       [site lex][mu][a][b][re, im],  lex = x + Lx (y + Ly (z + Lz t)),
+ *       U_mu(x) transports from x + mu to x.
+ *
+ * STREAMS.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ * default stream.  Operator calls are asynchronous on that stream and
+ * allocate nothing.  Solves synchronise the stream and fill their stats.
+ *
+ * ERRORS.  Every call returns a dwf_status; dwf_last_error() returns a
+ * thread-local message for the last failure on the calling thread.  A
+ * failed argument check leaves the handle unchanged.  Device kernels never
+ * trap: a bounded wait that runs out sets a device error word, reported as
+ * DWF_ERR_DEVICE by dwf_check_device() and by the solves.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DWF_OK = 0,
+    DWF_ERR_ARG = 1,            /* invalid argument (nothing was launched)  */
+    DWF_ERR_CUDA = 2,           /* a CUDA runtime call failed               */
+    DWF_ERR_NOT_CONVERGED = 3,  /* solve hit maxiter; x = last iterate      */
+    DWF_ERR_TIMEOUT = 4,        /* solve hit max_seconds; x = last iterate  */
+    DWF_ERR_NAN = 5,            /* NaN/Inf met in a solve                   */
+    DWF_ERR_UNSUPPORTED = 6,    /* valid but not implemented combination    */
+    DWF_ERR_DEVICE = 7          /* a device-side bounded wait ran out       */
+} dwf_status;
+
+typedef enum { DWF_FP64 = 0, DWF_FP32 = 1, DWF_BF16 = 2 } dwf_prec;
+
+/* Lattice and action.  dims = (Lx, Ly, Lz, Lt), Lx even; Shamir: b5 = 1,
+ * c5 = 0; Moebius: b5, c5 free (Sec. 2.3 uses both kinds of action). */
+typedef struct {
+    int dims[4];
+    int Ls;
+    double M5, mf, b5, c5;
+} dwf_params;
+
+typedef struct {
+    int origin[4];
+    int extent[4];
+} dwf_box;
+
+typedef struct dwf_handle dwf_handle;
+
+/* ------------------------------------------------------------- set-up */
+
+/* Create a handle for the whole lattice (boxes = NULL, nbox = 0) or for the
+ * Dirichlet blocks D_Omega of `nbox` boxes (Sec. 2.1, Sec. 2.4).  Builds the
+ * site lists, neighbour tables and tile tables on the host and allocates all
+ * device workspace for up to `nrhs_max` right-hand sides, on the current
+ * CUDA device.  Errors: DWF_ERR_ARG (Lx odd, Ls < 1, extents out of range,
+ * nrhs_max < 1 or Ls * nrhs_max > 256), DWF_ERR_CUDA (allocation). */
+dwf_status dwf_create(dwf_handle** h, const dwf_params* p, const dwf_box* boxes,
+                      int nbox, int nrhs_max);
+dwf_status dwf_destroy(dwf_handle* h);
+
+/* Number of sites of the handle's domain with parity `parity`. */
+dwf_status dwf_domain_sites(const dwf_handle* h, int parity, int64_t* nsites);
+/* Offset and count of box `box`'s parity-`parity` sites in the cb field. */
+dwf_status dwf_box_sites(const dwf_handle* h, int box, int parity,
+                         int64_t* offset, int64_t* count);
+
+/* Load the gauge field (device pointer, canonical complex128 layout of the
+ * whole lattice, read during the call only).  Builds the FP64/FP32/BF16
+ * per-parity link tables (forward U_mu(x) and backward U_mu(x-mu)^+ per
+ * site, zero for links cut by the domain); ends with a stream sync. */
+dwf_status dwf_set_gauge(dwf_handle* h, const double* U, void* stream);
+
+/* canonical complex128 <-> full field of precision `prec` (layout kernels). */
+dwf_status dwf_pack(dwf_handle* h, void* dst, const double* src, int nrhs,
+                    dwf_prec prec, void* stream);
+dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs,
+                      dwf_prec prec, void* stream);
+
+/* ---------------------------------------------------------- operators
+ * `in` and `out` are device cb (or full) fields of precision `prec` with
+ * `nrhs` <= nrhs_max right-hand sides; they must not alias.  For DWF_BF16
+ * the arithmetic is FP32 on BF16 operands (links and spinors).          */
+
+/* out = M_{p,1-p} in  (off-diagonal block of D, the hop with the
+ * (b5 + c5 S5) factor folded in), p = out_parity; dagger: out =
+ * (M_{1-p,p})^+ in.  `in` has parity 1 - p. */
+dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parity,
+                         int dagger, dwf_prec prec, int nrhs, void* stream);
+
+/* out = M_ee in (= M_oo in; either parity, `parity` selects the site count);
+ * dagger: M_ee^+ in. */
+dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity,
+                     int dagger, dwf_prec prec, int nrhs, void* stream);
+
+/* out = M_ee^-1 in (closed form per chirality); dagger: (M_ee^+)^-1 in. */
+dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity,
+                         int dagger, dwf_prec prec, int nrhs, void* stream);
+
+/* out = M_pc in on the odd checkerboard; dagger: M_pc^+ in. */
+dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger,
+                   dwf_prec prec, int nrhs, void* stream);
+
+/* out = D in (full fields, both parities) for a whole-lattice handle, or
+ * D_Omega in for a box handle; dagger: the adjoint. */
+dwf_status dwf_apply_d(dwf_handle* h, void* out, const void* in, int dagger,
+                       dwf_prec prec, int nrhs, void* stream);
+
+/* The Dirichlet block operator D_Omega (Sec. 2.1: the part of D connecting
+ * Omega with itself; Sec. 2.4: D with the links crossing the domain
+ * boundary set to zero) on a box handle.  Same as dwf_apply_d but fails with
+ * DWF_ERR_ARG on a whole-lattice handle. */
+dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dagger,
+                               dwf_prec prec, int nrhs, void* stream);
+
+/* ------------------------------------------------------------- solves */
+
+typedef struct {
+    double tol;          /* target |b - D x| / |b| per system (e.g. 1e-10)      */
+    int maxiter;         /* cap on inner iterations                              */
+    double delta;        /* reliable-update trigger (mixed precision), e.g. 0.1  */
+    int restart;         /* GCR restart length                                   */
+    int use_x0;          /* 1: x holds the initial guess                         */
+    dwf_prec inner_prec; /* DWF_FP64: plain FP64 CG; FP32/BF16: mixed precision  */
+    double max_seconds;  /* wall-clock cap (0 = none)                            */
+    int check_every;     /* iterations per captured CUDA graph (0 = default 8)   */
+} dwf_solver_params;
+
+typedef struct {
+    int iters;             /* inner iterations                               */
+    int reliable_updates;  /* FP64 residual recomputations                   */
+    int op_applies;        /* M_pc or M_pc^+ applications (any precision)    */
+    int status;            /* dwf_status of this system                      */
+    double true_resid;     /* |b - D x| / |b| recomputed in FP64 at the end  */
+    double seconds;        /* wall time of the whole solve                   */
+} dwf_solver_stats;
+
+/* Solve D x = b (D_Omega x = b on a box handle) for every box and every
+ * right-hand side at once by even-odd preconditioned CGNE on
+ * M_pc^+ M_pc x_o = M_pc^+ b'_o, b'_o = b_o - M_oe M_ee^-1 b_e, then
+ * x_e = M_ee^-1 (b_e - M_eo x_o).  x, b: device full fields, FP64, nrhs
+ * right-hand sides.  inner_prec FP64 runs plain FP64 CG; FP32/BF16 runs the
+ * inner iteration with that operator and FP32 vectors, with FP64 reliable
+ * updates of the residual, FP64 solution accumulation and FP64 global
+ * reductions.  stats: array of nbox_or_1 * nrhs entries (box-major).
+ * Returns DWF_OK when every system reached tol. */
+dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
+                          const dwf_solver_params* sp, dwf_solver_stats* stats,
+                          void* stream);
+
+/* Device error word (bounded waits that ran out); DWF_ERR_DEVICE if set. */
+dwf_status dwf_check_device(dwf_handle* h);
+
+/* Thread-local description of the last failure. */
+const char* dwf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWF_H */

@@ -386,3 +386,24 @@ def eo_block_site(U, psi, p: DWFParams, site, dagger: bool = False):
         out += np.einsum("ij,ab,sjb->sia", one - g[mu], Uf, pf)
         out += np.einsum("ij,ba,sjb->sia", one + g[mu], np.conj(Ub), pb)
     return -0.5 * out
+
+
+# ----------------------------------------- operators of one Dirichlet block
+def eo_block_in(U, psi, p: DWFParams, mask, out_parity: int, dagger: bool = False):
+    """Off-diagonal block of P D P (mask form of D_Omega, Sec. 2.1) from
+    parity 1 - out_parity to out_parity: P M_{out,1-out} P psi (or adjoint)."""
+    src = restrict(parity_part(psi, 1 - out_parity), mask)
+    return restrict(parity_part(hop_part(U, src, p, dagger), out_parity), mask)
+
+
+def mpc_in(U, psi_o, p: DWFParams, mask, dagger: bool = False):
+    """Schur operator of the Dirichlet block P D P on the sites of ``mask``
+    (M_oo - M_oe M_ee^-1 M_eo with every hop restricted to the block)."""
+    H = lambda f: restrict(hop_part(U, restrict(f, mask), p, dagger), mask)
+    t = mooee_inv(H(psi_o), p, dagger)
+    return restrict(mooee(psi_o, p, dagger), mask) - H(t)
+
+
+def box_mask(dims, box) -> np.ndarray:
+    """Boolean 4D mask of one box (origin, extent), periodic wrap allowed."""
+    return box_id_field(dims, [box]) == 0

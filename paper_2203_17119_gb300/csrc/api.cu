@@ -1,0 +1,184 @@
+// extern "C" entry points of include/dwf.h: argument checks, then the
+// operator compositions of ops.cu, the layout kernels of domain.cu and the
+// solver of solver.cu.
+#include <cstdio>
+
+#include "dev_common.cuh"
+#include "dwf_internal.cuh"
+
+namespace dwf {
+const char* last_error();
+}
+
+using namespace dwf;
+
+static bool bad_prec(dwf_prec p) { return p != DWF_FP64 && p != DWF_FP32 && p != DWF_BF16; }
+
+static dwf_status check_op(dwf_handle* h, const void* out, const void* in, dwf_prec prec, int nrhs,
+                           const char* who) {
+    DWF_TRY(check_handle(h));
+    if (out == nullptr || in == nullptr) {
+        set_error("%s: null field pointer", who);
+        return DWF_ERR_ARG;
+    }
+    if (out == in) {
+        set_error("%s: out and in must not alias", who);
+        return DWF_ERR_ARG;
+    }
+    if (bad_prec(prec)) {
+        set_error("%s: bad precision %d", who, (int)prec);
+        return DWF_ERR_ARG;
+    }
+    if (nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("%s: nrhs = %d outside [1, %d]", who, nrhs, h->nrhs_max);
+        return DWF_ERR_ARG;
+    }
+    if (!h->have_gauge) {
+        set_error("%s: no gauge field loaded (dwf_set_gauge)", who);
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
+}
+
+extern "C" {
+
+const char* dwf_last_error(void) { return dwf::last_error(); }
+
+dwf_status dwf_create(dwf_handle** h, const dwf_params* p, const dwf_box* boxes, int nbox,
+                      int nrhs_max) {
+    return dwf::create(h, p, boxes, nbox, nrhs_max);
+}
+
+dwf_status dwf_destroy(dwf_handle* h) { return dwf::destroy(h); }
+
+dwf_status dwf_domain_sites(const dwf_handle* h, int parity, int64_t* nsites) {
+    DWF_TRY(check_handle(h));
+    if (nsites == nullptr || (parity != 0 && parity != 1)) {
+        set_error("dwf_domain_sites: bad argument");
+        return DWF_ERR_ARG;
+    }
+    *nsites = h->nsite[parity];
+    return DWF_OK;
+}
+
+dwf_status dwf_box_sites(const dwf_handle* h, int box, int parity, int64_t* offset, int64_t* count) {
+    DWF_TRY(check_handle(h));
+    if (box < 0 || box >= h->nbox || (parity != 0 && parity != 1) || !offset || !count) {
+        set_error("dwf_box_sites: bad argument");
+        return DWF_ERR_ARG;
+    }
+    *offset = h->box_off[parity][box];
+    *count = h->box_cnt[parity][box];
+    return DWF_OK;
+}
+
+dwf_status dwf_set_gauge(dwf_handle* h, const double* U, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (U == nullptr) {
+        set_error("dwf_set_gauge: null gauge pointer");
+        return DWF_ERR_ARG;
+    }
+    return dwf::set_gauge(h, U, (cudaStream_t)stream);
+}
+
+dwf_status dwf_pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_prec prec, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (!dst || !src || bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("dwf_pack: bad argument");
+        return DWF_ERR_ARG;
+    }
+    return dwf::pack(h, dst, src, nrhs, prec, (cudaStream_t)stream);
+}
+
+dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf_prec prec, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (!dst || !src || bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("dwf_unpack: bad argument");
+        return DWF_ERR_ARG;
+    }
+    return dwf::unpack(h, dst, src, nrhs, prec, (cudaStream_t)stream);
+}
+
+dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
+                         dwf_prec prec, int nrhs, void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_dslash_eo"));
+    if (out_parity != 0 && out_parity != 1) {
+        set_error("dwf_dslash_eo: out_parity must be 0 or 1");
+        return DWF_ERR_ARG;
+    }
+    return op_dslash_eo(h, out, in, out_parity, dagger ? 1 : 0, prec, nrhs, h->d_tmp,
+                        (cudaStream_t)stream);
+}
+
+dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity, int dagger, dwf_prec prec,
+                     int nrhs, void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mooee"));
+    if (parity != 0 && parity != 1) {
+        set_error("dwf_mooee: parity must be 0 or 1");
+        return DWF_ERR_ARG;
+    }
+    return op_local(h, L_MOOEE, out, in, nullptr, parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0,
+                    nullptr, (cudaStream_t)stream);
+}
+
+dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity, int dagger,
+                         dwf_prec prec, int nrhs, void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mooee_inv"));
+    if (parity != 0 && parity != 1) {
+        set_error("dwf_mooee_inv: parity must be 0 or 1");
+        return DWF_ERR_ARG;
+    }
+    return op_local(h, L_MINV, out, in, nullptr, parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0,
+                    nullptr, (cudaStream_t)stream);
+}
+
+dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec, int nrhs,
+                   void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mpc"));
+    return op_mpc(h, out, in, dagger ? 1 : 0, prec, prec, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr,
+                  (cudaStream_t)stream);
+}
+
+dwf_status dwf_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec, int nrhs,
+                       void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_apply_d"));
+    return op_apply_d(h, out, in, dagger ? 1 : 0, prec, nrhs, h->d_tmp, (cudaStream_t)stream);
+}
+
+dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec,
+                               int nrhs, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (!h->dirichlet) {
+        set_error("dwf_dirichlet_block: handle was created for the whole lattice (no boxes)");
+        return DWF_ERR_ARG;
+    }
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_dirichlet_block"));
+    return op_apply_d(h, out, in, dagger ? 1 : 0, prec, nrhs, h->d_tmp, (cudaStream_t)stream);
+}
+
+dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
+                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (sp != nullptr && bad_prec(sp->inner_prec)) {
+        set_error("dwf_cgne_solve: bad inner precision");
+        return DWF_ERR_ARG;
+    }
+    if (x != nullptr && x == b) {
+        set_error("dwf_cgne_solve: x and b must not alias");
+        return DWF_ERR_ARG;
+    }
+    return cgne_solve(h, x, b, nrhs, sp, stats, (cudaStream_t)stream);
+}
+
+dwf_status dwf_check_device(dwf_handle* h) {
+    DWF_TRY(check_handle(h));
+    int e = 0;
+    DWF_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        set_error("device error word 0x%x (a bounded wait ran out)", e);
+        return DWF_ERR_DEVICE;
+    }
+    return DWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "dwf.h"
+
+namespace dwf {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kMaxLanes = 256;   // Ls * nrhs
+constexpr int kMaxLs = 32;
+
+// ------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+#define DWF_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            ::dwf::set_error("%s failed: %s (%s:%d)", #call,                  \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);     \
+            return DWF_ERR_CUDA;                                              \
+        }                                                                     \
+    } while (0)
+#define DWF_TRY(expr)                                                         \
+    do {                                                                      \
+        dwf_status s_ = (expr);                                               \
+        if (s_ != DWF_OK) return s_;                                          \
+    } while (0)
+
+// ------------------------------------------------------- tile tables
+// A tile is a contiguous range of one box's sites of one parity:
+// {box, begin, count, 0}.  Every kernel walks a tile table.
+struct TileSet {
+    int T = 0;
+    int ntiles[2] = {0, 0};
+    int4* d_tiles[2] = {nullptr, nullptr};
+    std::vector<int> box_tile_begin[2];          // nbox + 1 entries
+    int* d_box_tile_begin[2] = {nullptr, nullptr};
+};
+
+// Scalar coefficients of the 5th-dimension operators, host-computed in FP64.
+struct FiveD {
+    int Ls;
+    double mf, b5, c5, d, e;
+    double a;        // -e/d
+    double inv_d;    // 1/d
+    double inv_den;  // 1/(d (1 + mf a^Ls))
+};
+
+// Solver workspace of one precision configuration (allocated on first use).
+struct SolverWS {
+    bool ready = false;
+    int nrhs = 0;
+    dwf_prec prec = DWF_FP64;
+    size_t field_elems = 0;      // complex elements of one odd cb field
+    // FP64 state (always)
+    double* x64 = nullptr;       // odd x
+    double* bp64 = nullptr;      // b'_o
+    double* t64a = nullptr;
+    double* t64b = nullptr;
+    double* t64c = nullptr;
+    double* t64d = nullptr;
+    double* full64a = nullptr;   // full-field temporaries (both parities)
+    // inner-loop vectors (FP32 for mixed, FP64 for plain)
+    void* x_lo = nullptr;
+    void* r = nullptr;
+    void* p = nullptr;
+    void* t = nullptr;
+    void* tmp1 = nullptr;        // operator intermediates (op precision)
+    void* tmp2 = nullptr;
+    void* tmp3 = nullptr;
+    // reduction partials and per-system scalars
+    double* part = nullptr;      // [4][ntiles * nrhs]
+    double* sys = nullptr;       // per-system scalars, see solver.cu
+    double* h_sys = nullptr;     // pinned host mirror
+    int nsys = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_iters = 0;
+    cudaStream_t graph_stream = nullptr;
+};
+
+}  // namespace dwf
+
+struct dwf_handle {
+    dwf_params p;
+    int nbox = 1;                 // whole lattice = one box
+    bool dirichlet = false;
+    std::vector<dwf_box> boxes;
+    int nrhs_max = 1;
+    int device = 0;
+    int64_t nsite[2] = {0, 0};
+    int64_t vol = 0;              // total sites of the domain
+    std::vector<int64_t> box_vol;
+    std::vector<int64_t> box_off[2], box_cnt[2];
+    // device tables
+    int* d_nbr[2] = {nullptr, nullptr};        // [nsite][8]
+    int* d_site_box[2] = {nullptr, nullptr};   // [nsite]
+    int* d_site_local[2] = {nullptr, nullptr}; // [nsite] box-local lex
+    int64_t* d_link_src[2] = {nullptr, nullptr}; // [nsite][8] global link or -1
+    int64_t* d_box_canon_vol = nullptr;        // [nbox] box volumes
+    void* d_links[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    bool have_gauge = false;
+    std::map<int, dwf::TileSet> tiles;
+    int* d_err = nullptr;
+    void* d_tmp = nullptr;        // one FP64 cb field x nrhs_max (operator calls)
+    void* d_tmp2 = nullptr;
+    dwf::FiveD f5[2];             // [dagger] (identical scalars, kept per use)
+    std::map<int, dwf::SolverWS> ws;   // keyed by prec * 64 + nrhs
+    // autotuned tile sizes: nrhs -> sites per tile
+    std::map<int, int> tuned_T;
+};
+
+namespace dwf {
+
+// ------------------------------------------------------ host helpers
+const TileSet& get_tiles(dwf_handle* h, int T);
+dwf_status check_handle(const dwf_handle* h);
+size_t prec_size(dwf_prec p);   // bytes per real
+
+// ------------------------------------------------------ launchers
+// hop kinds
+enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1 };
+// site-local operator kinds
+enum LocalOp { L_B = 0, L_MOOEE = 1, L_MINV = 2, L_BMINV = 3, L_POST = 4, L_COPY = 5 };
+
+struct HopCall {
+    const void* in;          // parity 1-p cb field (prec_in)
+    void* out;               // parity p cb field (prec_out)
+    const void* xmoo;        // EPI_MOO: parity p field of prec_out (M_oo input)
+    int out_parity;
+    int dagger;
+    dwf_prec prec_link;      // links / arithmetic class
+    dwf_prec prec_in, prec_out;
+    int nrhs;
+    double scale;            // out = [M_oo x +] scale * Dh in
+    double* partial;         // EPI_MOO: per tile, per rhs |out|^2 (nullable)
+    int T;                   // tile size (0 = tuned/default)
+};
+dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
+
+struct LocalCall {
+    LocalOp op;
+    const void* in;          // field of prec_in
+    const void* in2;         // L_POST: second input (prec_in2)
+    void* out;               // prec_out
+    int parity;
+    int dagger;
+    dwf_prec prec_in, prec_in2, prec_out;
+    int nrhs;
+    double scale;
+    // fused CG update (L_POST only): x += alpha p, r -= alpha * out; |r|^2
+    void* cg_x; void* cg_r; const void* cg_p; dwf_prec prec_vec;
+    const double* alpha;     // per-system (device)
+    const int* run;          // per-system run flags (device, nullable)
+    double* partial;         // per tile, per rhs |result|^2 (nullable)
+    int T;
+};
+dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s);
+
+// elementwise / reduction kernels (blas.cu)
+dwf_status launch_convert(void* dst, dwf_prec pd, const void* src, dwf_prec ps,
+                          size_t n_complex, cudaStream_t s);
+// partial sums per tile and rhs: q0 = Re<a,b> (a == b: |a|^2)
+dwf_status launch_dot_partial(dwf_handle* h, int parity, const void* a, const void* b,
+                              dwf_prec pa, dwf_prec pb, int nrhs, double* partial,
+                              int T, cudaStream_t s);
+// per system (box, rhs): out[sys] = sum over the box's tiles of partial
+dwf_status launch_reduce_sys(dwf_handle* h, int parity, const double* partial, int nrhs,
+                             double* out, int T, cudaStream_t s);
+// y = a*x + b*y per system (scalars from device arrays or immediates)
+dwf_status launch_axpby(dwf_handle* h, int parity, int nrhs, const double* a_sys, double a_imm,
+                        const void* x, dwf_prec px, const double* b_sys, double b_imm,
+                        void* y, dwf_prec py, const int* run, int T, cudaStream_t s);
+
+// ------------------------------------------------------ compositions
+struct CgFuse {
+    void* x;
+    void* r;
+    const void* p;
+    const double* alpha;
+    const int* run;
+};
+dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
+                  dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
+                  const void* xmoo, double* partial, cudaStream_t s);
+dwf_status op_local(dwf_handle* h, LocalOp op, void* out, const void* in, const void* in2,
+                    int parity, int dagger, dwf_prec pin, dwf_prec pin2, dwf_prec pout, int nrhs,
+                    double scale, double* partial, cudaStream_t s);
+dwf_status op_dslash_eo(dwf_handle* h, void* out, const void* in, int p, int dagger,
+                        dwf_prec prec, int nrhs, void* tmp, cudaStream_t s);
+dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec pv, dwf_prec po,
+                  int nrhs, void* tmpA, void* tmpB, double* partial, const CgFuse* cg,
+                  cudaStream_t s);
+dwf_status op_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec,
+                      int nrhs, void* tmp, cudaStream_t s);
+size_t cb_elems(const dwf_handle* h, int parity, int nrhs);
+int tile_for(dwf_handle* h, int nrhs);
+
+// ------------------------------------------------------ domain / solver
+dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, int nbox,
+                  int nrhs_max);
+dwf_status destroy(dwf_handle* h);
+dwf_status set_gauge(dwf_handle* h, const double* U, cudaStream_t s);
+dwf_status pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_prec prec,
+                cudaStream_t s);
+dwf_status unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf_prec prec,
+                  cudaStream_t s);
+void free_solver_ws(dwf_handle* h);
+dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
+                      const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user);
+
+}  // namespace dwf

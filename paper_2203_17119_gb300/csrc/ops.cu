@@ -1,0 +1,168 @@
+// Operator compositions built from the hop and site-local kernels.
+//
+//   M_{p,1-p}        = -Dh_{p,1-p} (b5 + c5 S5) / 2          (off-diagonal block of D)
+//   (M_{1-p,p})^+    = -(b5 + c5 S5^+) Dh^+_{p,1-p} / 2
+//   M_pc             = M_oo - (1/4) Dh_oe [ (b5 + c5 S5) M_ee^-1 ] Dh_eo (b5 + c5 S5)
+//   M_pc^+           = M_oo^+ - (1/4) (b5 + c5 S5^+) Dh^+_oe [ M_ee^-+ (b5 + c5 S5^+) ] Dh^+_eo
+//   D                = [[M_ee, M_eo], [M_oe, M_oo]]
+//
+// (the bracketed site-local factors commute: per chirality both are functions
+// of the same twisted shift).  Shamir (c5 = 0) skips the (b5 + c5 S5) passes
+// and folds b5 into the hop scale.
+#include "dev_common.cuh"
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+// Sites per tile for every kernel of an operator chain with nrhs right-hand
+// sides: the autotuned value if there is one, else 16, at most 256 / N5 so
+// that a hop CTA (N5 / VL threads per site) never exceeds 256 threads.
+int tile_for(dwf_handle* h, int nrhs) {
+    auto it = h->tuned_T.find(nrhs);
+    if (it != h->tuned_T.end()) return it->second;
+    const int n5 = h->p.Ls * nrhs;
+    int T = 16;
+    while (T > 1 && T * n5 > 256) T /= 2;
+    return T;
+}
+
+static int tileT(dwf_handle* h, int, dwf_prec, int nrhs) { return tile_for(h, nrhs); }
+
+size_t cb_elems(const dwf_handle* h, int parity, int nrhs) {
+    return (size_t)h->nsite[parity] * 12 * h->p.Ls * nrhs;   // complex elements
+}
+
+static bool shamir(const dwf_handle* h) { return h->p.c5 == 0.0; }
+
+dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
+                  dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
+                  const void* xmoo, double* partial, cudaStream_t s) {
+    HopCall c;
+    c.in = in;
+    c.out = out;
+    c.xmoo = xmoo;
+    c.out_parity = out_parity;
+    c.dagger = dagger;
+    c.prec_link = link;
+    c.prec_in = pin;
+    c.prec_out = pout;
+    c.nrhs = nrhs;
+    c.scale = scale;
+    c.partial = partial;
+    c.T = tileT(h, 0, link, nrhs);
+    return launch_hop(h, c, s);
+}
+
+dwf_status op_local(dwf_handle* h, LocalOp op, void* out, const void* in, const void* in2,
+                    int parity, int dagger, dwf_prec pin, dwf_prec pin2, dwf_prec pout, int nrhs,
+                    double scale, double* partial, cudaStream_t s) {
+    LocalCall c{};
+    c.op = op;
+    c.in = in;
+    c.in2 = in2;
+    c.out = out;
+    c.parity = parity;
+    c.dagger = dagger;
+    c.prec_in = pin;
+    c.prec_in2 = pin2;
+    c.prec_out = pout;
+    c.nrhs = nrhs;
+    c.scale = scale;
+    c.partial = partial;
+    c.T = tileT(h, 0, pout == DWF_FP64 ? DWF_FP64 : DWF_FP32, nrhs);
+    return launch_local(h, c, s);
+}
+
+// out = M_{p,1-p} in (dagger: (M_{1-p,p})^+ in); in/out/link precision `prec`.
+dwf_status op_dslash_eo(dwf_handle* h, void* out, const void* in, int p, int dagger,
+                        dwf_prec prec, int nrhs, void* tmp, cudaStream_t s) {
+    const double b5 = h->p.b5;
+    if (shamir(h)) return op_hop(h, out, in, p, dagger, prec, prec, prec, nrhs, -0.5 * b5, nullptr, nullptr, s);
+    if (!dagger) {
+        DWF_TRY(op_local(h, L_B, tmp, in, nullptr, 1 - p, 0, prec, prec, prec, nrhs, 1.0, nullptr, s));
+        return op_hop(h, out, tmp, p, 0, prec, prec, prec, nrhs, -0.5, nullptr, nullptr, s);
+    }
+    DWF_TRY(op_hop(h, tmp, in, p, 1, prec, prec, prec, nrhs, 1.0, nullptr, nullptr, s));
+    return op_local(h, L_B, out, tmp, nullptr, p, 1, prec, prec, prec, nrhs, -0.5, nullptr, s);
+}
+
+// Schur operator on the odd checkerboard.  pv: precision of in/out (and of
+// the CG vectors), po: operator precision (links and intermediates).
+// tmpA/tmpB: cb temporaries of precision po.  partial: per-tile |out|^2.
+// cg: optional fused CG step of the adjoint (x += alpha p, r -= alpha out).
+
+dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec pv, dwf_prec po,
+                  int nrhs, void* tmpA, void* tmpB, double* partial, const CgFuse* cg,
+                  cudaStream_t s) {
+    const double b5 = h->p.b5;
+    if (!dagger) {
+        const void* src = in;
+        dwf_prec psrc = pv;
+        double sc1 = b5;
+        if (!shamir(h)) {
+            DWF_TRY(op_local(h, L_B, tmpA, in, nullptr, 1, 0, pv, pv, po, nrhs, 1.0, nullptr, s));
+            src = tmpA;
+            psrc = po;
+            sc1 = 1.0;
+        }
+        DWF_TRY(op_hop(h, tmpB, src, 0, 0, po, psrc, po, nrhs, sc1, nullptr, nullptr, s));
+        DWF_TRY(op_local(h, L_BMINV, tmpA, tmpB, nullptr, 0, 0, po, po, po, nrhs, 1.0, nullptr, s));
+        return op_hop(h, out, tmpA, 1, 0, po, po, pv, nrhs, -0.25, in, partial, s);
+    }
+    DWF_TRY(op_hop(h, tmpB, in, 0, 1, po, pv, po, nrhs, 1.0, nullptr, nullptr, s));
+    DWF_TRY(op_local(h, L_BMINV, tmpA, tmpB, nullptr, 0, 1, po, po, po, nrhs, 1.0, nullptr, s));
+    DWF_TRY(op_hop(h, tmpB, tmpA, 1, 1, po, po, po, nrhs, 1.0, nullptr, nullptr, s));
+    LocalCall c{};
+    c.op = L_POST;
+    c.in = in;
+    c.in2 = tmpB;
+    c.out = out;
+    c.parity = 1;
+    c.dagger = 1;
+    c.prec_in = pv;
+    c.prec_in2 = po;
+    c.prec_out = pv;
+    c.nrhs = nrhs;
+    c.scale = -0.25;
+    c.partial = partial;
+    c.T = tileT(h, 0, pv == DWF_FP64 ? DWF_FP64 : DWF_FP32, nrhs);
+    if (cg) {
+        c.cg_x = cg->x;
+        c.cg_r = cg->r;
+        c.cg_p = cg->p;
+        c.alpha = cg->alpha;
+        c.run = cg->run;
+        c.prec_vec = pv;
+    }
+    return launch_local(h, c, s);
+}
+
+// Full operator on full fields (both parities): D or D^+.
+dwf_status op_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec,
+                      int nrhs, void* tmp, cudaStream_t s) {
+    const size_t ps = prec_size(prec) * 2;
+    const size_t off1 = cb_elems(h, 0, nrhs) * ps;
+    char* o = (char*)out;
+    const char* i = (const char*)in;
+    for (int p = 0; p < 2; ++p) {
+        char* op = o + (p ? off1 : 0);
+        const char* ip = i + (p ? off1 : 0);
+        const char* iq = i + (p ? 0 : off1);
+        if (!dagger) {
+            const void* src = iq;
+            double sc = -0.5 * h->p.b5;
+            if (!shamir(h)) {
+                DWF_TRY(op_local(h, L_B, tmp, iq, nullptr, 1 - p, 0, prec, prec, prec, nrhs, 1.0, nullptr, s));
+                src = tmp;
+                sc = -0.5;
+            }
+            DWF_TRY(op_hop(h, op, src, p, 0, prec, prec, prec, nrhs, sc, ip, nullptr, s));
+        } else {
+            DWF_TRY(op_hop(h, tmp, iq, p, 1, prec, prec, prec, nrhs, 1.0, nullptr, nullptr, s));
+            DWF_TRY(op_local(h, L_POST, op, ip, tmp, p, 1, prec, prec, prec, nrhs, -0.5, nullptr, s));
+        }
+    }
+    return DWF_OK;
+}
+
+}  // namespace dwf

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of ``include/dwf.h`` (argument marshalling only).
+
+Every operator and solver step runs inside ``libdwf.so``; this module only
+passes device pointers, sizes and the current CUDA stream.  It raises
+``DWFError`` when the library has not been built or a call fails -- there
+is no CPU fallback.  Fields are ``torch`` CUDA tensors in the layouts that
+``include/dwf.h`` documents; torch is used for device memory and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libdwf.so")
+
+FP64, FP32, BF16 = 0, 1, 2
+_DTYPE = {FP64: torch.float64, FP32: torch.float32, BF16: torch.bfloat16}
+PREC = {"f64": FP64, "fp64": FP64, "f32": FP32, "fp32": FP32, "bf16": BF16}
+
+STATUS = {0: "DWF_OK", 1: "DWF_ERR_ARG", 2: "DWF_ERR_CUDA", 3: "DWF_ERR_NOT_CONVERGED",
+          4: "DWF_ERR_TIMEOUT", 5: "DWF_ERR_NAN", 6: "DWF_ERR_UNSUPPORTED", 7: "DWF_ERR_DEVICE"}
+
+
+class DWFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("Ls", C.c_int), ("M5", C.c_double),
+                ("mf", C.c_double), ("b5", C.c_double), ("c5", C.c_double)]
+
+
+class Box(C.Structure):
+    _fields_ = [("origin", C.c_int * 4), ("extent", C.c_int * 4)]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("delta", C.c_double),
+                ("restart", C.c_int), ("use_x0", C.c_int), ("inner_prec", C.c_int),
+                ("max_seconds", C.c_double), ("check_every", C.c_int)]
+
+
+class SolverStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("op_applies", C.c_int),
+                ("status", C.c_int), ("true_resid", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libdwf.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise DWFError(2, f"{LIB_PATH} is missing: run __graft_entry__.build() or "
+                              "python -m paper_2203_17119_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
+            "dwf_destroy": [vp],
+            "dwf_domain_sites": [vp, i, C.POINTER(C.c_int64)],
+            "dwf_box_sites": [vp, i, i, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "dwf_set_gauge": [vp, vp, vp],
+            "dwf_pack": [vp, vp, vp, i, i, vp],
+            "dwf_unpack": [vp, vp, vp, i, i, vp],
+            "dwf_dslash_eo": [vp, vp, vp, i, i, i, i, vp],
+            "dwf_mooee": [vp, vp, vp, i, i, i, i, vp],
+            "dwf_mooee_inv": [vp, vp, vp, i, i, i, i, vp],
+            "dwf_mpc": [vp, vp, vp, i, i, i, vp],
+            "dwf_apply_d": [vp, vp, vp, i, i, i, vp],
+            "dwf_dirichlet_block": [vp, vp, vp, i, i, i, vp],
+            "dwf_cgne_solve": [vp, vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+            "dwf_check_device": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.dwf_last_error.restype = C.c_char_p
+        L.dwf_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(st: int, allow=()):
+    if st != 0 and st not in allow:
+        raise DWFError(st, lib().dwf_last_error().decode())
+    return st
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise DWFError(1, "field tensors must live on the GPU")
+    if not t.is_contiguous():
+        raise DWFError(1, "field tensors must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Action:
+    """Operator parameters; Shamir is b5 = 1, c5 = 0."""
+    M5: float = 1.8
+    mf: float = 0.01
+    b5: float = 1.0
+    c5: float = 0.0
+
+
+class Handle:
+    """A ``dwf_handle``: the whole lattice (``boxes=None``) or the Dirichlet
+    blocks of a list of boxes ((origin[4], extent[4]) in x, y, z, t order)."""
+
+    def __init__(self, dims, Ls, action: Action, boxes=None, nrhs_max=1):
+        self.dims = tuple(int(d) for d in dims)
+        self.Ls = int(Ls)
+        self.action = action
+        self.nrhs_max = int(nrhs_max)
+        self.boxes = [tuple(map(tuple, b)) for b in boxes] if boxes else []
+        p = Params((C.c_int * 4)(*self.dims), self.Ls, action.M5, action.mf, action.b5, action.c5)
+        nb = len(self.boxes)
+        arr = (Box * max(nb, 1))()
+        for k, (o, e) in enumerate(self.boxes):
+            arr[k] = Box((C.c_int * 4)(*o), (C.c_int * 4)(*e))
+        h = C.c_void_p()
+        _check(lib().dwf_create(C.byref(h), C.byref(p), arr if nb else None, nb, self.nrhs_max))
+        self._h = h
+        n0, n1 = C.c_int64(), C.c_int64()
+        _check(lib().dwf_domain_sites(h, 0, C.byref(n0)))
+        _check(lib().dwf_domain_sites(h, 1, C.byref(n1)))
+        self.nsite = (n0.value, n1.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dwf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ fields
+    def cb_shape(self, parity, nrhs=1):
+        return (self.nsite[parity], 12, nrhs, self.Ls, 2)
+
+    def full_shape(self, nrhs=1):
+        return (self.nsite[0] + self.nsite[1], 12, nrhs, self.Ls, 2)
+
+    def empty_cb(self, parity, nrhs=1, prec=FP64):
+        return torch.empty(self.cb_shape(parity, nrhs), dtype=_DTYPE[prec], device="cuda")
+
+    def empty_full(self, nrhs=1, prec=FP64):
+        return torch.empty(self.full_shape(nrhs), dtype=_DTYPE[prec], device="cuda")
+
+    def box_sites(self, box, parity):
+        o, c = C.c_int64(), C.c_int64()
+        _check(lib().dwf_box_sites(self._h, box, parity, C.byref(o), C.byref(c)))
+        return o.value, c.value
+
+    # -------------------------------------------------------------- calls
+    def set_gauge(self, U: torch.Tensor, stream=None):
+        """U: complex128 or float64 CUDA tensor, canonical [site][mu][3][3]."""
+        if U.dtype == torch.complex128:
+            U = torch.view_as_real(U)
+        if U.dtype != torch.float64:
+            raise DWFError(1, "gauge field must be complex128 / float64")
+        _check(lib().dwf_set_gauge(self._h, _ptr(U), _stream(stream)))
+
+    def pack(self, canon: torch.Tensor, nrhs=1, prec=FP64, out=None, stream=None):
+        """canonical complex128 [box][r][l][s][spin][colour] -> full field."""
+        if canon.dtype == torch.complex128:
+            canon = torch.view_as_real(canon)
+        out = self.empty_full(nrhs, prec) if out is None else out
+        _check(lib().dwf_pack(self._h, _ptr(out), _ptr(canon), nrhs, prec, _stream(stream)))
+        return out
+
+    def unpack(self, field: torch.Tensor, nrhs=1, prec=FP64, out=None, stream=None):
+        n = (self.nsite[0] + self.nsite[1]) * 12 * nrhs * self.Ls
+        out = torch.empty((n, 2), dtype=torch.float64, device="cuda") if out is None else out
+        _check(lib().dwf_unpack(self._h, _ptr(out), _ptr(field), nrhs, prec, _stream(stream)))
+        return out
+
+    def dslash_eo(self, out, inp, out_parity, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_dslash_eo(self._h, _ptr(out), _ptr(inp), out_parity, int(dagger), prec,
+                                   nrhs, _stream(stream)))
+        return out
+
+    def mooee(self, out, inp, parity, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_mooee(self._h, _ptr(out), _ptr(inp), parity, int(dagger), prec, nrhs,
+                               _stream(stream)))
+        return out
+
+    def mooee_inv(self, out, inp, parity, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_mooee_inv(self._h, _ptr(out), _ptr(inp), parity, int(dagger), prec, nrhs,
+                                   _stream(stream)))
+        return out
+
+    def mpc(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_mpc(self._h, _ptr(out), _ptr(inp), int(dagger), prec, nrhs,
+                             _stream(stream)))
+        return out
+
+    def apply_d(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_apply_d(self._h, _ptr(out), _ptr(inp), int(dagger), prec, nrhs,
+                                 _stream(stream)))
+        return out
+
+    def dirichlet_block(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
+        _check(lib().dwf_dirichlet_block(self._h, _ptr(out), _ptr(inp), int(dagger), prec, nrhs,
+                                         _stream(stream)))
+        return out
+
+    def cgne_solve(self, x, b, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64, delta=0.1,
+                   use_x0=False, max_seconds=0.0, check_every=8, stream=None, allow_fail=False):
+        """Solve D x = b (D_Omega x = b on a box handle); x, b full FP64
+        fields.  Returns the list of per-system stats dicts (box-major)."""
+        sp = SolverParams(tol, maxiter, delta, 16, int(use_x0), inner, max_seconds, check_every)
+        nsys = max(len(self.boxes), 1) * nrhs
+        st = (SolverStats * nsys)()
+        rc = lib().dwf_cgne_solve(self._h, _ptr(x), _ptr(b), nrhs, C.byref(sp), st,
+                                  _stream(stream))
+        if not allow_fail:
+            _check(rc)
+        return [s.as_dict() for s in st], rc
+
+    def check_device(self):
+        return _check(lib().dwf_check_device(self._h))

@@ -1,0 +1,158 @@
+"""GPU parity of every operator entry point against the FP64 oracle.
+
+Element-by-element relative-L2 comparisons at sizes the oracle finishes in
+seconds, spanning several tiles with a ragged last tile, both parities,
+adjoints, Shamir and Moebius, several right-hand sides and Dirichlet boxes
+with odd extents and periodic wrap.  Tolerances (relative L2 per operator
+application): FP64 1e-12, FP32 1e-6, BF16 1e-2.
+"""
+
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import dwf as O
+from paper_2203_17119_gb300 import inputs
+from tests import layout as LY
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2203_17119_gb300 import dwf as G  # noqa: E402
+
+SHAMIR = O.DWFParams(M5=1.8, mf=0.01)
+MOBIUS = O.DWFParams(M5=1.8, mf=0.01, b5=1.5, c5=0.5)
+TOL = {G.FP64: 1e-12, G.FP32: 1e-6, G.BF16: 1e-2}
+# M_pc chains two hops and M_ee^-1: allow the FP32 rounding of three passes
+TOL_MPC = {G.FP64: 1e-12, G.FP32: 2e-6, G.BF16: 1.5e-2}
+
+CASES = {
+    # name: dims, Ls, params, boxes, nrhs, gauge kind
+    "shamir_haar_4444x8": ((4, 4, 4, 4), 8, SHAMIR, None, 1, "haar"),
+    "mobius_ragged_6622x6": ((6, 6, 2, 2), 6, MOBIUS, None, 1, "haar"),
+    "mobius_exp_4468x12_nrhs3": ((4, 4, 6, 8), 12, MOBIUS, None, 3, "exp"),
+    "mobius_boxes_odd_wrap": ((6, 4, 6, 8), 8, MOBIUS,
+                              [((1, 1, 1, 1), (3, 2, 5, 3)), ((5, 0, 3, 7), (4, 4, 4, 4)),
+                               ((0, 0, 0, 0), (6, 4, 6, 1))], 2, "haar"),
+}
+
+
+def _setup(name):
+    dims, Ls, prm, boxes, nrhs, kind = CASES[name]
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    U = inputs.gauge_field(dims, kind, eps=0.3, rng=rng)
+    nb = len(boxes) if boxes else 1
+    masks = [O.box_mask(dims, b) for b in boxes] if boxes else [np.ones(dims[::-1], bool)]
+    psi = [[O.restrict(inputs.gaussian_source(dims, Ls, rng=rng), masks[b]) for _ in range(nrhs)]
+           for b in range(nb)]
+    h = G.Handle(dims, Ls, G.Action(prm.M5, prm.mf, prm.b5, prm.c5), boxes=boxes, nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    return dims, Ls, prm, boxes, nrhs, U, masks, psi, h
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    return _setup(request.param)
+
+
+def _gpu(arr, prec):
+    t = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(arr)))
+    return t.to(device="cuda", dtype=G._DTYPE[prec]).contiguous()
+
+
+def _host(t):
+    return torch.view_as_complex(t.double().cpu().contiguous()).numpy()
+
+
+PRECS = [G.FP64, G.FP32, G.BF16]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_dslash_eo(case, prec, dagger, out_parity):
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    src = LY.to_cb(psi, dims, boxes, 1 - out_parity)
+    want_f = [[O.eo_block_in(U, f, prm, masks[b], out_parity, dagger) for f in psi[b]]
+              for b in range(len(psi))]
+    want = LY.to_cb(want_f, dims, boxes, out_parity)
+    out = h.empty_cb(out_parity, nrhs, prec)
+    h.dslash_eo(out, _gpu(src, prec), out_parity, dagger, prec, nrhs)
+    torch.cuda.synchronize()
+    assert LY.rel_l2(_host(out), want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_mooee_and_inverse(case, prec, dagger, parity):
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    src = LY.to_cb(psi, dims, boxes, parity)
+    for fn, ofn in ((h.mooee, O.mooee), (h.mooee_inv, O.mooee_inv)):
+        want = LY.to_cb([[ofn(f, prm, dagger) for f in psi[b]] for b in range(len(psi))],
+                        dims, boxes, parity)
+        out = h.empty_cb(parity, nrhs, prec)
+        fn(out, _gpu(src, prec), parity, dagger, prec, nrhs)
+        torch.cuda.synchronize()
+        assert LY.rel_l2(_host(out), want) <= TOL[prec], fn.__name__
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True])
+def test_mpc(case, prec, dagger):
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    po = [[O.parity_part(f, 1) for f in row] for row in psi]
+    src = LY.to_cb(po, dims, boxes, 1)
+    want = LY.to_cb([[O.mpc_in(U, f, prm, masks[b], dagger) for f in po[b]]
+                     for b in range(len(po))], dims, boxes, 1)
+    out = h.empty_cb(1, nrhs, prec)
+    h.mpc(out, _gpu(src, prec), dagger, prec, nrhs)
+    torch.cuda.synchronize()
+    assert LY.rel_l2(_host(out), want) <= TOL_MPC[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [False, True])
+def test_full_operator(case, prec, dagger):
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    src = LY.to_full(psi, dims, boxes)
+    if boxes:
+        want_f = [[O.dirichlet_D(U, f, prm, [boxes[b]], dagger) for f in psi[b]]
+                  for b in range(len(psi))]
+    else:
+        want_f = [[O.apply_D(U, f, prm, dagger) for f in psi[0]]]
+    want = LY.to_full(want_f, dims, boxes)
+    out = h.empty_full(nrhs, prec)
+    if boxes:
+        h.dirichlet_block(out, _gpu(src, prec), dagger, prec, nrhs)
+    else:
+        h.apply_d(out, _gpu(src, prec), dagger, prec, nrhs)
+    torch.cuda.synchronize()
+    assert LY.rel_l2(_host(out), want) <= TOL_MPC[prec]
+
+
+def test_dirichlet_block_rejects_whole_lattice():
+    h = G.Handle((4, 4, 4, 4), 4, G.Action(), nrhs_max=1)
+    U = inputs.gauge_field((4, 4, 4, 4), "haar", seed=1)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    a, b = h.empty_full(), h.empty_full()
+    with pytest.raises(G.DWFError):
+        h.dirichlet_block(a, b)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pack_unpack_layout(case, prec):
+    """The library's layout kernels agree with the test-side layout rules."""
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    canon = LY.canonical(psi, boxes, dims)
+    full = h.pack(torch.from_numpy(canon).cuda(), nrhs, prec)
+    torch.cuda.synchronize()
+    assert LY.rel_l2(_host(full), LY.to_full(psi, dims, boxes)) <= TOL[prec]
+    back = h.unpack(full, nrhs, prec)
+    torch.cuda.synchronize()
+    got = back.cpu().numpy().view(np.complex128).reshape(-1)
+    assert LY.rel_l2(got, canon) <= TOL[prec]

@@ -1,0 +1,109 @@
+"""GPU solves against the oracle: every solve must reach a true residual
+|b - D x| / |b| <= 1e-10, recomputed on the CPU by the FP64 oracle from the
+returned x, and agree with the oracle's own CGNE solution."""
+
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import dwf as O
+from paper_2203_17119_gb300 import inputs
+from tests import layout as LY
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2203_17119_gb300 import dwf as G  # noqa: E402
+
+SHAMIR = O.DWFParams(M5=1.8, mf=0.01)
+MOBIUS = O.DWFParams(M5=1.8, mf=0.01, b5=1.5, c5=0.5)
+
+
+def _problem(dims, Ls, prm, kind, boxes=None, nrhs=1, seed=0):
+    rng = np.random.default_rng(seed)
+    U = inputs.gauge_field(dims, kind, eps=0.3, rng=rng)
+    masks = [O.box_mask(dims, b) for b in boxes] if boxes else [np.ones(dims[::-1], bool)]
+    b = [[O.restrict(inputs.gaussian_source(dims, Ls, rng=rng), m) for _ in range(nrhs)]
+         for m in masks]
+    h = G.Handle(dims, Ls, G.Action(prm.M5, prm.mf, prm.b5, prm.c5), boxes=boxes, nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    bf = torch.view_as_real(torch.from_numpy(LY.to_full(b, dims, boxes))).cuda().contiguous()
+    return U, b, h, bf
+
+
+def _residuals(U, prm, x_fields, b_fields, boxes):
+    out = []
+    for k, row in enumerate(b_fields):
+        for r, bb in enumerate(row):
+            x = x_fields[k][r]
+            if boxes:
+                Dx = O.dirichlet_D(U, x, prm, [boxes[k]])
+            else:
+                Dx = O.apply_D(U, x, prm)
+            out.append(O.norm(bb - Dx) / O.norm(bb))
+    return out
+
+
+def _solve_and_check(dims, Ls, prm, kind, inner, boxes=None, nrhs=1, seed=1000, tol=1e-10):
+    U, b, h, bf = _problem(dims, Ls, prm, kind, boxes, nrhs, seed)
+    x = torch.zeros_like(bf)
+    stats, rc = h.cgne_solve(x, bf, nrhs=nrhs, tol=tol, inner=inner)
+    torch.cuda.synchronize()
+    xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, boxes, Ls)
+    res = _residuals(U, prm, xf, b, boxes)
+    for s, r in zip(stats, res):
+        assert s["status"] == 0
+        assert s["true_resid"] <= tol
+        assert r <= tol, (r, s)
+    return U, b, xf, stats
+
+
+def test_cgne_fp64_shamir_4444x8_haar():
+    """Shamir 4^4 x Ls=8, M5 = 1.8, m_f = 0.01, Haar links, FP64 CGNE to
+    1e-10; the solution also matches the oracle's own CGNE solution."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U, b, xf, stats = _solve_and_check(dims, Ls, SHAMIR, "haar", G.FP64, seed=1000)
+    x_or, info = O.cgne(U, b[0][0], SHAMIR, tol=1e-11)
+    assert LY.rel_l2(xf[0][0], x_or) <= 1e-7
+
+
+@pytest.mark.parametrize("inner", [G.FP64, G.FP32, G.BF16])
+def test_cgne_mobius_exp(inner):
+    _solve_and_check((4, 4, 4, 8), 8, MOBIUS, "exp", inner, seed=1001)
+
+
+def test_cgne_mixed_boxes_multi_rhs():
+    boxes = [((1, 1, 1, 1), (3, 2, 4, 5)), ((0, 0, 0, 0), (4, 4, 4, 8)),
+             ((2, 3, 1, 6), (2, 3, 3, 4))]
+    _solve_and_check((4, 4, 4, 8), 8, MOBIUS, "exp", G.FP32, boxes=boxes, nrhs=2, seed=1002)
+
+
+def test_not_converged_status():
+    U, b, h, bf = _problem((4, 4, 4, 4), 8, SHAMIR, "haar", seed=5)
+    x = torch.zeros_like(bf)
+    stats, rc = h.cgne_solve(x, bf, tol=1e-10, maxiter=3, allow_fail=True)
+    assert rc == 3 and stats[0]["status"] == 3
+    assert stats[0]["iters"] >= 3 and stats[0]["true_resid"] > 1e-10
+
+
+def test_nan_source_reported():
+    U, b, h, bf = _problem((4, 4, 4, 4), 8, SHAMIR, "haar", seed=6)
+    bf[3, 2, 0, 1, 0] = float("nan")
+    x = torch.zeros_like(bf)
+    stats, rc = h.cgne_solve(x, bf, tol=1e-10, allow_fail=True)
+    assert rc == 5 and stats[0]["status"] == 5
+
+
+def test_zero_source_and_initial_guess():
+    U, b, h, bf = _problem((4, 4, 4, 4), 8, MOBIUS, "haar", seed=7)
+    x = torch.zeros_like(bf)
+    stats, rc = h.cgne_solve(x, torch.zeros_like(bf), tol=1e-10)
+    assert stats[0]["iters"] == 0 and float(x.abs().max()) == 0.0
+    stats, rc = h.cgne_solve(x, bf, tol=1e-10)
+    it0 = stats[0]["iters"]
+    stats, rc = h.cgne_solve(x, bf, tol=1e-10, use_x0=True)
+    assert stats[0]["iters"] < max(2, it0 // 4)
