@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the domain wall fermion hot path on one GB300 (per rank).
+
+Workload (default): Moebius DWF on 16^4 x Ls=12 (b5=1.5, c5=0.5, M5=1.8,
+m_f=0.01), links U = exp(i 0.3 H) from seed 1001, one Gaussian source.
+One step = the whole hot path on that source:
+
+  * mixed-precision CGNE of D x = b to |b - D x|/|b| <= 1e-10 (FP32 operator,
+    FP32 vectors, FP64 reliable updates, FP64 reductions and solution);
+  * the same solve with the Dirichlet block operator D_Omega of the 14^4
+    interior box left by a band of width 2 in all four directions.
+
+The printed value is the Dslash-model throughput of the step: every Wilson
+hop the step applies counts 1320 flops per 5D site of its checkerboard,
+divided by the step time (CUDA events).  Beside it: time to solution of
+each solve, the plain FP64 CG time for the same system, the bare-hop
+roofline (FP32, L2 flushed between launches) and the CPU oracle baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DWF Dslash TFLOP/s & HBM GB/s; time-to-1e-10 residual vs plain FP64 CG"
+DIMS, LS = (16, 16, 16, 16), 12
+M5, MF, B5, C5 = 1.8, 0.01, 1.5, 0.5
+EPS, SEED = 0.3, 1001
+BAND_BOX = ((1, 1, 1, 1), (14, 14, 14, 14))
+FLOPS_PER_SITE = 1320
+WORKLOAD = ("Moebius DWF 16^4 x Ls=12 (b5=1.5, c5=0.5, M5=1.8, m_f=0.01, exp(i 0.3 H) links); "
+            "mixed FP32/FP64 CGNE to 1e-10 of D and of D_Omega (w=2 band, 14^4 interior box)")
+
+
+def hop_bytes_per_site(Ls, word):
+    """Algorithmic bytes per 5D output site of one hop: spinor in + out
+    (24 reals each) and the site's share of the 4V links (144/Ls reals)."""
+    return (48.0 + 144.0 / Ls) * word
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"dwf_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    act = G.Action(M5, MF, B5, C5)
+    rng = np.random.default_rng(SEED)
+    U = inputs.gauge_field(DIMS, "exp", eps=EPS, rng=rng)
+    src = inputs.gaussian_source(DIMS, LS, rng=rng)
+    Ut = torch.from_numpy(U.reshape(-1)).to(dev)
+    hD = G.Handle(DIMS, LS, act)
+    hD.set_gauge(Ut)
+    hO = G.Handle(DIMS, LS, act, boxes=[BAND_BOX])
+    hO.set_gauge(Ut)
+    # sources in the canonical layout -> device fields
+    canonD = torch.from_numpy(src.reshape(-1)).to(dev)
+    o, e = BAND_BOX
+    sub = src[o[3]:o[3] + e[3], o[2]:o[2] + e[2], o[1]:o[1] + e[1], o[0]:o[0] + e[0]]
+    canonO = torch.from_numpy(np.ascontiguousarray(sub).reshape(-1)).to(dev)
+    tiles = {"D": hD.autotune(1, G.FP32), "D_Omega": hO.autotune(1, G.FP32)}
+    bD, bO = hD.pack(canonD), hO.pack(canonO)
+    xD, xO = torch.zeros_like(bD), torch.zeros_like(bO)
+    sitesD = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
+    sitesO = (e[0] * e[1] * e[2] * e[3]) // 2 * LS
+    del canonD, canonO
+
+    def step(host=None):
+        stats = []
+        for h, x, b, hb, hx in ((hD, xD, bD, host and host[0], host and host[1]),
+                                (hO, xO, bO, host and host[2], host and host[3])):
+            if hb is not None:
+                b.copy_(hb, non_blocking=True)
+            x.zero_()
+            st, _ = h.cgne_solve(x, b, tol=1e-10, inner=G.FP32, delta=0.1)
+            if hx is not None:
+                hx.copy_(x, non_blocking=True)
+            stats.append(st[0])
+        return stats
+
+    def flops(stats):
+        # each M_pc application = 2 hops; + b' (1 hop), x_e (1 hop), final D (2 hops)
+        return sum((2 * s["op_applies"] + 4) * FLOPS_PER_SITE * n
+                   for s, n in zip(stats, (sitesD, sitesO)))
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = G.launch_count()
+    print(f"[bench] launches before timed region: {l0}", file=sys.stderr)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    all_stats = []
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        all_stats.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = G.launch_count() - l0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(times)
+    tot_flops = sum(flops(s) for s in all_stats)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * tot_flops / (tot_ms * 1e-3) / 1e12
+    last = all_stats[-1]
+
+    # ---- end to end: host (pinned) source in, solution out, per step
+    hb = [bD.cpu().pin_memory(), None, bO.cpu().pin_memory(), None]
+    hb[1] = torch.empty_like(hb[0]).pin_memory()
+    hb[3] = torch.empty_like(hb[2]).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    e2e_flops = 0
+    for k in range(args.steps):
+        e2e_ev[k][0].record(stream)
+        st = step(hb)
+        e2e_ev[k][1].record(stream)
+        e2e_flops += flops(st)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    h2d = (bD.numel() + bO.numel()) * bD.element_size()
+    d2h = (xD.numel() + xO.numel()) * xD.element_size()
+
+    # ---- plain FP64 CG on the same two systems (time to 1e-10)
+    fp64 = {}
+    for name, h, x, b in (("D", hD, xD, bD), ("D_Omega", hO, xO, bO)):
+        x.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        st, _ = h.cgne_solve(x, b, tol=1e-10, inner=G.FP64)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        fp64[name] = {"ms": s0.elapsed_time(s1), "iters": st[0]["iters"],
+                      "true_resid": st[0]["true_resid"]}
+    mixed_ms = {"D": last[0]["seconds"] * 1e3, "D_Omega": last[1]["seconds"] * 1e3}
+
+    # ---- bare hop (dominant kernel): CUDA events per launch, L2 flushed
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hop = {}
+    for name, prec, word in (("f32", G.FP32, 4), ("bf16", G.BF16, 2), ("f64", G.FP64, 8)):
+        inp = torch.randn(hD.cb_shape(1), device=dev).to(G._DTYPE[prec])
+        out = hD.empty_cb(0, 1, prec)
+        for _ in range(3):
+            hD.hop(out, inp, 0, prec=prec)
+        ts = []
+        for _ in range(max(args.steps, 10)):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hD.hop(out, inp, 0, prec=prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.mean(ts)
+        nbytes = hop_bytes_per_site(LS, word) * sitesD
+        hop[name] = {"ms": ms, "tflops": FLOPS_PER_SITE * sitesD / (ms * 1e-3) / 1e12,
+                     "gbs": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
+        del inp, out
+    del flush
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "hop_f32_traffic.json")))
+        src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2203_17119_gb300", "csrc", "hop.cu"),
+                                       "rb").read()).hexdigest()[:16]
+        if prof.get("hop_cu_sha256_16") == src_hash:
+            traffic = prof["dram_bytes_per_launch_scaled"]
+    except (OSError, ValueError, KeyError):
+        pass
+    roof = {"bound": "hbm", "kernel": "k_hop<float> (bare Wilson hop, FP32, Ls=12)",
+            "achieved": round(hop["f32"]["gbs"], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(hop["f32"]["gbs"] / peak, 3), "traffic": traffic,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+            else "fallback 6800 GB/s"}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded exp(i 0.3 H) SU(3) links, Gaussian source)",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS,
+                   "inner": "FP32 operator + FP32 vectors; FP64 reliable updates/reductions/x",
+                   "l2": "working set > L2 (FP64 + FP32 solver state ~0.6 GB per solve)",
+                   "parallelism": f"replicas x{world}", "autotuned_tile_sites": tiles},
+        "time_to_solution_ms": {k: round(v, 3) for k, v in mixed_ms.items()},
+        "iters": {"D": last[0]["iters"], "D_Omega": last[1]["iters"]},
+        "reliable_updates": {"D": last[0]["reliable_updates"], "D_Omega": last[1]["reliable_updates"]},
+        "true_resid": {"D": last[0]["true_resid"], "D_Omega": last[1]["true_resid"]},
+        "fp64_cg": fp64,
+        "speedup_vs_fp64_cg": {k: round(fp64[k]["ms"] / mixed_ms[k], 2) for k in mixed_ms},
+        "dslash": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
+                   for k, v in hop.items()},
+        "roofline": roof,
+        "e2e": {"value": round(world * e2e_flops / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return result
+
+
+# --------------------------------------------------------- CPU oracle leg
+def oracle_sample(seconds_hint=None):
+    """Time the oracle's Wilson hop (whole lattice, both parities) on the
+    workload's lattice once in a single-threaded subprocess; returns
+    (TFLOP/s, seconds, cores)."""
+    code = (
+        "import time, numpy as np, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from oracle import dwf as O\n"
+        "from paper_2203_17119_gb300 import inputs\n"
+        f"rng = np.random.default_rng({SEED})\n"
+        f"U = inputs.gauge_field({DIMS}, 'exp', eps={EPS}, rng=rng)\n"
+        f"psi = inputs.gaussian_source({DIMS}, {LS}, rng=rng)\n"
+        "t = time.perf_counter(); O.hop(U, psi); dt = time.perf_counter() - t\n"
+        "print(dt)\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    dt = float(out.stdout.strip().splitlines()[-1])
+    sites = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * LS   # both parities
+    return FLOPS_PER_SITE * sites / dt / 1e12, dt, 1
+
+
+def run_reference(args):
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        v, dt, cores = oracle_sample()
+        if k >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+    value = statistics.mean(vals)
+    sample = (f"oracle Wilson hop Dh on the whole 16^4 x Ls=12 lattice (both parities, "
+              f"{DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * LS} 5D sites) per step, numpy FP64, 1 thread")
+    return {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS}, "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_hop(args):
+    """Bare Wilson hop at a chosen size: --hop L Ls prec [nrhs] (CUDA events
+    per launch, L2 flushed between launches).  Used for the Dslash sweep and
+    as the command the hop profiles are captured from."""
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    L, Ls, prec_name = int(args.hop[0]), int(args.hop[1]), args.hop[2]
+    nrhs = int(args.hop[3]) if len(args.hop) > 3 else 1
+    prec = G.PREC[prec_name]
+    word = {G.FP64: 8, G.FP32: 4, G.BF16: 2}[prec]
+    dims = (L, L, L, L)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, seed=SEED)
+    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    del U
+    T = h.autotune(nrhs, prec) if not args.no_autotune else None
+    inp = torch.randn(h.cb_shape(1, nrhs), device="cuda").to(G._DTYPE[prec])
+    out = h.empty_cb(0, nrhs, prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        h.hop(out, inp, 0, prec=prec, nrhs=nrhs)
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.hop(out, inp, 0, prec=prec, nrhs=nrhs)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    sites = L ** 4 // 2 * Ls * nrhs
+    nbytes = (48.0 + 144.0 / (Ls * nrhs)) * word * sites
+    peak = 6800.0
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    print(json.dumps({"kernel": "hop", "lattice": [L] * 4, "Ls": Ls, "nrhs": nrhs, "prec": prec_name,
+                      "tile_sites": T, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
+                      "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
+                      "algorithmic_bytes": nbytes}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--hop", nargs="+", metavar="ARG",
+                    help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    if args.hop:
+        run_hop(args)
+        return
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, dt, cores = oracle_sample()
+            res["cpu_baseline"] = {
+                "value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                "sample": f"one oracle Wilson hop on the whole 16^4 x Ls=12 lattice ({dt:.1f} s, "
+                          "numpy FP64, 1 thread); same flop model as value"}
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

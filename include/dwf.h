@@ -141,6 +141,13 @@ dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs,
 dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parity,
                          int dagger, dwf_prec prec, int nrhs, void* stream);
 
+/* out = Dh_{p,1-p} in: the bare Wilson hop of D_W = (4 - M5) - Dh/2 on every
+ * lane (spin projection, SU(3) transport of two colour vectors, rebuild),
+ * links of precision `prec`; dagger swaps the projectors (1 -+ g_mu).  This
+ * single kernel is the one every operator above is built around. */
+dwf_status dwf_hop(dwf_handle* h, void* out, const void* in, int out_parity,
+                   int dagger, dwf_prec prec, int nrhs, void* stream);
+
 /* out = M_ee in (= M_oo in; either parity, `parity` selects the site count);
  * dagger: M_ee^+ in. */
 dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity,
@@ -153,6 +160,7 @@ dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity,
 /* out = M_pc in on the odd checkerboard; dagger: M_pc^+ in. */
 dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger,
                    dwf_prec prec, int nrhs, void* stream);
+
 
 /* out = D in (full fields, both parities) for a whole-lattice handle, or
  * D_Omega in for a box handle; dagger: the adjoint. */
@@ -200,6 +208,18 @@ typedef struct {
 dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
                           const dwf_solver_params* sp, dwf_solver_stats* stats,
                           void* stream);
+
+/* Autotuner: time the hop kernel for nrhs right-hand sides in precision
+ * `prec` over candidate tile sizes (sites per CTA tile: 8..128) and keep the
+ * fastest for every later call on this handle with that nrhs (all kernels of
+ * an operator chain share one tile table).  Synchronous; uses the handle's
+ * scratch fields, so it must not overlap other calls on the handle.
+ * tile_sites (nullable) receives the choice. */
+dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites);
+
+/* Number of kernels the library has launched in this process so far (a
+ * captured CUDA graph counts its kernels on every replay). */
+dwf_status dwf_launch_count(uint64_t* n);
 
 /* Device error word (bounded waits that ran out); DWF_ERR_DEVICE if set. */
 dwf_status dwf_check_device(dwf_handle* h);

@@ -110,6 +110,39 @@ dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parit
                         (cudaStream_t)stream);
 }
 
+dwf_status dwf_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger, dwf_prec prec,
+                   int nrhs, void* stream) {
+    DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_hop"));
+    if (out_parity != 0 && out_parity != 1) {
+        set_error("dwf_hop: out_parity must be 0 or 1");
+        return DWF_ERR_ARG;
+    }
+    return op_hop(h, out, in, out_parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0, nullptr, nullptr,
+                  (cudaStream_t)stream);
+}
+
+dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites) {
+    DWF_TRY(check_handle(h));
+    if (bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("dwf_autotune: bad precision or nrhs");
+        return DWF_ERR_ARG;
+    }
+    if (!h->have_gauge) {
+        set_error("dwf_autotune: no gauge field loaded");
+        return DWF_ERR_ARG;
+    }
+    return autotune(h, nrhs, prec, tile_sites);
+}
+
+dwf_status dwf_launch_count(uint64_t* n) {
+    if (n == nullptr) {
+        set_error("dwf_launch_count: null pointer");
+        return DWF_ERR_ARG;
+    }
+    *n = launch_count();
+    return DWF_OK;
+}
+
 dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity, int dagger, dwf_prec prec,
                      int nrhs, void* stream) {
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mooee"));

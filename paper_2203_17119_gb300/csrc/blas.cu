@@ -57,6 +57,7 @@ static dwf_status conv_from(void* dst, const void* src, dwf_prec ps, size_t n, c
         case DWF_FP32: k_convert<Sd, float><<<blocks, threads, 0, s>>>((Sd*)dst, (const float*)src, n); break;
         default: k_convert<Sd, bf16><<<blocks, threads, 0, s>>>((Sd*)dst, (const bf16*)src, n); break;
     }
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }
@@ -76,19 +77,27 @@ template <class Sx, class Sy>
 __global__ void k_axpby(const int4* __restrict__ tiles, int nrhs, int Ls, const double* a_sys,
                         double a_imm, const Sx* __restrict__ x, const double* b_sys, double b_imm,
                         Sy* __restrict__ y, const int* run) {
+    using R = typename std::conditional<std::is_same<Sx, double>::value ||
+                                            std::is_same<Sy, double>::value,
+                                        double, float>::type;
     const int4 tl = tiles[blockIdx.x];
-    const int64_t n = (int64_t)tl.z * 12 * nrhs * Ls;      // complex elements
+    const int npair = tl.z * 12 * nrhs * Ls / 2;   // pairs of complex (Ls is even)
     const int64_t off = (int64_t)tl.y * 12 * nrhs * Ls;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int r = (int)((i / Ls) % nrhs);
+    for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+        const int r = (2 * i / Ls) % nrhs;
         const int sys = tl.x * nrhs + r;
         if (run != nullptr && run[sys] == 0) continue;
-        const double av = a_sys ? a_sys[sys] : a_imm;
-        const double bv = b_sys ? b_sys[sys] : b_imm;
-        double xr = 0, xi = 0, yr = 0, yi = 0;
-        if (x != nullptr) ld2<Sx>(x + 2 * (off + i), xr, xi);
-        if (bv != 0.0) ld2<Sy>(y + 2 * (off + i), yr, yi);
-        st2<Sy>(y + 2 * (off + i), av * xr + bv * yr, av * xi + bv * yi);
+        const R av = (R)(a_sys ? a_sys[sys] : a_imm);
+        const R bv = (R)(b_sys ? b_sys[sys] : b_imm);
+        R xr[2] = {0, 0}, xi[2] = {0, 0}, yr[2] = {0, 0}, yi[2] = {0, 0};
+        if (x != nullptr) load_lanes<Sx, 2, R>(x + 2 * (off + 2 * i), xr, xi);
+        if (bv != (R)0) load_lanes<Sy, 2, R>(y + 2 * (off + 2 * i), yr, yi);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            yr[v] = av * xr[v] + bv * yr[v];
+            yi[v] = av * xi[v] + bv * yi[v];
+        }
+        store_lanes<Sy, 2, R>(y + 2 * (off + 2 * i), yr, yi);
     }
 }
 
@@ -107,6 +116,7 @@ static dwf_status axpby_y(const int4* tiles, int nt, int nrhs, int Ls, const dou
         default:
             k_axpby<bf16, Sy><<<nt, 256, 0, s>>>(tiles, nrhs, Ls, a_sys, a_imm, (const bf16*)x, b_sys, b_imm, (Sy*)y, run);
     }
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }
@@ -136,15 +146,24 @@ __global__ void __launch_bounds__(512) k_dot_partial(const int4* __restrict__ ti
     const int rows = tl.z * 12 * nrhs;
     const int64_t off = (int64_t)tl.y * 12 * nrhs * Ls;
     double acc = 0.0;
+    // FP64 inputs accumulate in FP64; FP32/BF16 rows sum in FP32, rows in FP64
+    using RA = typename std::conditional<std::is_same<Sa, double>::value ||
+                                             std::is_same<Sb, double>::value,
+                                         double, float>::type;
     for (int row = threadIdx.x; row < rows; row += blockDim.x) {
         const int64_t base = off + (int64_t)row * Ls;
-        for (int s = 0; s < Ls; ++s) {
-            double ar, ai, br, bi;
-            ld2<Sa>(a + 2 * (base + s), ar, ai);
-            if ((const void*)a == (const void*)b) { br = ar; bi = ai; }
-            else ld2<Sb>(b + 2 * (base + s), br, bi);
-            acc += ar * br + ai * bi;
+        RA rs = 0;
+        for (int s = 0; s < Ls; s += 2) {
+            RA ar[2], ai[2], br[2], bi[2];
+            load_lanes<Sa, 2, RA>(a + 2 * (base + s), ar, ai);
+            if ((const void*)a == (const void*)b) {
+                br[0] = ar[0]; bi[0] = ai[0]; br[1] = ar[1]; bi[1] = ai[1];
+            } else {
+                load_lanes<Sb, 2, RA>(b + 2 * (base + s), br, bi);
+            }
+            rs += ar[0] * br[0] + ai[0] * bi[0] + ar[1] * br[1] + ai[1] * bi[1];
         }
+        acc += (double)rs;
     }
     const int nr = nrhs;
     block_rhs_reduce(acc, s_red, nrhs, [&](int t) { return t < rows ? t % nr : -1; },
@@ -169,6 +188,7 @@ static dwf_status dot_a(const int4* tl, int nt, int nrhs, int Ls, const void* a,
         case DWF_FP32: k_dot_partial<Sa, float><<<nt, threads, 0, s>>>(tl, nrhs, Ls, (const Sa*)a, (const float*)b, partial); break;
         default: k_dot_partial<Sa, bf16><<<nt, threads, 0, s>>>(tl, nrhs, Ls, (const Sa*)a, (const bf16*)b, partial);
     }
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }
@@ -209,6 +229,7 @@ dwf_status launch_reduce_sys(dwf_handle* h, int parity, const double* partial, i
                              double* out, int T, cudaStream_t s) {
     const TileSet& ts = get_tiles(h, T > 0 ? T : 16);
     k_reduce_sys<<<h->nbox * nrhs, 256, 0, s>>>(partial, ts.d_box_tile_begin[parity], nrhs, out);
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }

@@ -7,6 +7,7 @@
 // and a zero link, and the kernels skip it.  Sites outside every box are not
 // stored at all, so the operator never touches Omega-bar.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,6 +28,19 @@ void set_error(const char* fmt, ...) {
 }
 
 const char* last_error() { return g_err; }
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local int g_capturing = 0;
+static thread_local int g_captured = 0;
+
+void note_launch() {
+    if (g_capturing) ++g_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void capture_begin() { g_capturing = 1; g_captured = 0; }
+int capture_end() { g_capturing = 0; return g_captured; }
+void note_graph_launch(int kernels) { g_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(); }
 
 size_t prec_size(dwf_prec p) { return p == DWF_FP64 ? 8 : (p == DWF_FP32 ? 4 : 2); }
 
@@ -150,6 +164,7 @@ static dwf_status pack_t(dwf_handle* h, S* dom, double* canon, int nrhs, cudaStr
                                                       h->d_site_local[p], h->d_box_canon_vol,
                                                       h->d_box_canon_vol + h->nbox, h->nsite[p],
                                                       off, nrhs, h->p.Ls);
+            note_launch();
             DWF_CUDA(cudaGetLastError());
         }
         off += n;
@@ -184,6 +199,7 @@ dwf_status set_gauge(dwf_handle* h, const double* U, cudaStream_t s) {
         const int64_t blocks = std::min<int64_t>((n * 9 + 255) / 256, 152 * 64);
         k_gather_links<<<(int)blocks, 256, 0, s>>>(U, h->d_link_src[p], n, (double*)h->d_links[0][p],
                                                    (float*)h->d_links[1][p], (bf16*)h->d_links[2][p]);
+        note_launch();
         DWF_CUDA(cudaGetLastError());
     }
     DWF_CUDA(cudaStreamSynchronize(s));
@@ -362,6 +378,8 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         if (st == DWF_OK)
             cudaMemcpy(h->d_box_canon_vol, bv.data(), bv.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     }
+    if (st == DWF_OK) st = init_hop_kernels();
+    if (st == DWF_OK) st = init_local_kernels();
     if (st == DWF_OK) st = dalloc(&h->d_err, 1);
     if (st == DWF_OK) {
         cudaMemset(h->d_err, 0, sizeof(int));
@@ -369,6 +387,7 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         st = dalloc((double**)&h->d_tmp, nmax);
         if (st == DWF_OK) st = dalloc((double**)&h->d_tmp2, nmax);
     }
+    if (st == DWF_OK) get_tiles(h, 32);   // default tile table, built up front
     if (st == DWF_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {

@@ -18,9 +18,18 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kMaxLanes = 256;   // Ls * nrhs
 constexpr int kMaxLs = 32;
+constexpr int kHopMaxSmem = 200 * 1024;   // dynamic shared memory cap of the hop
+constexpr int kMinTile = 4;               // smallest tile the autotuner may pick
 
 // ------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
+
+// kernel launch accounting (graph captures count into the graph instead)
+void note_launch();
+void capture_begin();
+int capture_end();           // kernels recorded since capture_begin
+void note_graph_launch(int kernels);
+uint64_t launch_count();
 #define DWF_CUDA(call)                                                        \
     do {                                                                      \
         cudaError_t e_ = (call);                                              \
@@ -86,6 +95,8 @@ struct SolverWS {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;
+    int graph_T = 0;
+    int graph_kernels = 0;
     cudaStream_t graph_stream = nullptr;
 };
 
@@ -131,7 +142,7 @@ size_t prec_size(dwf_prec p);   // bytes per real
 // hop kinds
 enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1 };
 // site-local operator kinds
-enum LocalOp { L_B = 0, L_MOOEE = 1, L_MINV = 2, L_BMINV = 3, L_POST = 4, L_COPY = 5 };
+enum LocalOp { L_B = 0, L_MOOEE = 1, L_MINV = 2, L_BMINV = 3, L_POST = 4, L_COPY = 5, L_PB = 6 };
 
 struct HopCall {
     const void* in;          // parity 1-p cb field (prec_in)
@@ -147,6 +158,9 @@ struct HopCall {
     int T;                   // tile size (0 = tuned/default)
 };
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
+dwf_status init_hop_kernels();
+dwf_status init_local_kernels();
+dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
 
 struct LocalCall {
     LocalOp op;
@@ -160,7 +174,7 @@ struct LocalCall {
     double scale;
     // fused CG update (L_POST only): x += alpha p, r -= alpha * out; |r|^2
     void* cg_x; void* cg_r; const void* cg_p; dwf_prec prec_vec;
-    const double* alpha;     // per-system (device)
+    const double* alpha;     // per-system (device); beta for L_PB
     const int* run;          // per-system run flags (device, nullable)
     double* partial;         // per tile, per rhs |result|^2 (nullable)
     int T;
@@ -203,6 +217,9 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
                   cudaStream_t s);
 dwf_status op_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec,
                       int nrhs, void* tmp, cudaStream_t s);
+dwf_status op_mpc_pre(dwf_handle* h, void* out, const void* p, const void* t1, dwf_prec pv,
+                      dwf_prec po, int nrhs, void* tmpA, void* tmpB, double* partial,
+                      cudaStream_t s);
 size_t cb_elems(const dwf_handle* h, int parity, int nrhs);
 int tile_for(dwf_handle* h, int nrhs);
 

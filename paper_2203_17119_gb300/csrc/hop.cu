@@ -17,6 +17,8 @@
 //            MOO     out = M_oo x + scale * Dh in  (+ per-tile |out|^2),
 //            the last step of the Schur operator M_pc = M_oo - M_oe M_ee^-1 M_eo.
 #include <cstdio>
+#include <map>
+#include <utility>
 
 #include "dev_common.cuh"
 #include "dwf_internal.cuh"
@@ -30,7 +32,7 @@ struct HopArgs {
     const void* links;   // parity table [site][8][9] complex (site-major)
     const int* nbr;      // [site][8]
     const int4* tiles;
-    int T, N5, Ls, nrhs;
+    int T, N5, Ls, nrhs, ntiles;
     double scale, d, e, mf;
     double* partial;
     int* err;
@@ -139,58 +141,90 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
         }
 }
 
+// Persistent kernel: CTA b takes tiles b, b + gridDim, ...; the links and
+// neighbour indices of the next tile are bulk-copied into the other half of
+// a double buffer while the current tile is computed.
 template <class Sin, class Sout, class SL, class R, int VL, bool DAG, int EPI>
-__global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
+__global__ void __launch_bounds__(256, 2) k_hop(const HopArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int4 tl = a.tiles[blockIdx.x];
-    const int begin = tl.y, count = tl.z;
     const int TPS = a.N5 / VL;
-    SL* s_link = reinterpret_cast<SL*>(smem);
-    int* s_nbr = reinterpret_cast<int*>(smem + (size_t)a.T * 144 * sizeof(SL));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)a.T * (144 * sizeof(SL) + 32));
+    const size_t link_bytes = (size_t)a.T * 144 * sizeof(SL);
+    const size_t buf_bytes = link_bytes + (size_t)a.T * 32;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * buf_bytes);
     double* s_red = reinterpret_cast<double*>(bar + 2);
     __shared__ int s_ok;
+    const int nt = a.ntiles;
+
+    auto issue = [&](int tile, int b) {
+        const int4 t = a.tiles[tile];
+        const uint32_t lb = (uint32_t)t.z * 144u * (uint32_t)sizeof(SL);
+        const uint32_t nb = (uint32_t)t.z * 32u;
+        unsigned char* base = smem + b * buf_bytes;
+        // order the generic-proxy reads of this buffer before the async write
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[b], lb + nb);
+        bulk_g2s(base, reinterpret_cast<const SL*>(a.links) + (int64_t)t.y * 144, lb, &bar[b]);
+        bulk_g2s(base + link_bytes, a.nbr + (int64_t)t.y * 8, nb, &bar[b]);
+    };
 
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
-        const uint32_t lb = (uint32_t)count * 144u * (uint32_t)sizeof(SL);
-        const uint32_t nb = (uint32_t)count * 32u;
-        mbar_expect_tx(bar, lb + nb);
-        bulk_g2s(s_link, reinterpret_cast<const SL*>(a.links) + (int64_t)begin * 144, lb, bar);
-        bulk_g2s(s_nbr, a.nbr + (int64_t)begin * 8, nb, bar);
-        bool ok = mbar_wait_bounded(bar, 0);
-        if (!ok) {
-            atomicOr(a.err, kErrBulkTimeout);
-            mbar_wait_bounded(bar, 0);   // give the copy a second chance to land
-        }
-        s_ok = ok ? 1 : 0;
+        if ((int)blockIdx.x < nt) issue(blockIdx.x, 0);
     }
     __syncthreads();
-    if (!s_ok) return;   // uniform across the CTA
 
-    const int sl = threadIdx.x / TPS;
-    const int lane0 = (threadIdx.x - sl * TPS) * VL;
-    const bool active = sl < count;
+    const int G = blockDim.x / TPS;
+    const int sg = threadIdx.x / TPS;
+    const int lane0 = (threadIdx.x - sg * TPS) * VL;
     const int N5 = a.N5;
-    double my_norm = 0.0;
+    const Sin* in = reinterpret_cast<const Sin*>(a.in);
 
-    if (active) {
+    int k = 0;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (threadIdx.x == 0) {
+            const int next = tile + gridDim.x;
+            if (next < nt) issue(next, b ^ 1);   // the other buffer is free
+            bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
+            if (!ok) {
+                atomicOr(a.err, kErrBulkTimeout);
+                mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            // a lost copy: let the one in flight land, then stop (uniform)
+            if (threadIdx.x == 0 && tile + gridDim.x < nt)
+                mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+            return;
+        }
+        const int4 tl = a.tiles[tile];
+        const int begin = tl.y, count = tl.z;
+        const SL* s_link_t = reinterpret_cast<const SL*>(smem + b * buf_bytes);
+        const int* s_nbr_t = reinterpret_cast<const int*>(smem + b * buf_bytes + link_bytes);
+        double tile_norm = 0.0;
+
+    for (int sl = sg; sg < G && sl < count; sl += G) {
         R ar[12][VL], ai[12][VL];
 #pragma unroll
         for (int c = 0; c < 12; ++c)
 #pragma unroll
             for (int v = 0; v < VL; ++v) ar[c][v] = ai[c][v] = (R)0;
         const Sin* in = reinterpret_cast<const Sin*>(a.in);
-        const int* nb = s_nbr + sl * 8;
-        const SL* lk = s_link + (size_t)sl * 144;
+        const int* nb = s_nbr_t + sl * 8;
+        const SL* lk = s_link_t + (size_t)sl * 144;
+        // +mu and -mu back to back: the row that is the +x neighbour of
+        // one site is the -x neighbour of the next, still in L1
         hop_dir<0, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<1, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<2, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
         hop_dir<4, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+        hop_dir<1, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
         hop_dir<5, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+        hop_dir<2, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
         hop_dir<6, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+        hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
         hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
 
         const R sc = (R)a.scale;
@@ -253,15 +287,17 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
                 if (sizeof(R) != 8) nrm += (double)part;
                 store_lanes<Sout, VL, R>(out + (int64_t)c * N5 * 2, orr, oi);
             }
-            my_norm = nrm;
+            tile_norm += nrm;
         }
     }
-    if (EPI == EPI_MOO && a.partial != nullptr) {
-        const int Ls = a.Ls;
-        block_rhs_reduce(
-            my_norm, s_red, a.nrhs,
-            [&](int t) { return (t / TPS < count) ? ((t % TPS) * VL) / Ls : -1; },
-            a.partial + (size_t)blockIdx.x * a.nrhs);
+        if (EPI == EPI_MOO && a.partial != nullptr) {
+            const int Ls = a.Ls;
+            block_rhs_reduce(
+                tile_norm, s_red, a.nrhs,
+                [&](int t) { return (t / TPS < G && t / TPS < count) ? ((t % TPS) * VL) / Ls : -1; },
+                a.partial + (size_t)tile * a.nrhs);
+        }
+        __syncthreads();   // buffer b is rewritten two tiles from now
     }
 }
 
@@ -287,15 +323,18 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     a.partial = c.partial;
     a.err = h->d_err;
     const int TPS = a.N5 / VL;
-    int threads = ts.T * TPS;
-    threads = (threads + 31) / 32 * 32;
-    if (threads > 256) {
-        set_error("hop: tile of %d sites x %d threads per site exceeds 256 threads", ts.T, TPS);
+    // site groups per CTA: as many as fit in 256 threads, at most T
+    int groups = 256 / TPS;
+    if (groups > ts.T) groups = ts.T;
+    if (groups < 1) {
+        set_error("hop: %d threads per site exceed 256", TPS);
         return DWF_ERR_ARG;
     }
-    const size_t smem = (size_t)ts.T * (144 * sizeof(SL) + 32) + 16 + (size_t)threads * 8;
+    int threads = (groups * TPS + 31) / 32 * 32;
+    const size_t smem = 2 * (size_t)ts.T * (144 * sizeof(SL) + 32) + 16 + (size_t)threads * 8;
     const int nt = ts.ntiles[p];
     if (nt == 0) return DWF_OK;
+    a.ntiles = nt;
     void (*kern)(const HopArgs);
     const bool moo = c.xmoo != nullptr;
     if (c.dagger)
@@ -304,18 +343,63 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     else
         kern = moo ? k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO>
                    : k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN>;
-    if (smem > 48 * 1024) DWF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<nt, threads, smem, s>>>(a);
+    if (smem > kHopMaxSmem) {
+        set_error("hop: tile of %d sites needs %zu bytes of shared memory", ts.T, smem);
+        return DWF_ERR_ARG;
+    }
+    // persistent grid: as many CTAs as are resident at once, at most one per tile
+    static std::map<std::pair<const void*, long>, int> occ_cache;
+    const auto key = std::make_pair((const void*)kern, (long)threads * 1000000L + (long)smem);
+    int per_sm = 0;
+    auto it = occ_cache.find(key);
+    if (it == occ_cache.end()) {
+        DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        occ_cache[key] = per_sm;
+    } else {
+        per_sm = it->second;
+    }
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int grid = (per_sm > 0 ? per_sm : 1) * n_sm;
+    if (grid > nt) grid = nt;
+    kern<<<grid, threads, smem, s>>>(a);
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }
 
+// Raise the dynamic shared-memory limit of every hop instantiation once, so
+// that launches recorded into a CUDA graph never need a host-side call.
+template <class Sin, class Sout, class SL, class R, int VL>
+static cudaError_t hop_attr() {
+    cudaError_t e = cudaSuccess;
+    void (*k[4])(const HopArgs) = {k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN>,
+                                   k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO>,
+                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN>,
+                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO>};
+    for (auto f : k) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
+        if (r != cudaSuccess) e = r;
+    }
+    return e;
+}
+
+dwf_status init_hop_kernels() {
+    DWF_CUDA((hop_attr<double, double, double, double, 1>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 2>()));
+    DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2>()));
+    DWF_CUDA((hop_attr<bf16, float, bf16, float, 2>()));
+    DWF_CUDA((hop_attr<float, bf16, bf16, float, 2>()));
+    DWF_CUDA((hop_attr<float, float, bf16, float, 2>()));
+    return DWF_OK;
+}
+
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {
-    int T = c.T > 0 ? c.T : 16;
-    const int vl = c.prec_link == DWF_FP64 ? 1 : 2;
-    const int tps = h->p.Ls * c.nrhs / vl;
-    while (T > 1 && T * tps > 256) T /= 2;     // at most 256 threads per CTA
-    const TileSet& ts = get_tiles(h, T);
+    const TileSet& ts = get_tiles(h, c.T > 0 ? c.T : 16);
     if (c.prec_link == DWF_FP64) {
         if (c.prec_in != DWF_FP64 || c.prec_out != DWF_FP64) return DWF_ERR_UNSUPPORTED;
         return launch_t<double, double, double, double, 1>(h, c, ts, s);

@@ -9,6 +9,7 @@
 //   L_BMINV  out = scale (b5 + c5 S5)(d + e S5)^-1 in          (commuting factors)
 //   L_POST   out = (d + e S5) in + scale (b5 + c5 S5) in2      (tail of M_pc^+)
 //            optionally fused with the CG update x += alpha p, r -= alpha out.
+//   L_PB     p = r + beta p (CG direction update), out = scale (b5 + c5 S5) p
 //
 // Per chirality S5 is a cyclic shift with a -mf twist (S_- on P_+, S_+ on
 // P_-, swapped for the adjoint), and (d + e S_-)^-1 has the closed form
@@ -103,141 +104,231 @@ __device__ __forceinline__ void minv5(const R* xr, const R* xi, R* yr, R* yi, in
     }
 }
 
-template <class S, class R, int LSM>
-__device__ __forceinline__ void load_row(const S* p, R* xr, R* xi, int Ls) {
-#pragma unroll
-    for (int s = 0; s < LSM; s += 2)
-        if (s < Ls) load_lanes<S, 2, R>(p + 2 * s, xr + s, xi + s);
-}
-
-template <class S, class R, int LSM>
-__device__ __forceinline__ void store_row(S* p, const R* xr, const R* xi, int Ls) {
-#pragma unroll
-    for (int s = 0; s < LSM; s += 2)
-        if (s < Ls) store_lanes<S, 2, R>(p + 2 * s, xr + s, xi + s);
-}
-
+// One pass over a tile, in blocks of RB = blockDim rows:
+//   1. coalesced vector loads of the block's rows (and of a second input)
+//      into shared memory, planes re/im with row stride Ls + 1;
+//   2. one thread per row applies the s-coupled operator in registers and
+//      writes the row back;
+//   3. coalesced epilogue: store, or the fused CG update of the vectors;
+//   4. per-row |.|^2 for the deterministic per-(tile, rhs) partial sums.
+// L_PB (the CG direction update fused with the next pre-op) does
+// p = r + beta p in step 1 (p: cg_p, read and written; r: in2; beta: alpha
+// array) and out = scale (b5 + c5 S5) p in step 2.
 template <class Sin, class Sin2, class Sout, class Svec, class R, int LSM>
 __global__ void __launch_bounds__(512) k_local(const LocalArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[512];
-    const int4 tl = a.tiles[blockIdx.x];
-    const int begin = tl.y, count = tl.z;
     const int Ls = a.Ls, nrhs = a.nrhs;
-    const int rows = count * 12 * nrhs;
+    const int RB = blockDim.x;
+    const int stride = Ls + 1;
+    R* Are = reinterpret_cast<R*>(smem_raw);
+    R* Aim = Are + RB * stride;
+    R* Bre = Aim + RB * stride;
+    R* Bim = Bre + RB * stride;
+    const int4 tl = a.tiles[blockIdx.x];
+    const int rows_total = tl.z * 12 * nrhs;
+    const int64_t tile_base = (int64_t)tl.y * 12 * nrhs * Ls;   // complex offset
+    const bool two = a.op == L_POST;
+    const bool cg = a.cg_r != nullptr;
+    const bool pb = a.op == L_PB;
     const R mf = (R)a.mf, b5 = (R)a.b5, c5 = (R)a.c5, d = (R)a.d, e = (R)a.e;
     const R sc = (R)a.scale;
-    double nrm_tot = 0.0;
-    // rows are assigned so that one thread always handles the same rhs
-    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-        const int r = row % nrhs;
-        const int c = (row / nrhs) % 12;
-        const int64_t base = ((int64_t)begin * 12 * nrhs + row) * Ls * 2;   // reals
-        const bool upper = c < 6;
-        // chirality of the shift: non-adjoint P_+ (upper) sees S_-
-        const bool down = (upper != (a.dagger != 0));
-        R xr[LSM], xi[LSM], yr[LSM], yi[LSM], tr[LSM], ti[LSM];
-        load_row<Sin, R, LSM>(reinterpret_cast<const Sin*>(a.in) + base, xr, xi, Ls);
-        switch (a.op) {
-            case L_B:
-            case L_MOOEE: {
-                const R c0 = a.op == L_B ? b5 : d;
-                const R c1 = a.op == L_B ? c5 : e;
-                shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
-#pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) {
-                        yr[s] = sc * (c0 * xr[s] + c1 * tr[s]);
-                        yi[s] = sc * (c0 * xi[s] + c1 * ti[s]);
-                    }
-                break;
+    double nrm = 0.0;
+    for (int rb0 = 0; rb0 < rows_total; rb0 += RB) {
+        const int nrows = min(RB, rows_total - rb0);
+        const int npair = nrows * Ls / 2;
+        const int64_t base = tile_base + (int64_t)rb0 * Ls;
+        // 1. loads
+        for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+            const int c0 = 2 * i;
+            const int row = c0 / Ls, s = c0 - row * Ls;
+            R xr[2], xi[2];
+            if (pb) {
+                const int sys = tl.x * nrhs + (rb0 + row) % nrhs;
+                Svec* pp = reinterpret_cast<Svec*>(const_cast<void*>(a.cg_p)) + 2 * (base + c0);
+                load_lanes<Svec, 2, R>(pp, xr, xi);
+                if (a.run == nullptr || a.run[sys] != 0) {
+                    R rr[2], ri[2];   // r is the second input of L_PB
+                    load_lanes<Sin2, 2, R>(reinterpret_cast<const Sin2*>(a.in2) + 2 * (base + c0), rr, ri);
+                    const R beta = (R)a.alpha[sys];
+                    xr[0] = rr[0] + beta * xr[0]; xi[0] = ri[0] + beta * xi[0];
+                    xr[1] = rr[1] + beta * xr[1]; xi[1] = ri[1] + beta * xi[1];
+                    store_lanes<Svec, 2, R>(pp, xr, xi);
+                }
+            } else {
+                load_lanes<Sin, 2, R>(reinterpret_cast<const Sin*>(a.in) + 2 * (base + c0), xr, xi);
             }
-            case L_MINV:
-            case L_BMINV: {
-                minv5<R, LSM>(xr, xi, tr, ti, Ls, down, mf, (R)a.a, e, (R)a.inv_d, (R)a.inv_den);
-                if (a.op == L_MINV) {
+            Are[row * stride + s] = xr[0]; Are[row * stride + s + 1] = xr[1];
+            Aim[row * stride + s] = xi[0]; Aim[row * stride + s + 1] = xi[1];
+            if (two) {
+                load_lanes<Sin2, 2, R>(reinterpret_cast<const Sin2*>(a.in2) + 2 * (base + c0), xr, xi);
+                Bre[row * stride + s] = xr[0]; Bre[row * stride + s + 1] = xr[1];
+                Bim[row * stride + s] = xi[0]; Bim[row * stride + s + 1] = xi[1];
+            }
+        }
+        __syncthreads();
+        // 2. one row per thread
+        if ((int)threadIdx.x < nrows) {
+            const int row = threadIdx.x;
+            const int c = ((rb0 + row) / nrhs) % 12;
+            // chirality of the shift: non-adjoint P_+ (upper spins) sees S_-
+            const bool down = ((c < 6) != (a.dagger != 0));
+            R xr[LSM], xi[LSM], yr[LSM], yi[LSM], tr[LSM], ti[LSM];
 #pragma unroll
-                    for (int s = 0; s < LSM; ++s)
-                        if (s < Ls) { yr[s] = sc * tr[s]; yi[s] = sc * ti[s]; }
-                } else {
-                    shift5<R, LSM>(tr, ti, xr, xi, Ls, down, mf);
+            for (int s = 0; s < LSM; ++s)
+                if (s < Ls) { xr[s] = Are[row * stride + s]; xi[s] = Aim[row * stride + s]; }
+            switch (a.op) {
+                case L_B:
+                case L_PB:
+                case L_MOOEE: {
+                    const R c0 = a.op == L_MOOEE ? d : b5;
+                    const R c1 = a.op == L_MOOEE ? e : c5;
+                    shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
 #pragma unroll
                     for (int s = 0; s < LSM; ++s)
                         if (s < Ls) {
-                            yr[s] = sc * (b5 * tr[s] + c5 * xr[s]);
-                            yi[s] = sc * (b5 * ti[s] + c5 * xi[s]);
+                            yr[s] = sc * (c0 * xr[s] + c1 * tr[s]);
+                            yi[s] = sc * (c0 * xi[s] + c1 * ti[s]);
                         }
+                    break;
                 }
-                break;
-            }
-            case L_POST: {
-                shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
+                case L_MINV:
+                case L_BMINV: {
+                    minv5<R, LSM>(xr, xi, tr, ti, Ls, down, mf, (R)a.a, e, (R)a.inv_d, (R)a.inv_den);
+                    if (a.op == L_MINV) {
 #pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) { yr[s] = d * xr[s] + e * tr[s]; yi[s] = d * xi[s] + e * ti[s]; }
-                load_row<Sin2, R, LSM>(reinterpret_cast<const Sin2*>(a.in2) + base, xr, xi, Ls);
-                shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
+                        for (int s = 0; s < LSM; ++s)
+                            if (s < Ls) { yr[s] = sc * tr[s]; yi[s] = sc * ti[s]; }
+                    } else {
+                        shift5<R, LSM>(tr, ti, xr, xi, Ls, down, mf);
 #pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) {
-                        yr[s] += sc * (b5 * xr[s] + c5 * tr[s]);
-                        yi[s] += sc * (b5 * xi[s] + c5 * ti[s]);
+                        for (int s = 0; s < LSM; ++s)
+                            if (s < Ls) {
+                                yr[s] = sc * (b5 * tr[s] + c5 * xr[s]);
+                                yi[s] = sc * (b5 * ti[s] + c5 * xi[s]);
+                            }
                     }
-                break;
-            }
-            default: {   // L_COPY
+                    break;
+                }
+                case L_POST: {
+                    shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
 #pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) { yr[s] = sc * xr[s]; yi[s] = sc * xi[s]; }
+                    for (int s = 0; s < LSM; ++s)
+                        if (s < Ls) { yr[s] = d * xr[s] + e * tr[s]; yi[s] = d * xi[s] + e * ti[s]; }
+#pragma unroll
+                    for (int s = 0; s < LSM; ++s)
+                        if (s < Ls) { xr[s] = Bre[row * stride + s]; xi[s] = Bim[row * stride + s]; }
+                    shift5<R, LSM>(xr, xi, tr, ti, Ls, down, mf);
+#pragma unroll
+                    for (int s = 0; s < LSM; ++s)
+                        if (s < Ls) {
+                            yr[s] += sc * (b5 * xr[s] + c5 * tr[s]);
+                            yi[s] += sc * (b5 * xi[s] + c5 * ti[s]);
+                        }
+                    break;
+                }
+                default: {   // L_COPY
+#pragma unroll
+                    for (int s = 0; s < LSM; ++s)
+                        if (s < Ls) { yr[s] = sc * xr[s]; yi[s] = sc * xi[s]; }
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < LSM; ++s)
+                if (s < Ls) { Are[row * stride + s] = yr[s]; Aim[row * stride + s] = yi[s]; }
+        }
+        __syncthreads();
+        // 3. epilogue
+        for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+            const int c0 = 2 * i;
+            const int row = c0 / Ls, s = c0 - row * Ls;
+            R yr[2] = {Are[row * stride + s], Are[row * stride + s + 1]};
+            R yi[2] = {Aim[row * stride + s], Aim[row * stride + s + 1]};
+            if (cg) {
+                const int sys = tl.x * nrhs + (rb0 + row) % nrhs;
+                Svec* rp = reinterpret_cast<Svec*>(a.cg_r) + 2 * (base + c0);
+                R rr[2], ri[2];
+                load_lanes<Svec, 2, R>(rp, rr, ri);
+                if (a.run == nullptr || a.run[sys] != 0) {
+                    const R alpha = (R)a.alpha[sys];
+                    Svec* xp = reinterpret_cast<Svec*>(a.cg_x) + 2 * (base + c0);
+                    R xr[2], xi[2], pr[2], pi[2];
+                    load_lanes<Svec, 2, R>(xp, xr, xi);
+                    load_lanes<Svec, 2, R>(reinterpret_cast<const Svec*>(a.cg_p) + 2 * (base + c0), pr, pi);
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        xr[v] += alpha * pr[v]; xi[v] += alpha * pi[v];
+                        rr[v] -= alpha * yr[v]; ri[v] -= alpha * yi[v];
+                    }
+                    store_lanes<Svec, 2, R>(xp, xr, xi);
+                    store_lanes<Svec, 2, R>(rp, rr, ri);
+                }
+                Bre[row * stride + s] = rr[0]; Bre[row * stride + s + 1] = rr[1];
+                Bim[row * stride + s] = ri[0]; Bim[row * stride + s + 1] = ri[1];
+            } else if (a.out != nullptr) {
+                store_lanes<Sout, 2, R>(reinterpret_cast<Sout*>(a.out) + 2 * (base + c0), yr, yi);
             }
         }
-        if (a.cg_r != nullptr) {
-            // fused CG step on the vectors: x += alpha p, r -= alpha y, |r|^2
-            const int sys = tl.x * nrhs + r;
-            const bool run = a.run == nullptr || a.run[sys] != 0;
-            const R alpha = (R)a.alpha[sys];
-            Svec* rp = reinterpret_cast<Svec*>(a.cg_r) + base;
-            load_row<Svec, R, LSM>(rp, tr, ti, Ls);
-            if (run) {
-                Svec* xp = reinterpret_cast<Svec*>(a.cg_x) + base;
-                const Svec* pp = reinterpret_cast<const Svec*>(a.cg_p) + base;
-                R pr[LSM], pi[LSM];
-                load_row<Svec, R, LSM>(pp, pr, pi, Ls);
-                load_row<Svec, R, LSM>(xp, xr, xi, Ls);
-#pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) {
-                        xr[s] += alpha * pr[s]; xi[s] += alpha * pi[s];
-                        tr[s] -= alpha * yr[s]; ti[s] -= alpha * yi[s];
-                    }
-                store_row<Svec, R, LSM>(xp, xr, xi, Ls);
-                store_row<Svec, R, LSM>(rp, tr, ti, Ls);
-            }
-            if (a.partial) {
-                double nn = 0.0;
-#pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) nn += (double)tr[s] * tr[s] + (double)ti[s] * ti[s];
-                nrm_tot += nn;
-            }
-        } else {
-            if (a.out != nullptr)
-                store_row<Sout, R, LSM>(reinterpret_cast<Sout*>(a.out) + base, yr, yi, Ls);
-            if (a.partial) {
-                double nn = 0.0;
-#pragma unroll
-                for (int s = 0; s < LSM; ++s)
-                    if (s < Ls) nn += (double)yr[s] * yr[s] + (double)yi[s] * yi[s];
-                nrm_tot += nn;
+        if (a.partial) {
+            __syncthreads();
+            // 4. per-row |.|^2 (of the updated residual for the CG step)
+            if ((int)threadIdx.x < nrows) {
+                const R* pr = cg ? Bre : Are;
+                const R* pi = cg ? Bim : Aim;
+                R acc = 0;
+                for (int s = 0; s < Ls; ++s) {
+                    const R u = pr[threadIdx.x * stride + s], v = pi[threadIdx.x * stride + s];
+                    acc += u * u + v * v;
+                }
+                nrm += (double)acc;
             }
         }
+        __syncthreads();
     }
     if (a.partial) {
-        // blockDim.x is a multiple of nrhs, so a thread's rows share one rhs
+        // blockDim.x is a multiple of nrhs: thread t's rows all have rhs t % nrhs
         const int nr = nrhs;
-        block_rhs_reduce(nrm_tot, s_red, nrhs,
-                         [&](int t) { return (t < rows) ? t % nr : -1; },
+        block_rhs_reduce(nrm, s_red, nrhs, [&](int t) { return t % nr; },
                          a.partial + (size_t)blockIdx.x * nrhs);
     }
+}
+
+template <class R>
+static int local_threads(int nrhs) {
+    int l = 32;
+    while (l % nrhs) l += 32;                  // lcm(32, nrhs)
+    if (l > 512) return -1;
+    const int target = sizeof(R) == 8 ? 128 : 256;
+    return l >= target ? l : l * (target / l);
+}
+
+template <class R>
+static size_t local_smem(int threads, int Ls) {
+    return (size_t)4 * threads * (Ls + 1) * sizeof(R);
+}
+
+template <class Sin, class Sin2, class Sout, class Svec, class R, int LSM>
+static cudaError_t local_attr() {
+    return cudaFuncSetAttribute(k_local<Sin, Sin2, Sout, Svec, R, LSM>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <class Sin, class Sin2, class Sout, class Svec, class R>
+static cudaError_t local_attr_all() {
+    cudaError_t e1 = local_attr<Sin, Sin2, Sout, Svec, R, 8>();
+    cudaError_t e2 = local_attr<Sin, Sin2, Sout, Svec, R, 16>();
+    cudaError_t e3 = local_attr<Sin, Sin2, Sout, Svec, R, 32>();
+    return e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+}
+
+dwf_status init_local_kernels() {
+    DWF_CUDA((local_attr_all<double, double, double, double, double>()));
+    DWF_CUDA((local_attr_all<float, float, float, float, float>()));
+    DWF_CUDA((local_attr_all<float, float, bf16, float, float>()));
+    DWF_CUDA((local_attr_all<bf16, bf16, bf16, float, float>()));
+    DWF_CUDA((local_attr_all<bf16, bf16, float, float, float>()));
+    DWF_CUDA((local_attr_all<float, bf16, float, float, float>()));
+    return DWF_OK;
 }
 
 template <class Sin, class Sin2, class Sout, class Svec, class R>
@@ -259,21 +350,24 @@ static dwf_status launch_lt(dwf_handle* h, const LocalCall& c, const TileSet& ts
     a.alpha = c.alpha; a.run = c.run; a.partial = c.partial;
     const int nt = ts.ntiles[c.parity];
     if (nt == 0) return DWF_OK;
-    // threads: a multiple of nrhs (so every thread keeps one rhs) and of 32
-    int l = 32;
-    while (l % c.nrhs) l += 32;              // lcm(32, nrhs)
-    if (l > 512) {
+    const int threads = local_threads<R>(c.nrhs);
+    if (threads < 0) {
         set_error("local: lcm(32, nrhs=%d) exceeds 512 threads", c.nrhs);
         return DWF_ERR_UNSUPPORTED;
     }
-    const int threads = l * (256 / l > 1 ? 256 / l : 1);
     const int Ls = h->p.Ls;
+    const size_t smem = local_smem<R>(threads, Ls);
+    if (smem > 200 * 1024) {
+        set_error("local: %zu bytes of shared memory for nrhs=%d, Ls=%d", smem, c.nrhs, Ls);
+        return DWF_ERR_UNSUPPORTED;
+    }
     if (Ls <= 8)
-        k_local<Sin, Sin2, Sout, Svec, R, 8><<<nt, threads, 0, s>>>(a);
+        k_local<Sin, Sin2, Sout, Svec, R, 8><<<nt, threads, smem, s>>>(a);
     else if (Ls <= 16)
-        k_local<Sin, Sin2, Sout, Svec, R, 16><<<nt, threads, 0, s>>>(a);
+        k_local<Sin, Sin2, Sout, Svec, R, 16><<<nt, threads, smem, s>>>(a);
     else
-        k_local<Sin, Sin2, Sout, Svec, R, 32><<<nt, threads, 0, s>>>(a);
+        k_local<Sin, Sin2, Sout, Svec, R, 32><<<nt, threads, smem, s>>>(a);
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
 }
@@ -286,7 +380,7 @@ dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s) {
         if (pi != DWF_FP64 || po != DWF_FP64 || p2 != DWF_FP64) return DWF_ERR_UNSUPPORTED;
         return launch_lt<double, double, double, double, double>(h, c, ts, s);
     }
-    // FP32 arithmetic; FP32 vectors for the fused CG update
+    // FP32 arithmetic; FP32 vectors for the fused CG updates
     if (pi == DWF_FP32 && p2 == DWF_FP32 && po == DWF_FP32)
         return launch_lt<float, float, float, float, float>(h, c, ts, s);
     if (pi == DWF_FP32 && p2 == DWF_FP32 && po == DWF_BF16)

@@ -9,6 +9,9 @@
 // (the bracketed site-local factors commute: per chirality both are functions
 // of the same twisted shift).  Shamir (c5 = 0) skips the (b5 + c5 S5) passes
 // and folds b5 into the hop scale.
+#include <algorithm>
+#include <vector>
+
 #include "dev_common.cuh"
 #include "dwf_internal.cuh"
 
@@ -20,10 +23,58 @@ namespace dwf {
 int tile_for(dwf_handle* h, int nrhs) {
     auto it = h->tuned_T.find(nrhs);
     if (it != h->tuned_T.end()) return it->second;
-    const int n5 = h->p.Ls * nrhs;
-    int T = 16;
-    while (T > 1 && T * n5 > 256) T /= 2;
-    return T;
+    return 32;
+}
+
+// Autotuner: time the bare hop of precision `prec` with nrhs right-hand
+// sides for each candidate tile size (CUDA events, median of 7 launches on a
+// private stream, scratch fields of the handle) and keep the fastest for
+// every kernel chain with this nrhs.
+dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
+    const int cands[] = {8, 16, 32, 64, 128};
+    cudaStream_t s;
+    DWF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const size_t bytes = cb_elems(h, 1, nrhs) * 2 * prec_size(prec);
+    cudaMemsetAsync(h->d_tmp2, 0, bytes, s);
+    float best_ms = 1e30f;
+    int best_T = tile_for(h, nrhs);
+    dwf_status st = DWF_OK;
+    for (int T : cands) {
+        const size_t smem = 2 * (size_t)T * (144 * prec_size(prec) + 32) + 16 + 256 * 8;
+        if (smem > (size_t)kHopMaxSmem) continue;   // double-buffered links + reduction scratch
+        HopCall c{};
+        c.in = h->d_tmp2;
+        c.out = h->d_tmp;
+        c.out_parity = 0;
+        c.prec_link = c.prec_in = c.prec_out = prec;
+        c.nrhs = nrhs;
+        c.scale = 1.0;
+        c.T = T;
+        std::vector<float> ts;
+        for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = launch_hop(h, c, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep >= 2) ts.push_back(ms);
+        }
+        if (st != DWF_OK) break;
+        std::sort(ts.begin(), ts.end());
+        const float med = ts[ts.size() / 2];
+        if (med < best_ms) { best_ms = med; best_T = T; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (st != DWF_OK) return st;
+    h->tuned_T[nrhs] = best_T;
+    if (best) *best = best_T;
+    return DWF_OK;
 }
 
 static int tileT(dwf_handle* h, int, dwf_prec, int nrhs) { return tile_for(h, nrhs); }
@@ -135,6 +186,16 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
         c.prec_vec = pv;
     }
     return launch_local(h, c, s);
+}
+
+// M_pc p when t1 = (b5 + c5 S5) p has already been formed (by the fused CG
+// direction update): out = M_oo p - (1/4) Dh_oe (b5 + c5 S5) M_ee^-1 Dh_eo t1.
+dwf_status op_mpc_pre(dwf_handle* h, void* out, const void* p, const void* t1, dwf_prec pv,
+                      dwf_prec po, int nrhs, void* tmpA, void* tmpB, double* partial,
+                      cudaStream_t s) {
+    DWF_TRY(op_hop(h, tmpB, t1, 0, 0, po, po, po, nrhs, 1.0, nullptr, nullptr, s));
+    DWF_TRY(op_local(h, L_BMINV, tmpA, tmpB, nullptr, 0, 0, po, po, po, nrhs, 1.0, nullptr, s));
+    return op_hop(h, out, tmpA, 1, 0, po, po, pv, nrhs, -0.25, p, partial, s);
 }
 
 // Full operator on full fields (both parities): D or D^+.

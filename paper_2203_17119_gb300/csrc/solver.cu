@@ -26,6 +26,8 @@
 // `check_every` iterations are replayed as one CUDA graph between host polls.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "dev_common.cuh"
@@ -78,7 +80,11 @@ __global__ void k_beta(SysView v, double delta) {
     v.dbl(S_BETA)[i] = rrn / rr;
     v.dbl(S_RR)[i] = rrn;
     const double nr = sqrt(rrn);
-    if (nr <= v.dbl(S_TARGET)[i] || (delta > 0.0 && nr <= delta * v.dbl(S_MAXR)[i]))
+    // FP64 update when the residual has dropped by delta, reached the target,
+    // or grown far beyond its value at the last update (a diverging
+    // low-precision recurrence)
+    if (nr <= v.dbl(S_TARGET)[i] || (delta > 0.0 && nr <= delta * v.dbl(S_MAXR)[i]) ||
+        nr > 1e3 * v.dbl(S_MAXR)[i])
         v.flg(F_NEED)[i] = 1;   // frozen by the next k_alpha until the FP64 update
 }
 
@@ -132,9 +138,11 @@ static dwf_status get_ws(dwf_handle* h, dwf_prec inner, int nrhs, SolverWS** out
     DWF_TRY(ws_alloc(&w.t, no * sv));
     DWF_TRY(ws_alloc(&w.tmp1, nm * so));
     DWF_TRY(ws_alloc(&w.tmp2, nm * so));
-    const TileSet& ts = get_tiles(h, tile_for(h, nrhs));
-    const int ntmax = ts.ntiles[0] > ts.ntiles[1] ? ts.ntiles[0] : ts.ntiles[1];
-    DWF_TRY(ws_alloc((void**)&w.part, (size_t)(ntmax + 1) * nrhs * sizeof(double)));
+    DWF_TRY(ws_alloc(&w.tmp3, no * so));   // t1 = (b5 + c5 S5) p, carried between iterations
+    // partials for any tile size the autotuner may pick (>= kMinTile sites)
+    const int64_t nsmax = h->nsite[0] > h->nsite[1] ? h->nsite[0] : h->nsite[1];
+    const size_t ntmax = (size_t)(nsmax / kMinTile + h->nbox + 1);
+    DWF_TRY(ws_alloc((void**)&w.part, ntmax * nrhs * sizeof(double)));
     w.nsys = h->nbox * nrhs;
     const size_t sys_bytes = (size_t)w.nsys * (S_NDBL * sizeof(double) + S_NINT * sizeof(int));
     DWF_TRY(ws_alloc((void**)&w.sys, sys_bytes));
@@ -166,10 +174,11 @@ static dwf_status cg_iteration(dwf_handle* h, SolverWS& w, SysView v, dwf_prec p
                                double delta, cudaStream_t s) {
     const int nrhs = w.nrhs;
     const int nb = (v.nsys + 127) / 128;
-    // t = M_pc p, |t|^2 = <p, A p>
-    DWF_TRY(op_mpc(h, w.t, w.p, 0, pv, po, nrhs, w.tmp1, w.tmp2, w.part, nullptr, s));
+    // t = M_pc p from t1 = (b5 + c5 S5) p, |t|^2 = <p, A p>
+    DWF_TRY(op_mpc_pre(h, w.t, w.p, w.tmp3, pv, po, nrhs, w.tmp1, w.tmp2, w.part, s));
     DWF_TRY(launch_reduce_sys(h, 1, w.part, nrhs, v.dbl(S_PAP), tile_for(h, nrhs), s));
     k_alpha<<<nb, 128, 0, s>>>(v);
+    note_launch();
     DWF_CUDA(cudaGetLastError());
     // A p = M_pc^+ t fused with x += alpha p, r -= alpha A p, |r|^2
     void* xv = (pv == DWF_FP64) ? (void*)w.x64 : w.x_lo;
@@ -177,10 +186,25 @@ static dwf_status cg_iteration(dwf_handle* h, SolverWS& w, SysView v, dwf_prec p
     DWF_TRY(op_mpc(h, nullptr, w.t, 1, pv, po, nrhs, w.tmp1, w.tmp2, w.part, &cg, s));
     DWF_TRY(launch_reduce_sys(h, 1, w.part, nrhs, v.dbl(S_TMP), tile_for(h, nrhs), s));
     k_beta<<<nb, 128, 0, s>>>(v, delta);
+    note_launch();
     DWF_CUDA(cudaGetLastError());
-    // p = r + beta p
-    return launch_axpby(h, 1, nrhs, nullptr, 1.0, w.r, pv, v.dbl(S_BETA), 0.0, w.p, pv,
-                        v.flg(F_RUN), tile_for(h, nrhs), s);
+    // p = r + beta p fused with the next iteration's t1 = (b5 + c5 S5) p
+    LocalCall c{};
+    c.op = L_PB;
+    c.out = w.tmp3;
+    c.in = w.p;
+    c.in2 = w.r;
+    c.parity = 1;
+    c.prec_in = pv;
+    c.prec_in2 = pv;
+    c.prec_out = po;
+    c.nrhs = nrhs;
+    c.scale = 1.0;
+    c.cg_p = w.p;
+    c.alpha = v.dbl(S_BETA);
+    c.run = v.flg(F_RUN);
+    c.T = tile_for(h, nrhs);
+    return launch_local(h, c, s);
 }
 
 dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
@@ -225,6 +249,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     DWF_TRY(norm2_sys(h, w, 0, be, DWF_FP64, v.dbl(S_TMP), s));
     DWF_TRY(norm2_sys(h, w, 1, bo, DWF_FP64, v.dbl(S_BN2), s));
     k_add2<<<(nsys + 127) / 128, 128, 0, s>>>(v.dbl(S_BN2), v.dbl(S_BN2), v.dbl(S_TMP), nsys);
+    note_launch();
     // b'_o = b_o - M_oe M_ee^-1 b_e
     DWF_TRY(op_local(h, L_MINV, w.t64a, be, nullptr, 0, 0, DWF_FP64, DWF_FP64, DWF_FP64, nrhs, 1.0, nullptr, s));
     DWF_TRY(op_dslash_eo(h, w.t64b, w.t64a, 1, 0, DWF_FP64, nrhs, w.t64d, s));
@@ -236,6 +261,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     const size_t sv = prec_size(pv) * 2;
     DWF_CUDA(cudaMemsetAsync(w.x_lo, 0, no * sv, s));
 
+    const bool trace = getenv("DWF_SOLVER_TRACE") != nullptr;
     // host-side per-system bookkeeping
     std::vector<int> active(nsys, 1), status(nsys, DWF_ERR_NOT_CONVERGED), reliable(nsys, 0);
     std::vector<double> bnorm(nsys), tres(nsys, 1.0), target(nsys);
@@ -252,7 +278,13 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
         if (pv == DWF_FP64) DWF_CUDA(cudaMemcpyAsync(w.r, w.t64d, no * 16, cudaMemcpyDeviceToDevice, s));
         else DWF_TRY(launch_convert(w.r, pv, w.t64d, DWF_FP64, no, s));
         DWF_TRY(norm2_sys(h, w, 1, w.r, pv, v.dbl(S_TMP), s));
-        if (first) DWF_CUDA(cudaMemcpyAsync(w.p, w.r, no * sv, cudaMemcpyDeviceToDevice, s));
+        // the search direction is kept across an update (Sleijpen & van der
+        // Vorst), except with the BF16 operator, whose ~1e-2 rounding breaks
+        // conjugacy: there the inner CG restarts from the new residual
+        if (first || po == DWF_BF16)
+            DWF_CUDA(cudaMemcpyAsync(w.p, w.r, no * sv, cudaMemcpyDeviceToDevice, s));
+        // t1 = (b5 + c5 S5) p for the next iteration's M_pc
+        DWF_TRY(op_local(h, L_B, w.tmp3, w.p, nullptr, 1, 0, pv, pv, po, nrhs, 1.0, nullptr, s));
         DWF_CUDA(cudaMemcpyAsync(hd, w.sys, sys_bytes, cudaMemcpyDeviceToHost, s));
         DWF_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < nsys; ++i) {
@@ -260,6 +292,9 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
             const double bn = bnorm[i] > 0 ? bnorm[i] : 1.0;
             const double tr = std::sqrt(HD(S_TR2, i)) / bn;
             const double rn = std::sqrt(HD(S_TMP, i));
+            if (trace && active[i])
+                fprintf(stderr, "[dwf cg] sys %d iters %d true_resid %.3e |r| %.3e target %.3e%s\n", i,
+                        HF(F_ITERS, i), tr, rn, HD(S_TARGET, i), HF(F_BAD, i) ? " BAD" : "");
             if (HF(F_BAD, i)) { status[i] = DWF_ERR_NAN; active[i] = 0; }
             if (!active[i]) { HF(F_RUN, i) = 0; HF(F_ACTIVE, i) = 0; continue; }
             tres[i] = tr;
@@ -291,20 +326,23 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     DWF_TRY(restart(true));
 
     // capture K iterations once per workspace
-    if (w.graph_exec == nullptr || w.graph_iters != K) {
+    if (w.graph_exec == nullptr || w.graph_iters != K || w.graph_T != tile_for(h, nrhs)) {
         if (w.graph_exec) { cudaGraphExecDestroy(w.graph_exec); w.graph_exec = nullptr; }
         if (w.graph) { cudaGraphDestroy(w.graph); w.graph = nullptr; }
         DWF_CUDA(cudaStreamSynchronize(s));
         DWF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        capture_begin();
         dwf_status st = DWF_OK;
         for (int k = 0; k < K && st == DWF_OK; ++k) st = cg_iteration(h, w, v, pv, po, delta, s);
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(s, &g);
+        w.graph_kernels = capture_end();
         if (st != DWF_OK) { if (g) cudaGraphDestroy(g); return st; }
         if (ce != cudaSuccess) { set_error("graph capture: %s", cudaGetErrorString(ce)); return DWF_ERR_CUDA; }
         w.graph = g;
         DWF_CUDA(cudaGraphInstantiate(&w.graph_exec, g, 0));
         w.graph_iters = K;
+        w.graph_T = tile_for(h, nrhs);
     }
 
     dwf_status result = DWF_OK;
@@ -314,6 +352,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
         for (int i = 0; i < nsys; ++i) any |= active[i] != 0;
         if (!any) break;
         DWF_CUDA(cudaGraphLaunch(w.graph_exec, s));
+        note_graph_launch(w.graph_kernels);
         DWF_CUDA(cudaMemcpyAsync(hd, w.sys, sys_bytes, cudaMemcpyDeviceToHost, s));
         DWF_CUDA(cudaStreamSynchronize(s));
         bool need = false, capped = false;
@@ -358,6 +397,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     DWF_TRY(norm2_sys(h, w, 0, w.full64a, DWF_FP64, v.dbl(S_TMP), s));
     DWF_TRY(norm2_sys(h, w, 1, w.full64a + 2 * ne, DWF_FP64, v.dbl(S_TR2), s));
     k_add2<<<(nsys + 127) / 128, 128, 0, s>>>(v.dbl(S_TR2), v.dbl(S_TR2), v.dbl(S_TMP), nsys);
+    note_launch();
     DWF_CUDA(cudaMemcpyAsync(hd, w.sys, sys_bytes, cudaMemcpyDeviceToHost, s));
     DWF_CUDA(cudaStreamSynchronize(s));
     int herr = 0;

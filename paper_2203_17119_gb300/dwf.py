@@ -83,6 +83,9 @@ def lib():
             "dwf_dirichlet_block": [vp, vp, vp, i, i, i, vp],
             "dwf_cgne_solve": [vp, vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_check_device": [vp],
+            "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
+            "dwf_launch_count": [C.POINTER(C.c_uint64)],
+            "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -92,6 +95,13 @@ def lib():
         L.dwf_last_error.argtypes = []
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    n = C.c_uint64()
+    _check(lib().dwf_launch_count(C.byref(n)))
+    return n.value
 
 
 def _check(st: int, allow=()):
@@ -202,6 +212,12 @@ class Handle:
                                    nrhs, _stream(stream)))
         return out
 
+    def hop(self, out, inp, out_parity, dagger=False, prec=FP64, nrhs=1, stream=None):
+        """Bare Wilson hop Dh (the dominant kernel)."""
+        _check(lib().dwf_hop(self._h, _ptr(out), _ptr(inp), out_parity, int(dagger), prec, nrhs,
+                             _stream(stream)))
+        return out
+
     def mooee(self, out, inp, parity, dagger=False, prec=FP64, nrhs=1, stream=None):
         _check(lib().dwf_mooee(self._h, _ptr(out), _ptr(inp), parity, int(dagger), prec, nrhs,
                                _stream(stream)))
@@ -239,6 +255,12 @@ class Handle:
         if not allow_fail:
             _check(rc)
         return [s.as_dict() for s in st], rc
+
+    def autotune(self, nrhs=1, prec=FP32):
+        """Pick the tile size (sites per CTA) for this nrhs by timing the hop."""
+        t = C.c_int()
+        _check(lib().dwf_autotune(self._h, nrhs, prec, C.byref(t)))
+        return t.value
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))
