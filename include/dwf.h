@@ -161,6 +161,21 @@ dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity,
 dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger,
                    dwf_prec prec, int nrhs, void* stream);
 
+/* Same result as dwf_mpc, for callers that may not allocate device memory
+ * where they apply the operator (a framework whose pool owns all device
+ * memory, a CUDA-graph capture in progress, a fixed-footprint embedding).
+ * The paper has no counterpart: it is a deployment convenience.  The two
+ * checkerboard temporaries come from a static device array of 2 x 32 MiB
+ * reserved on every GPU that loads the library (held until exit); requests
+ * needing more than 32 MiB per temporary fail with DWF_ERR_ARG, as do handles
+ * whose tile table for this nrhs was never built.  The call allocates
+ * nothing.  All calls on a device share the array (it keeps the last call's
+ * contents; nothing in it needs to start at zero), so calls that overlap on
+ * the GPU race: serialise them.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture. */
+dwf_status dwf_mpc_noalloc(dwf_handle* h, void* out, const void* in, int dagger,
+                           dwf_prec prec, int nrhs, void* stream);
 
 /* out = D in (full fields, both parities) for a whole-lattice handle, or
  * D_Omega in for a box handle; dagger: the adjoint. */

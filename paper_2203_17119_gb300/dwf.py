@@ -86,6 +86,7 @@ def lib():
             "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
             "dwf_launch_count": [C.POINTER(C.c_uint64)],
             "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
+            "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -231,6 +232,12 @@ class Handle:
     def mpc(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
         _check(lib().dwf_mpc(self._h, _ptr(out), _ptr(inp), int(dagger), prec, nrhs,
                              _stream(stream)))
+        return out
+
+    def mpc_noalloc(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
+        """M_pc with its temporaries in the library's static scratch array."""
+        _check(lib().dwf_mpc_noalloc(self._h, _ptr(out), _ptr(inp), int(dagger), prec, nrhs,
+                                     _stream(stream)))
         return out
 
     def apply_d(self, out, inp, dagger=False, prec=FP64, nrhs=1, stream=None):
