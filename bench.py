@@ -377,8 +377,74 @@ def run_hop(args):
                       "algorithmic_bytes": nbytes}))
 
 
+BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
+               ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
+               ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
+
+
+def run_batched(args):
+    """Six standalone Dirichlet boxes of uneven extents (8^4 ... 16^4) inside a
+    24^4 x Ls=16 Moebius lattice, nrhs right-hand sides each: the hop and a
+    mixed-precision CGNE of all 6 * nrhs systems in one persistent launch per
+    kernel (--batched NRHS [f32|bf16])."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    nrhs = int(args.batched[0])
+    prec = G.PREC[args.batched[1]] if len(args.batched) > 1 else G.FP32
+    dims, Ls = (24, 24, 24, 24), 16
+    rng = np.random.default_rng(1002)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
+    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), boxes=BATCH_BOXES, nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    del U
+    T = h.autotune(nrhs, prec)
+    vol = sum(int(np.prod(e)) for _, e in BATCH_BOXES)
+    # sources: per box and rhs, Gaussian on the box sites (canonical layout)
+    canon = torch.from_numpy(inputs.gaussian_source((vol * nrhs, 1, 1, 1), Ls, rng=rng).reshape(-1)).cuda()
+    b = h.pack(canon, nrhs)
+    del canon
+    word = {G.FP64: 8, G.FP32: 4, G.BF16: 2}[prec]
+    inp = b[h.nsite[0]:].to(G._DTYPE[prec]).contiguous()
+    out = h.empty_cb(0, nrhs, prec)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        h.hop(out, inp, 0, prec=prec, nrhs=nrhs)
+    ts = []
+    for _ in range(max(args.steps, 5)):
+        flush.fill_(1.0)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.hop(out, inp, 0, prec=prec, nrhs=nrhs)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(e))
+    ms = statistics.mean(ts)
+    sites = h.nsite[0] * Ls * nrhs     # output 5D sites of one hop (all boxes, all rhs)
+    nbytes = (48.0 + 144.0 / (Ls * nrhs)) * word * sites
+    del inp, out, flush
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    st, rc = h.cgne_solve(x, b, nrhs=nrhs, tol=1e-10, inner=prec, allow_fail=True)
+    torch.cuda.synchronize()
+    secs = time.time() - t0
+    print(json.dumps({
+        "workload": "6 Dirichlet boxes 8^4..16^4 in 24^4 x Ls=16, Moebius", "nrhs": nrhs,
+        "prec": args.batched[1] if len(args.batched) > 1 else "f32", "tile_sites": T,
+        "systems": len(st), "hop_ms": ms, "hop_tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
+        "hop_gbs": nbytes / (ms * 1e-3) / 1e9, "solve_seconds": secs,
+        "solve_status": rc, "max_iters": max(s["iters"] for s in st),
+        "max_true_resid": max(s["true_resid"] for s in st),
+        "seconds_per_system": secs / len(st)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--batched", nargs="+", metavar="ARG",
+                    help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--hop", nargs="+", metavar="ARG",
                     help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
     ap.add_argument("--no-autotune", action="store_true")
@@ -394,6 +460,9 @@ def main():
     rank = env_int("RANK", 0)
     if args.hop:
         run_hop(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
     if args.impl == "reference":
         if rank == 0:

@@ -99,6 +99,7 @@ typedef struct {
 } dwf_box;
 
 typedef struct dwf_handle dwf_handle;
+typedef struct dwf_nn dwf_nn;
 
 /* ------------------------------------------------------------- set-up */
 
@@ -200,6 +201,12 @@ typedef struct {
     dwf_prec inner_prec; /* DWF_FP64: plain FP64 CG; FP32/BF16: mixed precision  */
     double max_seconds;  /* wall-clock cap (0 = none)                            */
     int check_every;     /* iterations per captured CUDA graph (0 = default 8)   */
+    double* record_x;    /* CGNE, FP64 inner only: device buffer of record_max
+                            odd cb FP64 fields; the iterate x_o is copied into it
+                            every record_every iterations (a multiple of
+                            check_every), NULL = no recording                   */
+    int record_every;
+    int record_max;
 } dwf_solver_params;
 
 typedef struct {
@@ -209,6 +216,7 @@ typedef struct {
     int status;            /* dwf_status of this system                      */
     double true_resid;     /* |b - D x| / |b| recomputed in FP64 at the end  */
     double seconds;        /* wall time of the whole solve                   */
+    int recorded;          /* iterates written to record_x                   */
 } dwf_solver_stats;
 
 /* Solve D x = b (D_Omega x = b on a box handle) for every box and every
@@ -235,6 +243,46 @@ dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites)
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);
+
+/* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
+ * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
+ * itself stalls for Moebius DWF, whose Schur operator has the origin in its
+ * field of values); same b'_o / x_e / true-residual treatment as
+ * dwf_cgne_solve, stopping on |b - D x| / |b| <= tol.  If the true residual
+ * stops decreasing for two restarts (a poor K), the solve falls back to
+ * mixed-precision CGNE from the current x; stats.recorded = -1 marks that. 
+ * Inner vectors and operator FP32, solution and restarted residual FP64,
+ * FP64 inner products.  reliable_updates in stats counts restarts. */
+dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
+                         const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
+
+/* ------------------------------------------------ learned preconditioner
+ * K: two linear gauge-covariant parallel-transport layers (1 -> 16 -> 1
+ * channels).  Transports T_0 = 1, T_{1+mu} f(x) = U_mu(x) f(x+mu),
+ * T_{5+mu} f(x) = U_mu(x-mu)^+ f(x-mu), T_9 / T_10 = shift s+1 / s-1 with
+ * zero outside [0, Ls); layer: out^a = sum_{b,d} W[d][a][b] T_d in^b with
+ * complex 4x4 spin matrices W (gauge covariant: they commute with colour).
+ * K maps an odd cb field (embedded with zeros on even sites) to the odd
+ * part of the output.  Weights: W1[d][a][0][so][si] (11 x 16 x 16 complex)
+ * then W2[d][0][b][so][si], complex128 interleaved; applied in BF16,
+ * trained in FP32 with Adam (beta 0.9 / 0.999).  Created as the identity. */
+dwf_status dwf_nn_create(dwf_nn** K, int channels);
+dwf_status dwf_nn_destroy(dwf_nn* K);
+dwf_status dwf_nn_set_weights(dwf_nn* K, const double* w, size_t n_complex);
+dwf_status dwf_nn_get_weights(const dwf_nn* K, double* w, size_t n_complex);
+/* out = K in, odd cb FP32 fields with nrhs lanes (host workspace grows on
+ * first use per handle and nrhs). */
+dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs,
+                        void* stream);
+/* One Adam step on nrhs (r, e) pairs (odd cb FP32, one pair per lane,
+ * r = M_pc^+ M_pc e) of the loss  loss_kind 0: mean_k |K r_k - e_k|^2 / |e_k|^2;
+ * loss_kind 1: the energy-norm error mean_k <d_k, A d_k> / <e_k, r_k>,
+ * d_k = K r_k - e_k, A = M_pc^+ M_pc.  *loss receives the loss before the
+ * step.  Whole-lattice handles only. */
+dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const float* e, int nrhs,
+                             int loss_kind, double lr, double* loss, void* stream);
+/* Gradient of the last train step on handle h, layout of the weights. */
+dwf_status dwf_nn_last_grad(dwf_handle* h, double* g, size_t n_complex);
 
 /* Device error word (bounded waits that ran out); DWF_ERR_DEVICE if set. */
 dwf_status dwf_check_device(dwf_handle* h);

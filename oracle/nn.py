@@ -18,7 +18,11 @@ is the learned form added to the paper's local solves):
 * Network: 1 -> C -> 1 channels, two linear layers.  K acts on the odd
   checkerboard: the input is embedded with zeros on even sites and the
   output is restricted to odd sites.
-* Loss for a batch of pairs (r_k, e_k):  mean_k |K r_k - e_k|^2 / |e_k|^2.
+* Loss for a batch of pairs (r_k, e_k):  mean_k |K r_k - e_k|^2 / |e_k|^2,
+  or, given the operator A with A e_k = r_k, the error in the energy norm
+  mean_k <d_k, A d_k> / <e_k, r_k>, d_k = K r_k - e_k, whose gradient in
+  z = K r is 2 (A z - r) / <e, r>: it weighs each mode of the error by its
+  eigenvalue, the part a short-range K can represent.
   Gradients treat Re and Im of every weight as real parameters; with
   g = dL/dz (dL = Re<g, dz>) a layer z = W x back-propagates g_x = W^+ g and
   g_W = g x^+.
@@ -81,10 +85,11 @@ def apply_K(U, r, W1, W2):
     return parity_part(z, 1)
 
 
-def loss_and_grad(U, pairs, W1, W2):
-    """Mean relative squared error over (r, e) pairs and its gradients
-    (dL/dW1, dL/dW2) as complex arrays (real part / imaginary part of each
-    entry = derivative w.r.t. the real / imaginary part of the weight)."""
+def loss_and_grad(U, pairs, W1, W2, apply_A=None):
+    """Mean relative squared error over (r, e) pairs (or, with ``apply_A``,
+    the relative energy-norm error) and its gradients (dL/dW1, dL/dW2) as
+    complex arrays (real part / imaginary part of each entry = derivative
+    w.r.t. the real / imaginary part of the weight)."""
     nd, C = W1.shape[0], W1.shape[1]
     gW1 = np.zeros_like(W1)
     gW2 = np.zeros_like(W2)
@@ -99,10 +104,16 @@ def loss_and_grad(U, pairs, W1, W2):
         z = sum(np.einsum("ij,tzyxsja->tzyxsia", W2[d, 0, b], T1[d][b])
                 for d in range(nd) for b in range(C))
         z = parity_part(z, 1)
-        en = np.vdot(e, e).real
-        diff = z - e
-        L += np.vdot(diff, diff).real / en / n
-        gz = parity_part(2.0 * diff / en / n, 1)
+        if apply_A is None:
+            en = np.vdot(e, e).real
+            diff = z - e
+            L += np.vdot(diff, diff).real / en / n
+            gz = parity_part(2.0 * diff / en / n, 1)
+        else:
+            Az = apply_A(z)
+            er = np.vdot(e, r).real
+            L += (np.vdot(z, Az).real - 2 * np.vdot(z, r).real + er) / er / n
+            gz = parity_part(2.0 * (Az - r) / er / n, 1)
         # layer 2: z = sum_{d,b} W2[d,0,b] T_d phi1^b
         gphi1 = [np.zeros_like(x0) for _ in range(C)]
         for d in range(nd):
@@ -154,8 +165,9 @@ def identity_weights(C):
 
 
 def gcr(U, b_odd, p, apply_mpc, K=None, tol=1e-10, restart=16, maxiter=2000, bnorm=None):
-    """Right-preconditioned flexible GCR(restart) on M_pc x = b (odd sites):
-    z = K r, q = M_pc z, modified Gram-Schmidt of q against the previous q's
+    """Right-preconditioned flexible GCR(restart) on A x = b (odd sites),
+    A = ``apply_mpc`` (M_pc, or M_pc^+ M_pc for the normal equations):
+    z = K r, q = A z, modified Gram-Schmidt of q against the previous q's
     (the same combination applied to z), x += a z, r -= a q with
     a = <q, r> / <q, q>.  Returns (x, iterations)."""
     x = np.zeros_like(b_odd)

@@ -203,6 +203,16 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     return cgne_solve(h, x, b, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
+                         const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (x != nullptr && x == b) {
+        set_error("dwf_gcr_solve: x and b must not alias");
+        return DWF_ERR_ARG;
+    }
+    return gcr_solve(h, x, b, nrhs, K, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_check_device(dwf_handle* h) {
     DWF_TRY(check_handle(h));
     int e = 0;

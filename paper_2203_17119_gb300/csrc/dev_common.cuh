@@ -131,22 +131,33 @@ __device__ __forceinline__ void load_lanes(const S* __restrict__ p, R* re, R* im
     }
 }
 
-template <class S, int VL, class R>
+// Store VL consecutive complex numbers; CS = true uses the cache-streaming
+// hint (data written once and not re-read by this kernel: keep it from
+// evicting re-used lines in L2).
+template <class S, int VL, class R, bool CS = false>
 __device__ __forceinline__ void store_lanes(S* __restrict__ p, const R* re, const R* im) {
     if constexpr (std::is_same<S, double>::value) {
 #pragma unroll
-        for (int v = 0; v < VL; ++v)
-            reinterpret_cast<double2*>(p)[v] = make_double2((double)re[v], (double)im[v]);
+        for (int v = 0; v < VL; ++v) {
+            const double2 t = make_double2((double)re[v], (double)im[v]);
+            if (CS) __stcs(reinterpret_cast<double2*>(p) + v, t);
+            else reinterpret_cast<double2*>(p)[v] = t;
+        }
     } else if constexpr (std::is_same<S, float>::value) {
         if constexpr (VL % 2 == 0) {
 #pragma unroll
-            for (int v = 0; v < VL; v += 2)
-                reinterpret_cast<float4*>(p)[v / 2] =
-                    make_float4((float)re[v], (float)im[v], (float)re[v + 1], (float)im[v + 1]);
+            for (int v = 0; v < VL; v += 2) {
+                const float4 t = make_float4((float)re[v], (float)im[v], (float)re[v + 1], (float)im[v + 1]);
+                if (CS) __stcs(reinterpret_cast<float4*>(p) + v / 2, t);
+                else reinterpret_cast<float4*>(p)[v / 2] = t;
+            }
         } else {
 #pragma unroll
-            for (int v = 0; v < VL; ++v)
-                reinterpret_cast<float2*>(p)[v] = make_float2((float)re[v], (float)im[v]);
+            for (int v = 0; v < VL; ++v) {
+                const float2 t = make_float2((float)re[v], (float)im[v]);
+                if (CS) __stcs(reinterpret_cast<float2*>(p) + v, t);
+                else reinterpret_cast<float2*>(p)[v] = t;
+            }
         }
     } else {
         if constexpr (VL % 4 == 0) {
@@ -157,7 +168,8 @@ __device__ __forceinline__ void store_lanes(S* __restrict__ p, const R* re, cons
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     q[j] = __floats2bfloat162_rn((float)re[v + j], (float)im[v + j]);
-                reinterpret_cast<uint4*>(p)[v / 4] = t;
+                if (CS) __stcs(reinterpret_cast<uint4*>(p) + v / 4, t);
+                else reinterpret_cast<uint4*>(p)[v / 4] = t;
             }
         } else if constexpr (VL % 2 == 0) {
 #pragma unroll
@@ -167,7 +179,8 @@ __device__ __forceinline__ void store_lanes(S* __restrict__ p, const R* re, cons
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
                     q[j] = __floats2bfloat162_rn((float)re[v + j], (float)im[v + j]);
-                reinterpret_cast<uint2*>(p)[v / 2] = t;
+                if (CS) __stcs(reinterpret_cast<uint2*>(p) + v / 2, t);
+                else reinterpret_cast<uint2*>(p)[v / 2] = t;
             }
         } else {
 #pragma unroll

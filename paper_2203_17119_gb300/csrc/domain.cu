@@ -422,6 +422,8 @@ dwf_status destroy(dwf_handle* h) {
             cudaFree(kv.second.d_box_tile_begin[q]);
         }
     free_solver_ws(h);
+    free_nn_ws(h);
+    free_gcr_ws(h);
     delete h;
     return DWF_OK;
 }

@@ -129,6 +129,8 @@ struct dwf_handle {
     std::map<int, dwf::SolverWS> ws;   // keyed by prec * 64 + nrhs
     // autotuned tile sizes: nrhs -> sites per tile
     std::map<int, int> tuned_T;
+    // autotuned lanes per thread of the FP32 hop: nrhs -> VL
+    std::map<int, int> tuned_vl;
 };
 
 namespace dwf {
@@ -156,6 +158,7 @@ struct HopCall {
     double scale;            // out = [M_oo x +] scale * Dh in
     double* partial;         // EPI_MOO: per tile, per rhs |out|^2 (nullable)
     int T;                   // tile size (0 = tuned/default)
+    int VL = 0;              // lanes per thread (FP32 links: 1 or 2; 0 = default)
 };
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
 dwf_status init_hop_kernels();
@@ -233,6 +236,10 @@ dwf_status pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_prec 
 dwf_status unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf_prec prec,
                   cudaStream_t s);
 void free_solver_ws(dwf_handle* h);
+void free_nn_ws(dwf_handle* h);
+void free_gcr_ws(dwf_handle* h);
+dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
+                     const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user);
 dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
                       const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user);
 

@@ -145,7 +145,7 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
 // neighbour indices of the next tile are bulk-copied into the other half of
 // a double buffer while the current tile is computed.
 template <class Sin, class Sout, class SL, class R, int VL, bool DAG, int EPI>
-__global__ void __launch_bounds__(256, 2) k_hop(const HopArgs a) {
+__global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_hop(const HopArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int TPS = a.N5 / VL;
     const size_t link_bytes = (size_t)a.T * 144 * sizeof(SL);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256, 2) k_hop(const HopArgs a) {
                     orr[v] = sc * ar[c][v];
                     oi[v] = sc * ai[c][v];
                 }
-                store_lanes<Sout, VL, R>(out + (int64_t)c * N5 * 2, orr, oi);
+                store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
             }
         } else {
             // M_oo x = d x + e S5 x on this site's lanes; S5 (non-dagger):
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256, 2) k_hop(const HopArgs a) {
                     if (sizeof(R) == 8) nrm += (double)orr[v] * orr[v] + (double)oi[v] * oi[v];
                 }
                 if (sizeof(R) != 8) nrm += (double)part;
-                store_lanes<Sout, VL, R>(out + (int64_t)c * N5 * 2, orr, oi);
+                store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
             }
             tile_norm += nrm;
         }
@@ -391,6 +391,7 @@ static cudaError_t hop_attr() {
 dwf_status init_hop_kernels() {
     DWF_CUDA((hop_attr<double, double, double, double, 1>()));
     DWF_CUDA((hop_attr<float, float, float, float, 2>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 1>()));
     DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2>()));
     DWF_CUDA((hop_attr<bf16, float, bf16, float, 2>()));
     DWF_CUDA((hop_attr<float, bf16, bf16, float, 2>()));
@@ -406,6 +407,7 @@ dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {
     }
     if (c.prec_link == DWF_FP32) {
         if (c.prec_in != DWF_FP32 || c.prec_out != DWF_FP32) return DWF_ERR_UNSUPPORTED;
+        if (c.VL == 1) return launch_t<float, float, float, float, 1>(h, c, ts, s);
         return launch_t<float, float, float, float, 2>(h, c, ts, s);
     }
     // BF16 links: FP32 arithmetic, operands FP32 or BF16

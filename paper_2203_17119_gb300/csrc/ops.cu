@@ -41,8 +41,12 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     cudaMemsetAsync(h->d_tmp2, 0, bytes, s);
     float best_ms = 1e30f;
     int best_T = tile_for(h, nrhs);
+    int best_vl = 2;
     dwf_status st = DWF_OK;
+    const int nvl = prec == DWF_FP32 ? 2 : 1;
+    for (int vi = 0; vi < nvl; ++vi)
     for (int T : cands) {
+        const int vl = prec == DWF_FP32 ? (vi == 0 ? 2 : 1) : 0;
         const size_t smem = 2 * (size_t)T * (144 * prec_size(prec) + 32) + 16 + 256 * 8;
         if (smem > (size_t)kHopMaxSmem) continue;   // double-buffered links + reduction scratch
         HopCall c{};
@@ -53,6 +57,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         c.nrhs = nrhs;
         c.scale = 1.0;
         c.T = T;
+        c.VL = vl;
         std::vector<float> ts;
         for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
             cudaEventRecord(e0, s);
@@ -66,13 +71,14 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         if (st != DWF_OK) break;
         std::sort(ts.begin(), ts.end());
         const float med = ts[ts.size() / 2];
-        if (med < best_ms) { best_ms = med; best_T = T; }
+        if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
+    if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;
     if (best) *best = best_T;
     return DWF_OK;
 }
@@ -101,6 +107,10 @@ dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int 
     c.scale = scale;
     c.partial = partial;
     c.T = tileT(h, 0, link, nrhs);
+    if (link == DWF_FP32) {
+        auto it = h->tuned_vl.find(nrhs);
+        c.VL = it == h->tuned_vl.end() ? 2 : it->second;
+    }
     return launch_hop(h, c, s);
 }
 

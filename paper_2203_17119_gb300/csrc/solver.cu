@@ -347,12 +347,22 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
 
     dwf_status result = DWF_OK;
     bool timed_out = false;
+    // iterate recording (training data for the learned preconditioner)
+    const bool rec = sp->record_x != nullptr && pv == DWF_FP64 && sp->record_max > 0;
+    const int rec_batches = sp->record_every > K ? (sp->record_every + K - 1) / K : 1;
+    int recorded = 0, batch_no = 0;
     for (;;) {
         bool any = false;
         for (int i = 0; i < nsys; ++i) any |= active[i] != 0;
         if (!any) break;
         DWF_CUDA(cudaGraphLaunch(w.graph_exec, s));
         note_graph_launch(w.graph_kernels);
+        ++batch_no;
+        if (rec && recorded < sp->record_max && batch_no % rec_batches == 0) {
+            DWF_CUDA(cudaMemcpyAsync(sp->record_x + (size_t)recorded * no * 2, w.x64, no * 16,
+                                     cudaMemcpyDeviceToDevice, s));
+            ++recorded;
+        }
         DWF_CUDA(cudaMemcpyAsync(hd, w.sys, sys_bytes, cudaMemcpyDeviceToHost, s));
         DWF_CUDA(cudaStreamSynchronize(s));
         bool need = false, capped = false;
@@ -414,6 +424,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
             stats[i].status = status[i];
             stats[i].true_resid = tr;
             stats[i].seconds = secs;
+            stats[i].recorded = recorded;
         }
         if (status[i] != DWF_OK && result == DWF_OK) result = (dwf_status)status[i];
     }

@@ -44,12 +44,14 @@ class Box(C.Structure):
 class SolverParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("delta", C.c_double),
                 ("restart", C.c_int), ("use_x0", C.c_int), ("inner_prec", C.c_int),
-                ("max_seconds", C.c_double), ("check_every", C.c_int)]
+                ("max_seconds", C.c_double), ("check_every", C.c_int),
+                ("record_x", C.c_void_p), ("record_every", C.c_int), ("record_max", C.c_int)]
 
 
 class SolverStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("op_applies", C.c_int),
-                ("status", C.c_int), ("true_resid", C.c_double), ("seconds", C.c_double)]
+                ("status", C.c_int), ("true_resid", C.c_double), ("seconds", C.c_double),
+                ("recorded", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +89,14 @@ def lib():
             "dwf_launch_count": [C.POINTER(C.c_uint64)],
             "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
+            "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+            "dwf_nn_create": [C.POINTER(vp), i],
+            "dwf_nn_destroy": [vp],
+            "dwf_nn_set_weights": [vp, vp, C.c_size_t],
+            "dwf_nn_get_weights": [vp, vp, C.c_size_t],
+            "dwf_nn_apply": [vp, vp, vp, vp, i, vp],
+            "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
+            "dwf_nn_last_grad": [vp, vp, C.c_size_t],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -251,10 +261,17 @@ class Handle:
         return out
 
     def cgne_solve(self, x, b, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64, delta=0.1,
-                   use_x0=False, max_seconds=0.0, check_every=8, stream=None, allow_fail=False):
+                   use_x0=False, max_seconds=0.0, check_every=8, stream=None, allow_fail=False,
+                   record=None, record_every=8):
         """Solve D x = b (D_Omega x = b on a box handle); x, b full FP64
-        fields.  Returns the list of per-system stats dicts (box-major)."""
-        sp = SolverParams(tol, maxiter, delta, 16, int(use_x0), inner, max_seconds, check_every)
+        fields.  ``record``: optional FP64 device tensor of shape
+        (n, *cb_shape(1, nrhs)) receiving the odd iterates every
+        ``record_every`` iterations (FP64 inner solves).  Returns the list of
+        per-system stats dicts (box-major) and the status code."""
+        rp = C.c_void_p(record.data_ptr()) if record is not None else None
+        rmax = record.shape[0] if record is not None else 0
+        sp = SolverParams(tol, maxiter, delta, 16, int(use_x0), inner, max_seconds, check_every,
+                          rp, record_every, rmax)
         nsys = max(len(self.boxes), 1) * nrhs
         st = (SolverStats * nsys)()
         rc = lib().dwf_cgne_solve(self._h, _ptr(x), _ptr(b), nrhs, C.byref(sp), st,
@@ -269,5 +286,84 @@ class Handle:
         _check(lib().dwf_autotune(self._h, nrhs, prec, C.byref(t)))
         return t.value
 
+    def gcr_solve(self, x, b, K=None, nrhs=1, tol=1e-10, maxiter=100000, restart=16,
+                  max_seconds=0.0, stream=None, allow_fail=False):
+        """Flexible GCR with the learned preconditioner ``K`` (an ``NN``) or none."""
+        sp = SolverParams(tol, maxiter, 0.1, restart, 0, FP32, max_seconds, 8, None, 0, 0)
+        nsys = max(len(self.boxes), 1) * nrhs
+        st = (SolverStats * nsys)()
+        rc = lib().dwf_gcr_solve(self._h, _ptr(x), _ptr(b), nrhs, K._k if K is not None else None,
+                                 C.byref(sp), st, _stream(stream))
+        if not allow_fail:
+            _check(rc)
+        return [s.as_dict() for s in st], rc
+
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))
+
+
+class NN:
+    """The learned preconditioner K (``dwf_nn``): 1 -> 16 -> 1 channels."""
+
+    CHANNELS = 16
+
+    def __init__(self, channels=16):
+        k = C.c_void_p()
+        _check(lib().dwf_nn_create(C.byref(k), channels))
+        self._k = k
+        self.C = channels
+        self.nweights = 2 * 11 * channels * 16
+
+    def close(self):
+        if getattr(self, "_k", None):
+            lib().dwf_nn_destroy(self._k)
+            self._k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, W1, W2):
+        """W1 (11, C, 1, 4, 4) and W2 (11, 1, C, 4, 4) complex numpy arrays."""
+        import numpy as np
+        w = np.concatenate([np.ascontiguousarray(W1, dtype=np.complex128).reshape(-1),
+                            np.ascontiguousarray(W2, dtype=np.complex128).reshape(-1)])
+        _check(lib().dwf_nn_set_weights(self._k, w.ctypes.data_as(C.c_void_p), w.size))
+
+    def get_weights(self):
+        import numpy as np
+        w = np.zeros(self.nweights, dtype=np.complex128)
+        _check(lib().dwf_nn_get_weights(self._k, w.ctypes.data_as(C.c_void_p), w.size))
+        n1 = 11 * self.C * 16
+        return w[:n1].reshape(11, self.C, 1, 4, 4), w[n1:].reshape(11, 1, self.C, 4, 4)
+
+    def apply(self, h, out, inp, nrhs=1, stream=None):
+        _check(lib().dwf_nn_apply(self._k, h._h, _ptr(out), _ptr(inp), nrhs, _stream(stream)))
+        return out
+
+    def train_step(self, h, r, e, nrhs=1, lr=1e-3, energy=True, stream=None):
+        """One Adam step; ``energy`` selects the energy-norm loss (else the
+        relative error |K r - e|^2 / |e|^2)."""
+        loss = C.c_double()
+        _check(lib().dwf_nn_train_step(self._k, h._h, _ptr(r), _ptr(e), nrhs, int(energy), lr,
+                                       C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def last_grad(self, h):
+        import numpy as np
+        g = np.zeros(self.nweights, dtype=np.complex128)
+        _check(lib().dwf_nn_last_grad(h._h, g.ctypes.data_as(C.c_void_p), g.size))
+        n1 = 11 * self.C * 16
+        return g[:n1].reshape(11, self.C, 1, 4, 4), g[n1:].reshape(11, 1, self.C, 4, 4)
+
+    def save(self, path):
+        import numpy as np
+        W1, W2 = self.get_weights()
+        np.savez(path, W1=W1, W2=W2)
+
+    def load(self, path):
+        import numpy as np
+        z = np.load(path)
+        self.set_weights(z["W1"], z["W2"])

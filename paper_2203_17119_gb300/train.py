@@ -1,0 +1,160 @@
+"""Training and evaluation of the learned preconditioner K.
+
+Training pairs come from the solver itself: an FP64 CGNE solve records its
+odd iterates x_k; with the converged x* the pair is (r_k, e_k) with
+e_k = x* - x_k and r_k = M_pc^+ M_pc e_k (the residual of the normal
+equations that CGNE iterates on and that flexible GCR is preconditioned
+for), both divided by |e_k|.  The network is
+then fitted with Adam on the energy-norm error mean <d, A d> / <e, r>,
+d = K r - e, A = M_pc^+ M_pc (or on |K r - e|^2 / |e|^2), batches of pairs laid out
+as right-hand-side lanes of one field.  All arithmetic runs in the library
+(``dwf_cgne_solve``, ``dwf_mpc``, ``dwf_nn_train_step``); this module only
+moves tensors and loops.
+
+    python -m paper_2203_17119_gb300.train --train-dims 16 16 16 16 --train-Ls 12 \\
+        --sources 64 --iterates 64 --out K.npz --eval-dims 24 24 24 24 --eval-Ls 16
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from paper_2203_17119_gb300 import dwf as G
+from paper_2203_17119_gb300 import inputs
+
+
+def make_pairs(h, b_canon, n_iterates=64, record_every=4, tol=1e-10):
+    """Pairs from one FP64 solve of D x = b on a whole-lattice handle with
+    nrhs = 1.  Returns (r, e): FP32 odd cb fields, shape (n, *cb_shape(1))."""
+    b = h.pack(b_canon)
+    x = torch.zeros_like(b)
+    rec = torch.empty((n_iterates,) + h.cb_shape(1), dtype=torch.float64, device=b.device)
+    st, _ = h.cgne_solve(x, b, tol=tol, inner=G.FP64, record=rec, record_every=record_every,
+                         check_every=min(record_every, 8))
+    n = st[0]["recorded"]
+    xs = x[h.nsite[0]:].contiguous()
+    r_out, e_out = [], []
+    for k in range(n):
+        e = (xs - rec[k]).contiguous()
+        nrm = float(e.norm())
+        if nrm == 0.0:
+            continue
+        e /= nrm
+        t = torch.empty_like(e)
+        r = torch.empty_like(e)
+        h.mpc(t, e, prec=G.FP64)
+        h.mpc(r, t, dagger=True, prec=G.FP64)
+        r_out.append(r.float())
+        e_out.append(e.float())
+    torch.cuda.synchronize()
+    return torch.stack(r_out), torch.stack(e_out)
+
+
+def _batch(fields, idx):
+    """Stack single-rhs cb fields (n, site, 12, 1, Ls, 2) into lanes."""
+    return torch.cat([fields[i] for i in idx], dim=2).contiguous()
+
+
+def train(K, h, r, e, steps=100, batch=4, lr=1e-3, seed=0, energy=True):
+    """Adam steps on random minibatches of the pairs (r, e) (energy-norm loss
+    by default); returns the losses."""
+    g = np.random.default_rng(seed)
+    n = r.shape[0]
+    losses = []
+    for _ in range(steps):
+        idx = g.choice(n, size=batch, replace=n < batch)
+        losses.append(K.train_step(h, _batch(r, idx), _batch(e, idx), batch, lr=lr, energy=energy))
+    return losses
+
+
+def initial_network(d):
+    """K = 1/d^2 on the identity transport: the scale of the inverse of the
+    diagonal of M_pc^+ M_pc (M_oo = d + e S5, |e| << d), plus a small
+    symmetry-breaking start for the other channels."""
+    K = G.NN()
+    W1 = np.zeros((11, 16, 1, 4, 4), dtype=np.complex128)
+    W2 = np.zeros((11, 1, 16, 4, 4), dtype=np.complex128)
+    W1[0, 0, 0] = np.eye(4) / d ** 2
+    W2[0, 0, 0] = np.eye(4)
+    rng = np.random.default_rng(7)
+    W1[:, 1:] += 1e-3 * (rng.standard_normal(W1[:, 1:].shape) + 1j * rng.standard_normal(W1[:, 1:].shape))
+    W2[:, :, 1:] += 1e-3 * (rng.standard_normal(W2[:, :, 1:].shape)
+                            + 1j * rng.standard_normal(W2[:, :, 1:].shape))
+    K.set_weights(W1, W2)
+    return K
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 16])
+    ap.add_argument("--train-Ls", type=int, default=12)
+    ap.add_argument("--sources", type=int, default=64)
+    ap.add_argument("--iterates", type=int, default=64)
+    ap.add_argument("--steps-per-source", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--mf", type=float, default=0.005)
+    ap.add_argument("--out", default="K.npz")
+    ap.add_argument("--eval-dims", type=int, nargs=4, default=None)
+    ap.add_argument("--eval-Ls", type=int, default=16)
+    a = ap.parse_args()
+    act = G.Action(1.8, a.mf, 1.5, 0.5)
+    d = 1.5 * (4 - 1.8) + 1
+    dims = tuple(a.train_dims)
+    rng = np.random.default_rng(1004)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    Ut = torch.from_numpy(U.reshape(-1)).cuda()
+    h1 = G.Handle(dims, a.train_Ls, act, nrhs_max=1)
+    h1.set_gauge(Ut)
+    hb = G.Handle(dims, a.train_Ls, act, nrhs_max=a.batch)
+    hb.set_gauge(Ut)
+    K = initial_network(d)
+    t0 = time.time()
+    log = []
+    npairs = 0
+    for s in range(a.sources):
+        b = inputs.gaussian_source(dims, a.train_Ls, rng=rng)
+        r, e = make_pairs(h1, torch.from_numpy(b.reshape(-1)).cuda(), a.iterates,
+                          record_every=4)
+        npairs += r.shape[0]
+        losses = train(K, hb, r, e, steps=a.steps_per_source, batch=a.batch, lr=a.lr, seed=s)
+        log.append({"source": s, "pairs": int(r.shape[0]), "loss_first": losses[0],
+                    "loss_last": losses[-1], "t": time.time() - t0})
+        print(json.dumps(log[-1]), flush=True)
+        del r, e
+    K.save(a.out)
+    res = {"train_pairs": npairs, "train_seconds": time.time() - t0, "weights": a.out}
+    if a.eval_dims:
+        res["eval"] = evaluate(K, tuple(a.eval_dims), a.eval_Ls, act)
+    print(json.dumps(res), flush=True)
+
+
+def evaluate(K, dims, Ls, act, seed=1004):
+    """Time to 1e-10: GCR with K, GCR without K, mixed CG and FP64 CG."""
+    rng = np.random.default_rng(seed + 10)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    h = G.Handle(dims, Ls, act)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    b = h.pack(torch.from_numpy(inputs.gaussian_source(dims, Ls, rng=rng).reshape(-1)).cuda())
+    out = {}
+    for name, fn in (("gcr_K", lambda x: h.gcr_solve(x, b, K=K, tol=1e-10)),
+                     ("gcr", lambda x: h.gcr_solve(x, b, K=None, tol=1e-10)),
+                     ("cg_mixed_fp32", lambda x: h.cgne_solve(x, b, tol=1e-10, inner=G.FP32)),
+                     ("cg_fp64", lambda x: h.cgne_solve(x, b, tol=1e-10, inner=G.FP64))):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.time()
+        st, rc = fn(x)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.time() - t, "iters": st[0]["iters"],
+                     "true_resid": st[0]["true_resid"], "status": st[0]["status"]}
+    return out
+
+
+if __name__ == "__main__":
+    main()
