@@ -240,6 +240,12 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
  * tile_sites (nullable) receives the choice. */
 dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites);
 
+/* Manual counterpart of dwf_autotune: sites per tile (kMinTile = 4 .. 256,
+ * limited by the FP64 hop's shared memory) and lanes per thread of the FP32
+ * hop (1 or 2) for every later call with this nrhs.  Builds the tile table
+ * (allocates); DWF_ERR_ARG on values out of range. */
+dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_thread);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);
@@ -277,7 +283,8 @@ dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, i
 /* One Adam step on nrhs (r, e) pairs (odd cb FP32, one pair per lane,
  * r = M_pc^+ M_pc e) of the loss  loss_kind 0: mean_k |K r_k - e_k|^2 / |e_k|^2;
  * loss_kind 1: the energy-norm error mean_k <d_k, A d_k> / <e_k, r_k>,
- * d_k = K r_k - e_k, A = M_pc^+ M_pc.  *loss receives the loss before the
+ * d_k = K r_k - e_k, A = M_pc^+ M_pc; loss_kind 2: the A^2-norm error
+ * mean_k |A d_k|^2 / |r_k|^2 = |A K r_k - r_k|^2 / |r_k|^2.  *loss receives the loss before the
  * step.  Whole-lattice handles only. */
 dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const float* e, int nrhs,
                              int loss_kind, double lr, double* loss, void* stream);

@@ -22,7 +22,9 @@ is the learned form added to the paper's local solves):
   or, given the operator A with A e_k = r_k, the error in the energy norm
   mean_k <d_k, A d_k> / <e_k, r_k>, d_k = K r_k - e_k, whose gradient in
   z = K r is 2 (A z - r) / <e, r>: it weighs each mode of the error by its
-  eigenvalue, the part a short-range K can represent.
+  eigenvalue, the part a short-range K can represent; or in the A^2 norm,
+  |A (K r - e)|^2 / |A e|^2 = |A K r - r|^2 / |r|^2, the residual left by one
+  GCR step with z = K r.
   Gradients treat Re and Im of every weight as real parameters; with
   g = dL/dz (dL = Re<g, dz>) a layer z = W x back-propagates g_x = W^+ g and
   g_W = g x^+.
@@ -85,11 +87,13 @@ def apply_K(U, r, W1, W2):
     return parity_part(z, 1)
 
 
-def loss_and_grad(U, pairs, W1, W2, apply_A=None):
+def loss_and_grad(U, pairs, W1, W2, apply_A=None, kind=None):
     """Mean relative squared error over (r, e) pairs (or, with ``apply_A``,
     the relative energy-norm error) and its gradients (dL/dW1, dL/dW2) as
     complex arrays (real part / imaginary part of each entry = derivative
-    w.r.t. the real / imaginary part of the weight)."""
+    w.r.t. the real / imaginary part of the weight).  ``kind`` "a2" (with
+    ``apply_A``) measures the error in the A^2 norm instead:
+    |A (K r - e)|^2 / |A e|^2 = |A z - r|^2 / |r|^2, gradient 2 A (A z - r) / |r|^2."""
     nd, C = W1.shape[0], W1.shape[1]
     gW1 = np.zeros_like(W1)
     gW2 = np.zeros_like(W2)
@@ -109,6 +113,11 @@ def loss_and_grad(U, pairs, W1, W2, apply_A=None):
             diff = z - e
             L += np.vdot(diff, diff).real / en / n
             gz = parity_part(2.0 * diff / en / n, 1)
+        elif kind == "a2":
+            res = apply_A(z) - r
+            rr = np.vdot(r, r).real
+            L += np.vdot(res, res).real / rr / n
+            gz = parity_part(2.0 * apply_A(res) / rr / n, 1)
         else:
             Az = apply_A(z)
             er = np.vdot(e, r).real

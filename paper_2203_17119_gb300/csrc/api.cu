@@ -134,6 +134,25 @@ dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites)
     return autotune(h, nrhs, prec, tile_sites);
 }
 
+dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_thread) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max || tile_sites < kMinTile || tile_sites > 256 ||
+        (lanes_per_thread != 1 && lanes_per_thread != 2)) {
+        set_error("dwf_set_tile: nrhs in [1, nrhs_max], tile_sites in [%d, 256], lanes 1 or 2",
+                  kMinTile);
+        return DWF_ERR_ARG;
+    }
+    const size_t smem = 2 * (size_t)tile_sites * (144 * 8 + 32) + 16 + 256 * 8;
+    if (smem > (size_t)kHopMaxSmem) {
+        set_error("dwf_set_tile: %d sites per tile exceed the FP64 hop's shared memory", tile_sites);
+        return DWF_ERR_ARG;
+    }
+    h->tuned_T[nrhs] = tile_sites;
+    h->tuned_vl[nrhs] = lanes_per_thread;
+    get_tiles(h, tile_sites);
+    return DWF_OK;
+}
+
 dwf_status dwf_launch_count(uint64_t* n) {
     if (n == nullptr) {
         set_error("dwf_launch_count: null pointer");

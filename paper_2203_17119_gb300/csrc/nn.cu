@@ -660,6 +660,22 @@ dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const flo
             L += h2[k] / h1[k] / nrhs;
             coef[k] = 2.0 / (h1[k] * nrhs);
         }
+    } else if (loss_kind == 2) {
+        // A^2 norm: |A z - r|^2 / |r|^2, gradient 2 A (A z - r) / |r|^2, held in z
+        DWF_TRY(op_mpc(h, w.at, zo, 0, DWF_FP32, DWF_FP32, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
+        DWF_TRY(op_mpc(h, w.aw, w.at, 1, DWF_FP32, DWF_FP32, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
+        DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, -1.0, r, DWF_FP32, nullptr, 1.0, w.aw, DWF_FP32, nullptr, T, s));
+        DWF_TRY(dot(w.aw, w.aw, d1));
+        DWF_TRY(dot(r, r, d3));
+        DWF_CUDA(cudaMemcpyAsync(h1.data(), d1, nrhs * 8, cudaMemcpyDeviceToHost, s));
+        DWF_CUDA(cudaMemcpyAsync(h3.data(), d3, nrhs * 8, cudaMemcpyDeviceToHost, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < nrhs; ++k) {
+            L += h1[k] / h3[k] / nrhs;
+            coef[k] = 2.0 / (h3[k] * nrhs);
+        }
+        DWF_TRY(op_mpc(h, w.at, w.aw, 0, DWF_FP32, DWF_FP32, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
+        DWF_TRY(op_mpc(h, zo, w.at, 1, DWF_FP32, DWF_FP32, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
     } else {
         // energy norm of A = M_pc^+ M_pc: (<z,Az> - 2 Re<z,r> + <e,r>) / <e,r>,
         // gradient 2 (A z - r) / <e,r>, held in z

@@ -39,6 +39,10 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     cudaEventCreate(&e1);
     const size_t bytes = cb_elems(h, 1, nrhs) * 2 * prec_size(prec);
     cudaMemsetAsync(h->d_tmp2, 0, bytes, s);
+    // candidates are timed with L2 flushed (solves stream more than L2 holds)
+    const size_t flush_bytes = (size_t)256 << 20;
+    void* flush = nullptr;
+    DWF_CUDA(cudaMalloc(&flush, flush_bytes));
     float best_ms = 1e30f;
     int best_T = tile_for(h, nrhs);
     int best_vl = 2;
@@ -47,7 +51,9 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     for (int vi = 0; vi < nvl; ++vi)
     for (int T : cands) {
         const int vl = prec == DWF_FP32 ? (vi == 0 ? 2 : 1) : 0;
-        const size_t smem = 2 * (size_t)T * (144 * prec_size(prec) + 32) + 16 + 256 * 8;
+        // the tile table is shared by every precision of an operator chain
+        // (FP64 reliable updates included): size the check for FP64 links
+        const size_t smem = 2 * (size_t)T * (144 * 8 + 32) + 16 + 256 * 8;
         if (smem > (size_t)kHopMaxSmem) continue;   // double-buffered links + reduction scratch
         HopCall c{};
         c.in = h->d_tmp2;
@@ -60,6 +66,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         c.VL = vl;
         std::vector<float> ts;
         for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
+            cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
             st = launch_hop(h, c, s);
             cudaEventRecord(e1, s);
@@ -75,6 +82,8 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(flush);
     cudaStreamDestroy(s);
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;

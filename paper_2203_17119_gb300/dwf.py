@@ -88,6 +88,7 @@ def lib():
             "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
             "dwf_launch_count": [C.POINTER(C.c_uint64)],
             "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
+            "dwf_set_tile": [vp, i, i, i],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
@@ -298,6 +299,10 @@ class Handle:
             _check(rc)
         return [s.as_dict() for s in st], rc
 
+    def set_tile(self, nrhs=1, tile_sites=32, lanes_per_thread=2):
+        """Fix the tile size and FP32 hop lanes per thread for this nrhs."""
+        _check(lib().dwf_set_tile(self._h, nrhs, tile_sites, lanes_per_thread))
+
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))
 
@@ -343,11 +348,14 @@ class NN:
         _check(lib().dwf_nn_apply(self._k, h._h, _ptr(out), _ptr(inp), nrhs, _stream(stream)))
         return out
 
-    def train_step(self, h, r, e, nrhs=1, lr=1e-3, energy=True, stream=None):
-        """One Adam step; ``energy`` selects the energy-norm loss (else the
-        relative error |K r - e|^2 / |e|^2)."""
+    LOSS = {"error": 0, "energy": 1, "a2": 2}
+
+    def train_step(self, h, r, e, nrhs=1, lr=1e-3, energy=True, loss_kind=None, stream=None):
+        """One Adam step.  loss_kind: "error" |K r - e|^2/|e|^2, "energy"
+        (default; energy=False selects "error"), or "a2" |A K r - r|^2/|r|^2."""
+        kind = self.LOSS[loss_kind] if loss_kind else (1 if energy else 0)
         loss = C.c_double()
-        _check(lib().dwf_nn_train_step(self._k, h._h, _ptr(r), _ptr(e), nrhs, int(energy), lr,
+        _check(lib().dwf_nn_train_step(self._k, h._h, _ptr(r), _ptr(e), nrhs, kind, lr,
                                        C.byref(loss), _stream(stream)))
         return loss.value
 

@@ -60,15 +60,16 @@ def _batch(fields, idx):
     return torch.cat([fields[i] for i in idx], dim=2).contiguous()
 
 
-def train(K, h, r, e, steps=100, batch=4, lr=1e-3, seed=0, energy=True):
+def train(K, h, r, e, steps=100, batch=4, lr=1e-3, seed=0, energy=True, loss_kind=None):
     """Adam steps on random minibatches of the pairs (r, e) (energy-norm loss
-    by default); returns the losses."""
+    by default, see NN.train_step); returns the losses."""
     g = np.random.default_rng(seed)
     n = r.shape[0]
     losses = []
     for _ in range(steps):
         idx = g.choice(n, size=batch, replace=n < batch)
-        losses.append(K.train_step(h, _batch(r, idx), _batch(e, idx), batch, lr=lr, energy=energy))
+        losses.append(K.train_step(h, _batch(r, idx), _batch(e, idx), batch, lr=lr, energy=energy,
+                                   loss_kind=loss_kind))
     return losses
 
 
@@ -102,6 +103,7 @@ def main():
     ap.add_argument("--out", default="K.npz")
     ap.add_argument("--eval-dims", type=int, nargs=4, default=None)
     ap.add_argument("--eval-Ls", type=int, default=16)
+    ap.add_argument("--loss", default="a2", choices=["error", "energy", "a2"])
     a = ap.parse_args()
     act = G.Action(1.8, a.mf, 1.5, 0.5)
     d = 1.5 * (4 - 1.8) + 1
@@ -122,7 +124,8 @@ def main():
         r, e = make_pairs(h1, torch.from_numpy(b.reshape(-1)).cuda(), a.iterates,
                           record_every=4)
         npairs += r.shape[0]
-        losses = train(K, hb, r, e, steps=a.steps_per_source, batch=a.batch, lr=a.lr, seed=s)
+        losses = train(K, hb, r, e, steps=a.steps_per_source, batch=a.batch, lr=a.lr, seed=s,
+                       loss_kind=a.loss)
         log.append({"source": s, "pairs": int(r.shape[0]), "loss_first": losses[0],
                     "loss_last": losses[-1], "t": time.time() - t0})
         print(json.dumps(log[-1]), flush=True)

@@ -57,8 +57,8 @@ def odd_host(t, dims, Ls):
     return LY.from_cb(arr, dims, None, 1, Ls)[0]
 
 
-def test_forward_matches_oracle():
-    dims, Ls, nrhs = (4, 4, 2, 4), 6, 2
+@pytest.mark.parametrize("dims,Ls,nrhs", [((4, 4, 2, 4), 6, 2), ((4, 2, 2, 4), 16, 1)])
+def test_forward_matches_oracle(dims, Ls, nrhs):
     rng, U, h = setup(dims, Ls, nrhs, 11)
     W1, W2 = rand_weights(rng)
     K = G.NN()
@@ -85,7 +85,7 @@ def test_identity_network_is_identity():
     assert float((out - x).abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("energy", [False, True])
+@pytest.mark.parametrize("energy", [False, True, "a2"])
 def test_gradient_matches_oracle(energy):
     dims, Ls, nrhs = (4, 2, 2, 4), 4, 2
     rng, U, h = setup(dims, Ls, nrhs, 13)
@@ -98,10 +98,11 @@ def test_gradient_matches_oracle(energy):
         pairs = [(A(e), e) for e in es]
     else:
         pairs = [(O.parity_part(inputs.gaussian_source(dims, Ls, rng=rng), 1), e) for e in es]
+    kind = "a2" if energy == "a2" else ("energy" if energy else "error")
     loss = K.train_step(h, odd_gpu([p[0] for p in pairs], dims), odd_gpu([p[1] for p in pairs], dims),
-                        nrhs, lr=0.0, energy=energy)
+                        nrhs, lr=0.0, loss_kind=kind)
     g1, g2 = K.last_grad(h)
-    L, w1, w2 = N.loss_and_grad(U, pairs, W1, W2, A)
+    L, w1, w2 = N.loss_and_grad(U, pairs, W1, W2, A, "a2" if energy == "a2" else None)
     assert abs(loss - L) <= 1e-5 * abs(L)
     assert np.linalg.norm(g1 - w1) <= 2e-4 * np.linalg.norm(w1)
     assert np.linalg.norm(g2 - w2) <= 2e-4 * np.linalg.norm(w2)
@@ -129,8 +130,9 @@ def test_gcr_solve(use_k):
 def test_training_generalises_and_gcr_converges():
     """Pairs (r, e) from the iterates of FP64 CGNE solves; Adam on the
     energy-norm loss must lower the held-out loss of the 1/d^2-initialised
-    network by >= 10%, and GCR with the trained K must reach 1e-10 (by itself
-    or through its CG fallback), with the iteration counts reported."""
+    network by >= 30% (A^2-norm loss: the residual left by one GCR step), and
+    GCR with the trained K must reach 1e-10 (by itself or through its CG
+    fallback), with the iteration counts reported."""
     from paper_2203_17119_gb300 import train as TR
     dims, Ls, nrhs = (4, 4, 4, 8), 8, 4
     rng, U, h = setup(dims, Ls, nrhs, 15, kind="exp")
@@ -145,15 +147,16 @@ def test_training_generalises_and_gcr_converges():
     def held_out(K):
         n = (r_ho.shape[0] // nrhs) * nrhs
         return np.mean([K.train_step(h, TR._batch(r_ho, range(i, i + nrhs)),
-                                     TR._batch(e_ho, range(i, i + nrhs)), nrhs, lr=0.0)
+                                     TR._batch(e_ho, range(i, i + nrhs)), nrhs, lr=0.0,
+                                     loss_kind="a2")
                         for i in range(0, n, nrhs)])
 
     d = MOBIUS.d
     before = held_out(TR.initial_network(d))
     K = TR.initial_network(d)
-    TR.train(K, h, r_tr, e_tr, steps=200, batch=nrhs, lr=1e-3, seed=0)
+    TR.train(K, h, r_tr, e_tr, steps=200, batch=nrhs, lr=1e-3, seed=0, loss_kind="a2")
     after = held_out(K)
-    assert after < 0.9 * before, (before, after)
+    assert after < 0.7 * before, (before, after)
     b = inputs.gaussian_source(dims, Ls, rng=rng)
     bf = torch.view_as_real(torch.from_numpy(LY.to_full([[b]], dims, None))).cuda().contiguous()
     its = {}

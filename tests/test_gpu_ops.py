@@ -156,3 +156,43 @@ def test_pack_unpack_layout(case, prec):
     torch.cuda.synchronize()
     got = back.cpu().numpy().view(np.complex128).reshape(-1)
     assert LY.rel_l2(got, canon) <= TOL[prec]
+
+
+@pytest.mark.parametrize("tile,vl", [(4, 1), (8, 2), (48, 1), (64, 2)])
+def test_tile_and_lane_variants(tile, vl):
+    """Every (tile size, lanes per thread) choice the autotuner can make gives
+    the same operator: hop-based dslash_eo and M_pc in FP32 and FP64."""
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = _setup("mobius_boxes_odd_wrap")
+    h.set_tile(nrhs, tile, vl)
+    po = [[O.parity_part(f, 1) for f in row] for row in psi]
+    src = LY.to_cb(po, dims, boxes, 1)
+    want = LY.to_cb([[O.mpc_in(U, f, prm, masks[b]) for f in po[b]] for b in range(len(po))],
+                    dims, boxes, 1)
+    for prec in (G.FP64, G.FP32):
+        out = h.empty_cb(1, nrhs, prec)
+        h.mpc(out, _gpu(src, prec), False, prec, nrhs)
+        torch.cuda.synchronize()
+        assert LY.rel_l2(_host(out), want) <= TOL_MPC[prec], prec
+    want0 = LY.to_cb([[O.eo_block_in(U, f, prm, masks[b], 0) for f in psi[b]]
+                      for b in range(len(psi))], dims, boxes, 0)
+    out = h.empty_cb(0, nrhs, G.FP32)
+    h.dslash_eo(out, _gpu(LY.to_cb(psi, dims, boxes, 1), G.FP32), 0, False, G.FP32, nrhs)
+    torch.cuda.synchronize()
+    assert LY.rel_l2(_host(out), want0) <= TOL[G.FP32]
+
+
+def test_autotuned_solve_still_exact():
+    """After dwf_autotune (which may pick the one-lane FP32 hop), a mixed
+    solve still reaches 1e-10 by the oracle."""
+    dims, Ls = (4, 4, 4, 8), 8
+    rng = np.random.default_rng(31)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    b = inputs.gaussian_source(dims, Ls, rng=rng)
+    h = G.Handle(dims, Ls, G.Action(MOBIUS.M5, MOBIUS.mf, MOBIUS.b5, MOBIUS.c5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.autotune(1, G.FP32)
+    bf = torch.view_as_real(torch.from_numpy(LY.to_full([[b]], dims, None))).cuda().contiguous()
+    x = torch.zeros_like(bf)
+    st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32)
+    xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
+    assert O.true_residual(U, xf, b, MOBIUS) <= 1e-10

@@ -58,7 +58,7 @@ def test_gauge_equivariance():
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
 
 
-@pytest.mark.parametrize("energy", [False, True])
+@pytest.mark.parametrize("energy", [False, True, "a2"])
 def test_gradient_central_differences(energy):
     dims, Ls, C = (4, 2, 2, 2), 4, 2
     rng = np.random.default_rng(4)
@@ -72,7 +72,8 @@ def test_gradient_central_differences(energy):
         pairs = [(inputs.gaussian_source(dims, Ls, rng=rng),
                   O.parity_part(inputs.gaussian_source(dims, Ls, rng=rng), 1)) for _ in range(2)]
     W1, W2 = rand_w(rng, C)
-    L, g1, g2 = N.loss_and_grad(U, pairs, W1, W2, A)
+    kind = "a2" if energy == "a2" else None
+    L, g1, g2 = N.loss_and_grad(U, pairs, W1, W2, A, kind)
     h = 1e-6
     picks = [(0, (0, 0, 0, 1, 2)), (0, (3, 1, 0, 0, 0)), (0, (9, 0, 0, 2, 3)),
              (1, (0, 0, 1, 3, 3)), (1, (6, 0, 0, 1, 0)), (1, (10, 0, 1, 2, 1))]
@@ -82,8 +83,8 @@ def test_gradient_central_differences(energy):
             Wm = [W1.copy(), W2.copy()]
             Wp[which][idx] += h * part
             Wm[which][idx] -= h * part
-            Lp = N.loss_and_grad(U, pairs, *Wp, A)[0]
-            Lm = N.loss_and_grad(U, pairs, *Wm, A)[0]
+            Lp = N.loss_and_grad(U, pairs, *Wp, A, kind)[0]
+            Lm = N.loss_and_grad(U, pairs, *Wm, A, kind)[0]
             fd = (Lp - Lm) / (2 * h)
             an = (g1 if which == 0 else g2)[idx]
             an = an.real if part == 1.0 else an.imag
