@@ -380,6 +380,14 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
     }
     if (st == DWF_OK) st = init_hop_kernels();
     if (st == DWF_OK) st = init_local_kernels();
+    if (st == DWF_OK) st = init_local_mat_kernels();
+    if (st == DWF_OK) {
+        std::vector<float> mats;
+        build_fived_mats(f5, mats);
+        st = dalloc(&h->d_mats, mats.size());
+        if (st == DWF_OK)
+            cudaMemcpy(h->d_mats, mats.data(), mats.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (st == DWF_OK) st = dalloc(&h->d_err, 1);
     if (st == DWF_OK) {
         cudaMemset(h->d_err, 0, sizeof(int));
@@ -416,6 +424,7 @@ dwf_status destroy(dwf_handle* h) {
     cudaFree(h->d_err);
     cudaFree(h->d_tmp);
     cudaFree(h->d_tmp2);
+    cudaFree(h->d_mats);
     for (auto& kv : h->tiles)
         for (int q = 0; q < 2; ++q) {
             cudaFree(kv.second.d_tiles[q]);

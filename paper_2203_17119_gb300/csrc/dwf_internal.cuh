@@ -126,6 +126,7 @@ struct dwf_handle {
     void* d_tmp = nullptr;        // one FP64 cb field x nrhs_max (operator calls)
     void* d_tmp2 = nullptr;
     dwf::FiveD f5[2];             // [dagger] (identical scalars, kept per use)
+    float* d_mats = nullptr;      // fifth-dimension operator matrices [4][2][Ls][Ls]
     std::map<int, dwf::SolverWS> ws;   // keyed by prec * 64 + nrhs
     // autotuned tile sizes: nrhs -> sites per tile
     std::map<int, int> tuned_T;
@@ -163,6 +164,8 @@ struct HopCall {
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
 dwf_status init_hop_kernels();
 dwf_status init_local_kernels();
+dwf_status init_local_mat_kernels();
+void build_fived_mats(const FiveD& f, std::vector<float>& out);
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
 
 struct LocalCall {

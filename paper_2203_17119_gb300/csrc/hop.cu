@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
             const R f_below = lo_wrap ? -mf : (R)1;
             const R f_above = hi_wrap ? -mf : (R)1;
             double nrm = 0.0;
+            float nrm_f = 0.f;   // FP32 arithmetic: one FP64 add per site, off the slow FP64 pipe
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
                 R xr[VL], xi[VL];
@@ -284,10 +285,10 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                     part += (float)(orr[v] * orr[v] + oi[v] * oi[v]);
                     if (sizeof(R) == 8) nrm += (double)orr[v] * orr[v] + (double)oi[v] * oi[v];
                 }
-                if (sizeof(R) != 8) nrm += (double)part;
+                if (sizeof(R) != 8) nrm_f += part;
                 store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
             }
-            tile_norm += nrm;
+            tile_norm += sizeof(R) == 8 ? nrm : (double)nrm_f;
         }
     }
         if (EPI == EPI_MOO && a.partial != nullptr) {
