@@ -347,7 +347,11 @@ def run_hop(args):
     h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), nrhs_max=nrhs)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     del U
-    T = h.autotune(nrhs, prec) if not args.no_autotune else None
+    if args.hop_config:
+        T, vl = args.hop_config
+        h.set_tile(nrhs, T, vl)
+    else:
+        T = h.autotune(nrhs, prec) if not args.no_autotune else None
     inp = torch.randn(h.cb_shape(1, nrhs), device="cuda").to(G._DTYPE[prec])
     out = h.empty_cb(0, nrhs, prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -372,7 +376,7 @@ def run_hop(args):
     except (OSError, ValueError, KeyError):
         pass
     print(json.dumps({"kernel": "hop", "lattice": [L] * 4, "Ls": Ls, "nrhs": nrhs, "prec": prec_name,
-                      "tile_sites": T, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
+                      "tile_sites": T, "config": args.hop_config, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
                       "algorithmic_bytes": nbytes}))
 
@@ -448,6 +452,8 @@ def main():
     ap.add_argument("--hop", nargs="+", metavar="ARG",
                     help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--hop-config", nargs=2, type=int, metavar=("TILE", "VL"),
+                    help="--hop: fixed sites per tile and lanes per thread instead of autotuning")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -142,7 +142,7 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
                   kMinTile);
         return DWF_ERR_ARG;
     }
-    const size_t smem = 2 * (size_t)tile_sites * (144 * 8 + 32) + 16 + 256 * 8;
+    const size_t smem = hop_smem(tile_sites, 8, 8, nrhs);
     if (smem > (size_t)kHopMaxSmem) {
         set_error("dwf_set_tile: %d sites per tile exceed the FP64 hop's shared memory", tile_sites);
         return DWF_ERR_ARG;

@@ -21,6 +21,13 @@ constexpr int kMaxLs = 32;
 constexpr int kHopMaxSmem = 200 * 1024;   // dynamic shared memory cap of the hop
 constexpr int kMinTile = 4;               // smallest tile the autotuner may pick
 
+// Dynamic shared memory of the register hop: double-buffered links and
+// neighbour indices of T sites, two mbarriers, two arrival counters and the
+// per-warp norm partials.
+inline size_t hop_smem(int T, size_t link_word, int nwarps, int nrhs) {
+    return 2 * (size_t)T * (144 * link_word + 32) + 24 + (size_t)2 * nwarps * nrhs * 8;
+}
+
 // ------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
 
@@ -96,6 +103,7 @@ struct SolverWS {
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;
     int graph_T = 0;
+    double graph_delta = -1.0;   // reliable-update threshold captured in the graph
     int graph_kernels = 0;
     cudaStream_t graph_stream = nullptr;
 };

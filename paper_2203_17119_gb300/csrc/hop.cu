@@ -16,7 +16,9 @@
 // Epilogues: PLAIN   out = scale * Dh in
 //            MOO     out = M_oo x + scale * Dh in  (+ per-tile |out|^2),
 //            the last step of the Schur operator M_pc = M_oo - M_oe M_ee^-1 M_eo.
+#include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include <map>
 #include <utility>
 
@@ -38,17 +40,16 @@ struct HopArgs {
     int* err;
 };
 
+// One direction K (0..3: +mu, 4..7: -mu) for the VL lanes of one site; src
+// points at lane0 of the neighbour's spinor ([12][N5] complex), in global or
+// shared memory.
 template <int K, bool DAG, class Sin, class SL, class R, int VL>
-__device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s_nbr,
-                                        const SL* s_link, int N5, int lane0, R (&ar)[12][VL],
-                                        R (&ai)[12][VL]) {
+__device__ __forceinline__ void hop_dir_src(const Sin* __restrict__ src, const SL* s_link, int N5,
+                                            R (&ar)[12][VL], R (&ai)[12][VL]) {
     constexpr int MU = K & 3;
     constexpr bool FWD = K < 4;
     constexpr int SGI = (FWD != DAG) ? 1 : -1;   // (1 - SG g_mu) projector
     const R SG = (R)SGI;
-    const int n = s_nbr[K];
-    if (n < 0) return;   // link cut by a Dirichlet boundary
-    const Sin* src = in + ((int64_t)n * 12 * N5 + lane0) * 2;
     R ur[2][3][VL], ui[2][3][VL], lr[2][3][VL], li[2][3][VL];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
@@ -141,9 +142,211 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
         }
 }
 
+// The same direction for two lanes in FP32 with paired-FP32 instructions
+// (fma/mul .f32x2 on sm_100 and later): each float2 holds one real or
+// imaginary component of both lanes, so every operation of the scalar form
+// above is one instruction for the pair.  Same formulas, same order.  Used
+// for BF16 operands, whose conversion already yields separate components
+// (15% faster at 32^4 x 16); for FP32 operands the regrouping of the loaded
+// (re, im, re, im) quads and the extra register pressure made it slower.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int K, bool DAG, class Sin, class SL>
+__device__ __forceinline__ void hop_dir_x2(const Sin* __restrict__ src, const SL* s_link, int N5,
+                                           float2 (&ar)[12], float2 (&ai)[12]) {
+    constexpr int MU = K & 3;
+    constexpr bool FWD = K < 4;
+    constexpr float SG = (FWD != DAG) ? 1.f : -1.f;   // (1 - SG g_mu) projector
+    const float2 P = f2(SG), M = f2(-SG);
+    float2 ur[2][3], ui[2][3], lr[2][3], li[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float re[2], im[2];
+            load_lanes<Sin, 2, float>(src + (int64_t)((sp * 3 + c) * N5) * 2, re, im);
+            ur[sp][c] = make_float2(re[0], re[1]);
+            ui[sp][c] = make_float2(im[0], im[1]);
+            load_lanes<Sin, 2, float>(src + (int64_t)(((sp + 2) * 3 + c) * N5) * 2, re, im);
+            lr[sp][c] = make_float2(re[0], re[1]);
+            li[sp][c] = make_float2(im[0], im[1]);
+        }
+    // half spinor h = u - SG A_mu l
+    float2 hr[2][3], hi[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (MU == 0) {
+            hr[0][c] = fma2(M, li[1][c], ur[0][c]);
+            hi[0][c] = fma2(P, lr[1][c], ui[0][c]);
+            hr[1][c] = fma2(M, li[0][c], ur[1][c]);
+            hi[1][c] = fma2(P, lr[0][c], ui[1][c]);
+        } else if (MU == 1) {
+            hr[0][c] = fma2(P, lr[1][c], ur[0][c]);
+            hi[0][c] = fma2(P, li[1][c], ui[0][c]);
+            hr[1][c] = fma2(M, lr[0][c], ur[1][c]);
+            hi[1][c] = fma2(M, li[0][c], ui[1][c]);
+        } else if (MU == 2) {
+            hr[0][c] = fma2(M, li[0][c], ur[0][c]);
+            hi[0][c] = fma2(P, lr[0][c], ui[0][c]);
+            hr[1][c] = fma2(P, li[1][c], ur[1][c]);
+            hi[1][c] = fma2(M, lr[1][c], ui[1][c]);
+        } else {
+            hr[0][c] = fma2(M, lr[0][c], ur[0][c]);
+            hi[0][c] = fma2(M, li[0][c], ui[0][c]);
+            hr[1][c] = fma2(M, lr[1][c], ur[1][c]);
+            hi[1][c] = fma2(M, li[1][c], ui[1][c]);
+        }
+    }
+    // g = W h (two colour vectors)
+    const SL* w = s_link + K * 18;
+    float2 gr[2][3], gi[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float wr[3], wi[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) link_c<SL, float>(w, a * 3 + b, wr[b], wi[b]);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            float2 sr = __fmul2_rn(f2(wr[0]), hr[sp][0]);
+            float2 si = __fmul2_rn(f2(wr[0]), hi[sp][0]);
+            sr = fma2(f2(-wi[0]), hi[sp][0], sr);
+            si = fma2(f2(wi[0]), hr[sp][0], si);
+            sr = fma2(f2(wr[1]), hr[sp][1], sr); sr = fma2(f2(-wi[1]), hi[sp][1], sr);
+            si = fma2(f2(wr[1]), hi[sp][1], si); si = fma2(f2(wi[1]), hr[sp][1], si);
+            sr = fma2(f2(wr[2]), hr[sp][2], sr); sr = fma2(f2(-wi[2]), hi[sp][2], sr);
+            si = fma2(f2(wr[2]), hi[sp][2], si); si = fma2(f2(wi[2]), hr[sp][2], si);
+            gr[sp][a] = sr;
+            gi[sp][a] = si;
+        }
+    }
+    // reconstruct: upper += g, lower += -SG A_mu^+ g
+    const float2 one = f2(1.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ar[c] = fma2(one, gr[0][c], ar[c]);
+        ai[c] = fma2(one, gi[0][c], ai[c]);
+        ar[3 + c] = fma2(one, gr[1][c], ar[3 + c]);
+        ai[3 + c] = fma2(one, gi[1][c], ai[3 + c]);
+        if (MU == 0) {
+            ar[6 + c] = fma2(P, gi[1][c], ar[6 + c]);
+            ai[6 + c] = fma2(M, gr[1][c], ai[6 + c]);
+            ar[9 + c] = fma2(P, gi[0][c], ar[9 + c]);
+            ai[9 + c] = fma2(M, gr[0][c], ai[9 + c]);
+        } else if (MU == 1) {
+            ar[6 + c] = fma2(M, gr[1][c], ar[6 + c]);
+            ai[6 + c] = fma2(M, gi[1][c], ai[6 + c]);
+            ar[9 + c] = fma2(P, gr[0][c], ar[9 + c]);
+            ai[9 + c] = fma2(P, gi[0][c], ai[9 + c]);
+        } else if (MU == 2) {
+            ar[6 + c] = fma2(P, gi[0][c], ar[6 + c]);
+            ai[6 + c] = fma2(M, gr[0][c], ai[6 + c]);
+            ar[9 + c] = fma2(M, gi[1][c], ar[9 + c]);
+            ai[9 + c] = fma2(P, gr[1][c], ai[9 + c]);
+        } else {
+            ar[6 + c] = fma2(M, gr[0][c], ar[6 + c]);
+            ai[6 + c] = fma2(M, gi[0][c], ai[6 + c]);
+            ar[9 + c] = fma2(M, gr[1][c], ar[9 + c]);
+            ai[9 + c] = fma2(M, gi[1][c], ai[9 + c]);
+        }
+    }
+}
+
+template <int K, bool DAG, class Sin, class SL>
+__device__ __forceinline__ void hop_dir2(const Sin* __restrict__ in, const int* s_nbr,
+                                         const SL* s_link, int N5, int lane0, float2 (&ar)[12],
+                                         float2 (&ai)[12]) {
+    const int n = s_nbr[K];
+    if (n < 0) return;   // link cut by a Dirichlet boundary
+    hop_dir_x2<K, DAG, Sin, SL>(in + ((int64_t)n * 12 * N5 + lane0) * 2, s_link, N5, ar, ai);
+}
+
+template <int K, bool DAG, class Sin, class SL, class R, int VL>
+__device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s_nbr,
+                                        const SL* s_link, int N5, int lane0, R (&ar)[12][VL],
+                                        R (&ai)[12][VL]) {
+    const int n = s_nbr[K];
+    if (n < 0) return;   // link cut by a Dirichlet boundary
+    hop_dir_src<K, DAG, Sin, SL, R, VL>(in + ((int64_t)n * 12 * N5 + lane0) * 2, s_link, N5, ar, ai);
+}
+
+// Output of one site's VL lanes: PLAIN out = scale * acc; MOO out = M_oo x +
+// scale * acc, returning the lanes' |out|^2 (FP32 arithmetic: summed in FP32
+// per site, one FP64 add per site, off GB300's slow FP64 pipe).
+template <class Sout, class R, int VL, bool DAG, int EPI>
+__device__ __forceinline__ double hop_store(const HopArgs& a, int64_t site, int lane0,
+                                            const R (&ar)[12][VL], const R (&ai)[12][VL]) {
+    const int N5 = a.N5;
+    const R sc = (R)a.scale;
+    Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
+    if (EPI == EPI_PLAIN) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            R orr[VL], oi[VL];
+#pragma unroll
+            for (int v = 0; v < VL; ++v) {
+                orr[v] = sc * ar[c][v];
+                oi[v] = sc * ai[c][v];
+            }
+            store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
+        }
+        return 0.0;
+    }
+    // M_oo x = d x + e S5 x on this site's lanes; S5 (non-dagger):
+    // upper spins x_{s-1}, lower spins x_{s+1}, walls -mf.
+    const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
+    const int Ls = a.Ls;
+    const int s0 = lane0 % Ls;
+    const int rbase = lane0 - s0;
+    const R d = (R)a.d, e = (R)a.e, mf = (R)a.mf;
+    // neighbouring lanes below and above this thread's block
+    const bool lo_wrap = (s0 == 0);
+    const bool hi_wrap = (s0 + VL == Ls);
+    const int l_below = lo_wrap ? rbase + Ls - 1 : lane0 - 1;
+    const int l_above = hi_wrap ? rbase : lane0 + VL;
+    const R f_below = lo_wrap ? -mf : (R)1;
+    const R f_above = hi_wrap ? -mf : (R)1;
+    double nrm = 0.0;
+    float nrm_f = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        R xr[VL], xi[VL];
+        load_lanes<Sout, VL, R>(xb + (int64_t)(c * N5 + lane0) * 2, xr, xi);
+        // upper spins use S_- (x_{s-1}) unless dagger, lower S_+
+        const bool use_below = (c < 6) != DAG;
+        R nr, ni;
+        load_c1<Sout, R>(xb + (int64_t)(c * N5 + (use_below ? l_below : l_above)) * 2, nr, ni);
+        const R fn = use_below ? f_below : f_above;
+        R orr[VL], oi[VL];
+        float part = 0.f;
+#pragma unroll
+        for (int v = 0; v < VL; ++v) {
+            R sr, si;
+            if (use_below) {
+                sr = (v == 0) ? fn * nr : xr[v - 1];
+                si = (v == 0) ? fn * ni : xi[v - 1];
+            } else {
+                sr = (v == VL - 1) ? fn * nr : xr[(v + 1) % VL];
+                si = (v == VL - 1) ? fn * ni : xi[(v + 1) % VL];
+            }
+            orr[v] = d * xr[v] + e * sr + sc * ar[c][v];
+            oi[v] = d * xi[v] + e * si + sc * ai[c][v];
+            part += (float)(orr[v] * orr[v] + oi[v] * oi[v]);
+            if (sizeof(R) == 8) nrm += (double)orr[v] * orr[v] + (double)oi[v] * oi[v];
+        }
+        if (sizeof(R) != 8) nrm_f += part;
+        store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
+    }
+    return sizeof(R) == 8 ? nrm : (double)nrm_f;
+}
+
 // Persistent kernel: CTA b takes tiles b, b + gridDim, ...; the links and
-// neighbour indices of the next tile are bulk-copied into the other half of
-// a double buffer while the current tile is computed.
+// neighbour indices of a tile arrive by bulk copy into one half of a double
+// buffer.  There is no CTA-wide barrier in the tile loop: each warp waits for
+// its tile's copy on the buffer's mbarrier, and the last warp to finish with
+// a buffer (a shared-memory arrival counter) sums the per-warp norm partials
+// in warp order and issues the copy of the tile two steps ahead into it, so
+// fast warps run on into the next tile.
 template <class Sin, class Sout, class SL, class R, int VL, bool DAG, int EPI>
 __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_hop(const HopArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -151,9 +354,10 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const size_t link_bytes = (size_t)a.T * 144 * sizeof(SL);
     const size_t buf_bytes = link_bytes + (size_t)a.T * 32;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * buf_bytes);
-    double* s_red = reinterpret_cast<double*>(bar + 2);
-    __shared__ int s_ok;
+    int* done = reinterpret_cast<int*>(bar + 2);              // [2] warps finished with a buffer
+    double* s_red = reinterpret_cast<double*>(bar + 3);       // [2][nwarps][nrhs]
     const int nt = a.ntiles;
+    const int nwarps = (int)(blockDim.x >> 5), warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     auto issue = [&](int tile, int b) {
         const int4 t = a.tiles[tile];
@@ -170,8 +374,10 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        done[0] = done[1] = 0;
         fence_mbar_init();
         if ((int)blockIdx.x < nt) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nt) issue(blockIdx.x + gridDim.x, 1);
     }
     __syncthreads();
 
@@ -179,26 +385,19 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const int sg = threadIdx.x / TPS;
     const int lane0 = (threadIdx.x - sg * TPS) * VL;
     const int N5 = a.N5;
-    const Sin* in = reinterpret_cast<const Sin*>(a.in);
+    const int rhs = lane0 / a.Ls;   // of this thread's lanes (threads without sites add 0)
+    const bool part = EPI == EPI_MOO && a.partial != nullptr;
 
     int k = 0;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x, ++k) {
         const int b = k & 1;
-        if (threadIdx.x == 0) {
-            const int next = tile + gridDim.x;
-            if (next < nt) issue(next, b ^ 1);   // the other buffer is free
-            bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
-            if (!ok) {
+        const uint32_t ph = (uint32_t)((k >> 1) & 1);
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], ph))) {
+            // a lost copy: record it, let it land, stop
+            if (lane == 0) {
                 atomicOr(a.err, kErrBulkTimeout);
-                mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1));
+                mbar_wait_bounded(&bar[b], ph);
             }
-            s_ok = ok ? 1 : 0;
-        }
-        __syncthreads();
-        if (!s_ok) {
-            // a lost copy: let the one in flight land, then stop (uniform)
-            if (threadIdx.x == 0 && tile + gridDim.x < nt)
-                mbar_wait_bounded(&bar[b ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
             return;
         }
         const int4 tl = a.tiles[tile];
@@ -206,99 +405,71 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         const SL* s_link_t = reinterpret_cast<const SL*>(smem + b * buf_bytes);
         const int* s_nbr_t = reinterpret_cast<const int*>(smem + b * buf_bytes + link_bytes);
         double tile_norm = 0.0;
-
-    for (int sl = sg; sg < G && sl < count; sl += G) {
-        R ar[12][VL], ai[12][VL];
+        for (int sl = sg; sg < G && sl < count; sl += G) {
+            R ar[12][VL], ai[12][VL];
+            const Sin* in = reinterpret_cast<const Sin*>(a.in);
+            const int* nb = s_nbr_t + sl * 8;
+            const SL* lk = s_link_t + (size_t)sl * 144;
+            // +mu and -mu back to back: the row that is the +x neighbour of
+            // one site is the -x neighbour of the next, still in L1
+            if constexpr (std::is_same<R, float>::value && VL == 2 && std::is_same<Sin, bf16>::value) {
+                float2 pr[12], pi[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c)
+                for (int c = 0; c < 12; ++c) pr[c] = pi[c] = make_float2(0.f, 0.f);
+                hop_dir2<0, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<4, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<1, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<5, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<2, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<6, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<3, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                hop_dir2<7, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
 #pragma unroll
-            for (int v = 0; v < VL; ++v) ar[c][v] = ai[c][v] = (R)0;
-        const Sin* in = reinterpret_cast<const Sin*>(a.in);
-        const int* nb = s_nbr_t + sl * 8;
-        const SL* lk = s_link_t + (size_t)sl * 144;
-        // +mu and -mu back to back: the row that is the +x neighbour of
-        // one site is the -x neighbour of the next, still in L1
-        hop_dir<0, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<4, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<1, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<5, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<2, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<6, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-        hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
-
-        const R sc = (R)a.scale;
-        const int64_t site = begin + sl;
-        Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
-        if (EPI == EPI_PLAIN) {
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                R orr[VL], oi[VL];
-#pragma unroll
-                for (int v = 0; v < VL; ++v) {
-                    orr[v] = sc * ar[c][v];
-                    oi[v] = sc * ai[c][v];
+                for (int c = 0; c < 12; ++c) {
+                    ar[c][0] = pr[c].x; ar[c][VL - 1] = pr[c].y;
+                    ai[c][0] = pi[c].x; ai[c][VL - 1] = pi[c].y;
                 }
-                store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c)
+#pragma unroll
+                    for (int v = 0; v < VL; ++v) ar[c][v] = ai[c][v] = (R)0;
+                hop_dir<0, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<4, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<1, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<5, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<2, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<6, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
             }
-        } else {
-            // M_oo x = d x + e S5 x on this site's lanes; S5 (non-dagger):
-            // upper spins x_{s-1}, lower spins x_{s+1}, walls -mf.
-            const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
-            const int Ls = a.Ls;
-            const int s0 = lane0 % Ls;
-            const int rbase = lane0 - s0;
-            const R d = (R)a.d, e = (R)a.e, mf = (R)a.mf;
-            // neighbouring lanes below and above this thread's block
-            const bool lo_wrap = (s0 == 0);
-            const bool hi_wrap = (s0 + VL == Ls);
-            const int l_below = lo_wrap ? rbase + Ls - 1 : lane0 - 1;
-            const int l_above = hi_wrap ? rbase : lane0 + VL;
-            const R f_below = lo_wrap ? -mf : (R)1;
-            const R f_above = hi_wrap ? -mf : (R)1;
-            double nrm = 0.0;
-            float nrm_f = 0.f;   // FP32 arithmetic: one FP64 add per site, off the slow FP64 pipe
+            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, begin + sl, lane0, ar, ai);
+        }
+        double* red = s_red + (size_t)b * nwarps * a.nrhs;
+        if (part) {
+            for (int r = 0; r < a.nrhs; ++r) {
+                double v = rhs == r ? tile_norm : 0.0;
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                R xr[VL], xi[VL];
-                load_lanes<Sout, VL, R>(xb + (int64_t)(c * N5 + lane0) * 2, xr, xi);
-                // upper spins use S_- (x_{s-1}) unless dagger, lower S_+
-                const bool use_below = (c < 6) != DAG;
-                R nr, ni;
-                load_c1<Sout, R>(xb + (int64_t)(c * N5 + (use_below ? l_below : l_above)) * 2, nr,
-                                 ni);
-                const R fn = use_below ? f_below : f_above;
-                R orr[VL], oi[VL];
-                float part = 0.f;
-#pragma unroll
-                for (int v = 0; v < VL; ++v) {
-                    R sr, si;
-                    if (use_below) {
-                        sr = (v == 0) ? fn * nr : xr[v - 1];
-                        si = (v == 0) ? fn * ni : xi[v - 1];
-                    } else {
-                        sr = (v == VL - 1) ? fn * nr : xr[(v + 1) % VL];
-                        si = (v == VL - 1) ? fn * ni : xi[(v + 1) % VL];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp * a.nrhs + r] = v;
+            }
+        }
+        __syncwarp();   // this warp's reads of buffer b are done
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&done[b], 1) == nwarps - 1) {   // the last warp out
+                __threadfence_block();
+                if (part)
+                    for (int r = 0; r < a.nrhs; ++r) {
+                        double sum = 0.0;
+                        for (int w = 0; w < nwarps; ++w) sum += red[w * a.nrhs + r];
+                        a.partial[(size_t)tile * a.nrhs + r] = sum;
                     }
-                    orr[v] = d * xr[v] + e * sr + sc * ar[c][v];
-                    oi[v] = d * xi[v] + e * si + sc * ai[c][v];
-                    part += (float)(orr[v] * orr[v] + oi[v] * oi[v]);
-                    if (sizeof(R) == 8) nrm += (double)orr[v] * orr[v] + (double)oi[v] * oi[v];
-                }
-                if (sizeof(R) != 8) nrm_f += part;
-                store_lanes<Sout, VL, R, true>(out + (int64_t)c * N5 * 2, orr, oi);
+                done[b] = 0;
+                const int next2 = tile + 2 * (int)gridDim.x;
+                if (next2 < nt) issue(next2, b);
             }
-            tile_norm += sizeof(R) == 8 ? nrm : (double)nrm_f;
         }
-    }
-        if (EPI == EPI_MOO && a.partial != nullptr) {
-            const int Ls = a.Ls;
-            block_rhs_reduce(
-                tile_norm, s_red, a.nrhs,
-                [&](int t) { return (t / TPS < G && t / TPS < count) ? ((t % TPS) * VL) / Ls : -1; },
-                a.partial + (size_t)tile * a.nrhs);
-        }
-        __syncthreads();   // buffer b is rewritten two tiles from now
     }
 }
 
@@ -332,7 +503,7 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
         return DWF_ERR_ARG;
     }
     int threads = (groups * TPS + 31) / 32 * 32;
-    const size_t smem = 2 * (size_t)ts.T * (144 * sizeof(SL) + 32) + 16 + (size_t)threads * 8;
+    const size_t smem = hop_smem(ts.T, sizeof(SL), threads / 32, c.nrhs);
     const int nt = ts.ntiles[p];
     if (nt == 0) return DWF_OK;
     a.ntiles = nt;
@@ -373,6 +544,15 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     return DWF_OK;
 }
 
+// FP32-arithmetic hop: two lanes per thread unless the call asks for one
+// (FP32 links only).
+template <class Sin, class Sout, class SL>
+static dwf_status launch_f32(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s) {
+    if constexpr (std::is_same<SL, float>::value)
+        if (c.VL == 1) return launch_t<Sin, Sout, SL, float, 1>(h, c, ts, s);
+    return launch_t<Sin, Sout, SL, float, 2>(h, c, ts, s);
+}
+
 // Raise the dynamic shared-memory limit of every hop instantiation once, so
 // that launches recorded into a CUDA graph never need a host-side call.
 template <class Sin, class Sout, class SL, class R, int VL>
@@ -408,18 +588,13 @@ dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {
     }
     if (c.prec_link == DWF_FP32) {
         if (c.prec_in != DWF_FP32 || c.prec_out != DWF_FP32) return DWF_ERR_UNSUPPORTED;
-        if (c.VL == 1) return launch_t<float, float, float, float, 1>(h, c, ts, s);
-        return launch_t<float, float, float, float, 2>(h, c, ts, s);
+        return launch_f32<float, float, float>(h, c, ts, s);
     }
     // BF16 links: FP32 arithmetic, operands FP32 or BF16
-    if (c.prec_in == DWF_BF16 && c.prec_out == DWF_BF16)
-        return launch_t<bf16, bf16, bf16, float, 2>(h, c, ts, s);
-    if (c.prec_in == DWF_BF16 && c.prec_out == DWF_FP32)
-        return launch_t<bf16, float, bf16, float, 2>(h, c, ts, s);
-    if (c.prec_in == DWF_FP32 && c.prec_out == DWF_BF16)
-        return launch_t<float, bf16, bf16, float, 2>(h, c, ts, s);
-    if (c.prec_in == DWF_FP32 && c.prec_out == DWF_FP32)
-        return launch_t<float, float, bf16, float, 2>(h, c, ts, s);
+    if (c.prec_in == DWF_BF16 && c.prec_out == DWF_BF16) return launch_f32<bf16, bf16, bf16>(h, c, ts, s);
+    if (c.prec_in == DWF_BF16 && c.prec_out == DWF_FP32) return launch_f32<bf16, float, bf16>(h, c, ts, s);
+    if (c.prec_in == DWF_FP32 && c.prec_out == DWF_BF16) return launch_f32<float, bf16, bf16>(h, c, ts, s);
+    if (c.prec_in == DWF_FP32 && c.prec_out == DWF_FP32) return launch_f32<float, float, bf16>(h, c, ts, s);
     return DWF_ERR_UNSUPPORTED;
 }
 

@@ -47,13 +47,13 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     int best_T = tile_for(h, nrhs);
     int best_vl = 2;
     dwf_status st = DWF_OK;
-    const int nvl = prec == DWF_FP32 ? 2 : 1;
-    for (int vi = 0; vi < nvl; ++vi)
+    // lanes per thread: FP32 tries both, the others have one kernel
+    const std::vector<int> vls = prec == DWF_FP32 ? std::vector<int>{2, 1} : std::vector<int>{0};
+    for (int vl : vls)
     for (int T : cands) {
-        const int vl = prec == DWF_FP32 ? (vi == 0 ? 2 : 1) : 0;
         // the tile table is shared by every precision of an operator chain
         // (FP64 reliable updates included): size the check for FP64 links
-        const size_t smem = 2 * (size_t)T * (144 * 8 + 32) + 16 + 256 * 8;
+        const size_t smem = hop_smem(T, 8, 8, nrhs);
         if (smem > (size_t)kHopMaxSmem) continue;   // double-buffered links + reduction scratch
         HopCall c{};
         c.in = h->d_tmp2;

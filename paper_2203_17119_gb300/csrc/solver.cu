@@ -326,7 +326,9 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     DWF_TRY(restart(true));
 
     // capture K iterations once per workspace
-    if (w.graph_exec == nullptr || w.graph_iters != K || w.graph_T != tile_for(h, nrhs)) {
+    // (delta is a kernel argument of the captured k_beta: a new delta re-captures)
+    if (w.graph_exec == nullptr || w.graph_iters != K || w.graph_T != tile_for(h, nrhs) ||
+        w.graph_delta != delta) {
         if (w.graph_exec) { cudaGraphExecDestroy(w.graph_exec); w.graph_exec = nullptr; }
         if (w.graph) { cudaGraphDestroy(w.graph); w.graph = nullptr; }
         DWF_CUDA(cudaStreamSynchronize(s));
@@ -343,6 +345,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
         DWF_CUDA(cudaGraphInstantiate(&w.graph_exec, g, 0));
         w.graph_iters = K;
         w.graph_T = tile_for(h, nrhs);
+        w.graph_delta = delta;
     }
 
     dwf_status result = DWF_OK;

@@ -107,3 +107,24 @@ def test_zero_source_and_initial_guess():
     it0 = stats[0]["iters"]
     stats, rc = h.cgne_solve(x, bf, tol=1e-10, use_x0=True)
     assert stats[0]["iters"] < max(2, it0 // 4)
+
+
+def test_reliable_update_threshold_is_honoured():
+    """A smaller reliable-update threshold delta (residual drop between FP64
+    updates) on the same handle and workspace gives fewer updates; both
+    solves reach 1e-10 by the oracle."""
+    dims, Ls = (4, 4, 4, 8), 8
+    rng = np.random.default_rng(41)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    b = inputs.gaussian_source(dims, Ls, rng=rng)
+    h = G.Handle(dims, Ls, G.Action(MOBIUS.M5, MOBIUS.mf, MOBIUS.b5, MOBIUS.c5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    bf = torch.view_as_real(torch.from_numpy(LY.to_full([[b]], dims, None))).cuda().contiguous()
+    upd = {}
+    for delta in (0.3, 0.003):
+        x = torch.zeros_like(bf)
+        st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32, delta=delta)
+        xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
+        assert st[0]["status"] == 0 and O.true_residual(U, xf, b, MOBIUS) <= 1e-10
+        upd[delta] = st[0]["reliable_updates"]
+    assert upd[0.003] < upd[0.3], upd
