@@ -143,7 +143,7 @@ def run_ours(args, rank, world):
             if hb is not None:
                 b.copy_(hb, non_blocking=True)
             x.zero_()
-            st, _ = h.cgne_solve(x, b, tol=1e-10, inner=G.FP32, delta=0.1)
+            st, _ = h.cgne_solve(x, b, tol=1e-10, inner=G.FP32)
             if hx is not None:
                 hx.copy_(x, non_blocking=True)
             stats.append(st[0])

@@ -195,7 +195,10 @@ dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dag
 typedef struct {
     double tol;          /* target |b - D x| / |b| per system (e.g. 1e-10)      */
     int maxiter;         /* cap on inner iterations                              */
-    double delta;        /* reliable-update trigger (mixed precision), e.g. 0.1  */
+    double delta;        /* reliable-update trigger (mixed precision): an FP64
+                            update when |r| drops below delta times its value at
+                            the last update; <= 0 selects 0.01 for the FP32
+                            operator, 0.1 for BF16 (rounding ~1e-2)            */
     int restart;         /* GCR restart length                                   */
     int use_x0;          /* 1: x holds the initial guess                         */
     dwf_prec inner_prec; /* DWF_FP64: plain FP64 CG; FP32/BF16: mixed precision  */

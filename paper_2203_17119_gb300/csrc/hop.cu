@@ -274,9 +274,8 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
 // scale * acc, returning the lanes' |out|^2 (FP32 arithmetic: summed in FP32
 // per site, one FP64 add per site, off GB300's slow FP64 pipe).
 template <class Sout, class R, int VL, bool DAG, int EPI>
-__device__ __forceinline__ double hop_store(const HopArgs& a, int64_t site, int lane0,
+__device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t site, int lane0,
                                             const R (&ar)[12][VL], const R (&ai)[12][VL]) {
-    const int N5 = a.N5;
     const R sc = (R)a.scale;
     Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
     if (EPI == EPI_PLAIN) {
@@ -347,10 +346,13 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int64_t site, int 
 // a buffer (a shared-memory arrival counter) sums the per-warp norm partials
 // in warp order and issues the copy of the tile two steps ahead into it, so
 // fast warps run on into the next tile.
-template <class Sin, class Sout, class SL, class R, int VL, bool DAG, int EPI>
+// CN5 > 0 fixes N5 = Ls * nrhs at compile time (the common single-rhs
+// cases), so the row offsets of every spinor load and store are immediates.
+template <class Sin, class Sout, class SL, class R, int VL, bool DAG, int EPI, int CN5>
 __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_hop(const HopArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int TPS = a.N5 / VL;
+    const int N5 = CN5 > 0 ? CN5 : a.N5;
+    const int TPS = N5 / VL;
     const size_t link_bytes = (size_t)a.T * 144 * sizeof(SL);
     const size_t buf_bytes = link_bytes + (size_t)a.T * 32;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * buf_bytes);
@@ -384,7 +386,6 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const int G = blockDim.x / TPS;
     const int sg = threadIdx.x / TPS;
     const int lane0 = (threadIdx.x - sg * TPS) * VL;
-    const int N5 = a.N5;
     const int rhs = lane0 / a.Ls;   // of this thread's lanes (threads without sites add 0)
     const bool part = EPI == EPI_MOO && a.partial != nullptr;
 
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                 hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
             }
-            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, begin + sl, lane0, ar, ai);
+            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai);
         }
         double* red = s_red + (size_t)b * nwarps * a.nrhs;
         if (part) {
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
 }
 
 // ------------------------------------------------------------- launcher
-template <class Sin, class Sout, class SL, class R, int VL>
+template <class Sin, class Sout, class SL, class R, int VL, int CN5 = 0>
 static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s) {
     const int p = c.out_parity;
     HopArgs a;
@@ -510,11 +511,11 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     void (*kern)(const HopArgs);
     const bool moo = c.xmoo != nullptr;
     if (c.dagger)
-        kern = moo ? k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO>
-                   : k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN>;
+        kern = moo ? k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO, CN5>
+                   : k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN, CN5>;
     else
-        kern = moo ? k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO>
-                   : k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN>;
+        kern = moo ? k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO, CN5>
+                   : k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN, CN5>;
     if (smem > kHopMaxSmem) {
         set_error("hop: tile of %d sites needs %zu bytes of shared memory", ts.T, smem);
         return DWF_ERR_ARG;
@@ -548,20 +549,33 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
 // (FP32 links only).
 template <class Sin, class Sout, class SL>
 static dwf_status launch_f32(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s) {
-    if constexpr (std::is_same<SL, float>::value)
-        if (c.VL == 1) return launch_t<Sin, Sout, SL, float, 1>(h, c, ts, s);
+    const int N5 = h->p.Ls * c.nrhs;
+    if constexpr (std::is_same<SL, float>::value) {
+        if (c.VL == 1) {
+            if (N5 == 12) return launch_t<Sin, Sout, SL, float, 1, 12>(h, c, ts, s);
+            if (N5 == 16) return launch_t<Sin, Sout, SL, float, 1, 16>(h, c, ts, s);
+            return launch_t<Sin, Sout, SL, float, 1>(h, c, ts, s);
+        }
+    }
+    constexpr bool spec = (std::is_same<SL, float>::value && std::is_same<Sin, float>::value &&
+                           std::is_same<Sout, float>::value) ||
+                          (std::is_same<Sin, bf16>::value && std::is_same<Sout, bf16>::value);
+    if constexpr (spec) {
+        if (N5 == 12) return launch_t<Sin, Sout, SL, float, 2, 12>(h, c, ts, s);
+        if (N5 == 16) return launch_t<Sin, Sout, SL, float, 2, 16>(h, c, ts, s);
+    }
     return launch_t<Sin, Sout, SL, float, 2>(h, c, ts, s);
 }
 
 // Raise the dynamic shared-memory limit of every hop instantiation once, so
 // that launches recorded into a CUDA graph never need a host-side call.
-template <class Sin, class Sout, class SL, class R, int VL>
+template <class Sin, class Sout, class SL, class R, int VL, int CN5 = 0>
 static cudaError_t hop_attr() {
     cudaError_t e = cudaSuccess;
-    void (*k[4])(const HopArgs) = {k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN>,
-                                   k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO>,
-                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN>,
-                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO>};
+    void (*k[4])(const HopArgs) = {k_hop<Sin, Sout, SL, R, VL, false, EPI_PLAIN, CN5>,
+                                   k_hop<Sin, Sout, SL, R, VL, false, EPI_MOO, CN5>,
+                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN, CN5>,
+                                   k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO, CN5>};
     for (auto f : k) {
         cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
         if (r != cudaSuccess) e = r;
@@ -577,6 +591,12 @@ dwf_status init_hop_kernels() {
     DWF_CUDA((hop_attr<bf16, float, bf16, float, 2>()));
     DWF_CUDA((hop_attr<float, bf16, bf16, float, 2>()));
     DWF_CUDA((hop_attr<float, float, bf16, float, 2>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 2, 12>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 2, 16>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 1, 12>()));
+    DWF_CUDA((hop_attr<float, float, float, float, 1, 16>()));
+    DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2, 12>()));
+    DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2, 16>()));
     return DWF_OK;
 }
 

@@ -241,7 +241,11 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     const double* bo = b + 2 * ne;
     double* xe = x;
     double* xo = x + 2 * ne;
-    const double delta = (po == DWF_FP64) ? 0.0 : (sp->delta > 0 ? sp->delta : 0.1);
+    // default threshold: FP32 keeps the recursive residual accurate over two
+    // decades (6 FP64 updates instead of 11 on a 16^4 x 12 Moebius solve, same
+    // iteration count); BF16 rounding allows one
+    const double delta = (po == DWF_FP64) ? 0.0
+                         : (sp->delta > 0 ? sp->delta : (po == DWF_BF16 ? 0.1 : 0.01));
     const int K = sp->check_every > 0 ? sp->check_every : 8;
 
     DWF_CUDA(cudaMemsetAsync(w.sys, 0, sys_bytes, s));

@@ -261,7 +261,7 @@ class Handle:
                                          _stream(stream)))
         return out
 
-    def cgne_solve(self, x, b, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64, delta=0.1,
+    def cgne_solve(self, x, b, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64, delta=0.0,
                    use_x0=False, max_seconds=0.0, check_every=8, stream=None, allow_fail=False,
                    record=None, record_every=8):
         """Solve D x = b (D_Omega x = b on a box handle); x, b full FP64
