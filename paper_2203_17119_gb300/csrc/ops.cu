@@ -26,10 +26,13 @@ int tile_for(dwf_handle* h, int nrhs) {
     return 32;
 }
 
-// Autotuner: time the bare hop of precision `prec` with nrhs right-hand
-// sides for each candidate tile size (CUDA events, median of 7 launches on a
-// private stream, scratch fields of the handle) and keep the fastest for
-// every kernel chain with this nrhs.
+// Autotuner: for each candidate (tile size, lanes per thread) time what a
+// CG iteration applies, M_pc and M_pc^+ with the operator of precision
+// `prec` (the hops and the fifth-dimension kernels share the tile table; for
+// FP64, whose fields do not fit the scratch twice, the bare hop), with CUDA
+// events, median of 7 runs on a private stream with L2 flushed before each,
+// on the handle's scratch fields; keep the fastest for every kernel chain
+// with this nrhs.
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     const int cands[] = {8, 16, 32, 64, 128};
     cudaStream_t s;
@@ -39,6 +42,13 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     cudaEventCreate(&e1);
     const size_t bytes = cb_elems(h, 1, nrhs) * 2 * prec_size(prec);
     cudaMemsetAsync(h->d_tmp2, 0, bytes, s);
+    // FP32 / BF16 fields: two per FP64-sized scratch field
+    unsigned char* t1 = reinterpret_cast<unsigned char*>(h->d_tmp);
+    unsigned char* t2 = reinterpret_cast<unsigned char*>(h->d_tmp2);
+    const bool chain = prec != DWF_FP64;
+    if (chain) cudaMemsetAsync(t2 + bytes, 0, bytes, s);
+    const auto saved_T = h->tuned_T;
+    const auto saved_vl = h->tuned_vl;
     // candidates are timed with L2 flushed (solves stream more than L2 holds)
     const size_t flush_bytes = (size_t)256 << 20;
     void* flush = nullptr;
@@ -68,7 +78,15 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
             cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
-            st = launch_hop(h, c, s);
+            if (chain) {
+                h->tuned_T[nrhs] = T;
+                if (vl > 0) h->tuned_vl[nrhs] = vl;
+                st = op_mpc(h, t2 + bytes, t2, 0, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
+                if (st == DWF_OK)
+                    st = op_mpc(h, t2, t2 + bytes, 1, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
+            } else {
+                st = launch_hop(h, c, s);
+            }
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0;
@@ -85,6 +103,8 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     cudaStreamSynchronize(s);
     cudaFree(flush);
     cudaStreamDestroy(s);
+    h->tuned_T = saved_T;
+    h->tuned_vl = saved_vl;
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
     if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;

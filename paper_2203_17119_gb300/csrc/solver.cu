@@ -49,9 +49,8 @@ struct SysView {
     __host__ __device__ int* flg(int k) const { return f + (size_t)k * nsys; }
 };
 
-__global__ void k_alpha(SysView v) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.nsys) return;
+// alpha = <r, r> / <p, A p> for system i
+__device__ void alpha_step(SysView v, int i) {
     double a = 0.0;
     // a system whose last iteration asked for an FP64 update is frozen here,
     // after its search direction has been updated
@@ -65,9 +64,7 @@ __global__ void k_alpha(SysView v) {
 }
 
 // after r -= alpha A p: beta, iteration count, reliable-update trigger
-__global__ void k_beta(SysView v, double delta) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.nsys) return;
+__device__ void beta_step(SysView v, int i, double delta) {
     if (!v.flg(F_RUN)[i]) { v.dbl(S_BETA)[i] = 0.0; return; }
     const double rrn = v.dbl(S_TMP)[i];
     const double rr = v.dbl(S_RR)[i];
@@ -85,7 +82,35 @@ __global__ void k_beta(SysView v, double delta) {
     // low-precision recurrence)
     if (nr <= v.dbl(S_TARGET)[i] || (delta > 0.0 && nr <= delta * v.dbl(S_MAXR)[i]) ||
         nr > 1e3 * v.dbl(S_MAXR)[i])
-        v.flg(F_NEED)[i] = 1;   // frozen by the next k_alpha until the FP64 update
+        v.flg(F_NEED)[i] = 1;   // frozen by the next alpha step until the FP64 update
+}
+
+// One block per system: the deterministic sum of its tiles' partials (the
+// same order as k_reduce_sys), then the CG scalar step of that system --
+// STEP 0: <p, A p> and alpha, STEP 1: |r|^2 and beta.
+template <int STEP>
+__global__ void k_reduce_step(const double* __restrict__ partial, const int* __restrict__ box_tb,
+                              int nrhs, SysView v, double delta) {
+    __shared__ double sh[256];
+    const int sys = blockIdx.x;
+    const int box = sys / nrhs, r = sys % nrhs;
+    const int t0 = box_tb[box], t1 = box_tb[box + 1];
+    double acc = 0.0;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) acc += partial[(size_t)t * nrhs + r];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    if (STEP == 0) {
+        v.dbl(S_PAP)[sys] = sh[0];
+        alpha_step(v, sys);
+    } else {
+        v.dbl(S_TMP)[sys] = sh[0];
+        beta_step(v, sys, delta);
+    }
 }
 
 __global__ void k_add2(double* out, const double* a, const double* b, int n) {
@@ -173,19 +198,17 @@ static dwf_status true_residual(dwf_handle* h, SolverWS& w, SysView v, cudaStrea
 static dwf_status cg_iteration(dwf_handle* h, SolverWS& w, SysView v, dwf_prec pv, dwf_prec po,
                                double delta, cudaStream_t s) {
     const int nrhs = w.nrhs;
-    const int nb = (v.nsys + 127) / 128;
     // t = M_pc p from t1 = (b5 + c5 S5) p, |t|^2 = <p, A p>
     DWF_TRY(op_mpc_pre(h, w.t, w.p, w.tmp3, pv, po, nrhs, w.tmp1, w.tmp2, w.part, s));
-    DWF_TRY(launch_reduce_sys(h, 1, w.part, nrhs, v.dbl(S_PAP), tile_for(h, nrhs), s));
-    k_alpha<<<nb, 128, 0, s>>>(v);
+    const int* box_tb = get_tiles(h, tile_for(h, nrhs)).d_box_tile_begin[1];
+    k_reduce_step<0><<<v.nsys, 256, 0, s>>>(w.part, box_tb, nrhs, v, delta);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     // A p = M_pc^+ t fused with x += alpha p, r -= alpha A p, |r|^2
     void* xv = (pv == DWF_FP64) ? (void*)w.x64 : w.x_lo;
     CgFuse cg{xv, w.r, w.p, v.dbl(S_ALPHA), v.flg(F_RUN)};
     DWF_TRY(op_mpc(h, nullptr, w.t, 1, pv, po, nrhs, w.tmp1, w.tmp2, w.part, &cg, s));
-    DWF_TRY(launch_reduce_sys(h, 1, w.part, nrhs, v.dbl(S_TMP), tile_for(h, nrhs), s));
-    k_beta<<<nb, 128, 0, s>>>(v, delta);
+    k_reduce_step<1><<<v.nsys, 256, 0, s>>>(w.part, box_tb, nrhs, v, delta);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     // p = r + beta p fused with the next iteration's t1 = (b5 + c5 S5) p
@@ -330,7 +353,7 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
     DWF_TRY(restart(true));
 
     // capture K iterations once per workspace
-    // (delta is a kernel argument of the captured k_beta: a new delta re-captures)
+    // (delta is a kernel argument of the captured beta step: a new delta re-captures)
     if (w.graph_exec == nullptr || w.graph_iters != K || w.graph_T != tile_for(h, nrhs) ||
         w.graph_delta != delta) {
         if (w.graph_exec) { cudaGraphExecDestroy(w.graph_exec); w.graph_exec = nullptr; }
