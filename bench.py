@@ -220,7 +220,9 @@ def run_ours(args, rank, world):
     # ---- bare hop (dominant kernel): CUDA events per launch, L2 flushed
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     hop = {}
-    for name, prec, word in (("f32", G.FP32, 4), ("bf16", G.BF16, 2), ("f64", G.FP64, 8)):
+    for name, prec, word in (("f32", G.FP32, 4), ("bf16", G.BF16, 2), ("bf16_tc", G.BF16, 2),
+                             ("f64", G.FP64, 8)):
+        hD.set_hop_kernel(1, 1 if name == "bf16_tc" else 0)
         inp = torch.randn(hD.cb_shape(1), device=dev).to(G._DTYPE[prec])
         out = hD.empty_cb(0, 1, prec)
         for _ in range(3):
@@ -239,6 +241,7 @@ def run_ours(args, rank, world):
         hop[name] = {"ms": ms, "tflops": FLOPS_PER_SITE * sitesD / (ms * 1e-3) / 1e12,
                      "gbs": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
         del inp, out
+    hD.set_hop_kernel(1, 0)
     del flush
 
     peaks = {}
@@ -350,6 +353,8 @@ def run_hop(args):
     if args.hop_config:
         T, vl = args.hop_config
         h.set_tile(nrhs, T, vl)
+    if args.tc:
+        h.set_hop_kernel(nrhs, 1)
     else:
         T = h.autotune(nrhs, prec) if not args.no_autotune else None
     inp = torch.randn(h.cb_shape(1, nrhs), device="cuda").to(G._DTYPE[prec])
@@ -376,7 +381,7 @@ def run_hop(args):
     except (OSError, ValueError, KeyError):
         pass
     print(json.dumps({"kernel": "hop", "lattice": [L] * 4, "Ls": Ls, "nrhs": nrhs, "prec": prec_name,
-                      "tile_sites": T, "config": args.hop_config, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
+                      "tile_sites": T, "config": args.hop_config, "tensor_cores": bool(args.tc), "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
                       "algorithmic_bytes": nbytes}))
 
@@ -452,6 +457,7 @@ def main():
     ap.add_argument("--hop", nargs="+", metavar="ARG",
                     help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tc", action="store_true", help="--hop bf16: the tensor-core kernel")
     ap.add_argument("--hop-config", nargs=2, type=int, metavar=("TILE", "VL"),
                     help="--hop: fixed sites per tile and lanes per thread instead of autotuning")
     ap.add_argument("--gpus", type=int, default=1)

@@ -249,6 +249,17 @@ dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites)
  * (allocates); DWF_ERR_ARG on values out of range. */
 dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_thread);
 
+/* Kernel of the hop with the BF16 operator (BF16 links; operands BF16 or
+ * FP32) for every later call with this nrhs: 0 = FP32 SIMT arithmetic,
+ * 1 = tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+ * per site and mu the colour contraction U h of the +mu and -mu hops for
+ * 8 lanes x 2 spins is one 16 x 16 x 8 MMA, the lower spins a second one.
+ * The projected half spinor is rounded to BF16 (relative ~4e-3, within the
+ * BF16 operator's tolerance).  Sec. 2.1 (the Dirac operator of the solves).
+ * dwf_autotune(prec = DWF_BF16) picks between the two.  DWF_ERR_ARG on
+ * values out of range. */
+dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);

@@ -153,6 +153,16 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
     return DWF_OK;
 }
 
+dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max || (kernel != 0 && kernel != 1)) {
+        set_error("dwf_set_hop_kernel: nrhs in [1, nrhs_max], kernel 0 (SIMT) or 1 (tensor cores)");
+        return DWF_ERR_ARG;
+    }
+    h->tuned_tc[nrhs] = kernel;
+    return DWF_OK;
+}
+
 dwf_status dwf_launch_count(uint64_t* n) {
     if (n == nullptr) {
         set_error("dwf_launch_count: null pointer");

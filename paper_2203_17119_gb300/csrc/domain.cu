@@ -381,6 +381,7 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
     if (st == DWF_OK) st = init_hop_kernels();
     if (st == DWF_OK) st = init_local_kernels();
     if (st == DWF_OK) st = init_local_mat_kernels();
+    if (st == DWF_OK) st = init_hop_tc_kernels();
     if (st == DWF_OK) {
         std::vector<float> mats;
         build_fived_mats(f5, mats);

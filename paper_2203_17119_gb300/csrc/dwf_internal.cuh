@@ -140,6 +140,8 @@ struct dwf_handle {
     std::map<int, int> tuned_T;
     // autotuned lanes per thread of the FP32 hop: nrhs -> VL
     std::map<int, int> tuned_vl;
+    // BF16-operator hop kernel: nrhs -> 0 (SIMT) or 1 (tensor cores)
+    std::map<int, int> tuned_tc;
 };
 
 namespace dwf {
@@ -168,8 +170,11 @@ struct HopCall {
     double* partial;         // EPI_MOO: per tile, per rhs |out|^2 (nullable)
     int T;                   // tile size (0 = tuned/default)
     int VL = 0;              // lanes per thread (FP32 links: 1 or 2; 0 = default)
+    int tc = 0;              // BF16 links: 1 = tensor-core kernel (hop_tc.cu)
 };
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
+dwf_status launch_hop_tc(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s);
+dwf_status init_hop_tc_kernels();
 dwf_status init_hop_kernels();
 dwf_status init_local_kernels();
 dwf_status init_local_mat_kernels();

@@ -611,6 +611,7 @@ dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {
         return launch_f32<float, float, float>(h, c, ts, s);
     }
     // BF16 links: FP32 arithmetic, operands FP32 or BF16
+    if (c.tc) return launch_hop_tc(h, c, ts, s);
     if (c.prec_in == DWF_BF16 && c.prec_out == DWF_BF16) return launch_f32<bf16, bf16, bf16>(h, c, ts, s);
     if (c.prec_in == DWF_BF16 && c.prec_out == DWF_FP32) return launch_f32<bf16, float, bf16>(h, c, ts, s);
     if (c.prec_in == DWF_FP32 && c.prec_out == DWF_BF16) return launch_f32<float, bf16, bf16>(h, c, ts, s);

@@ -49,6 +49,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     if (chain) cudaMemsetAsync(t2 + bytes, 0, bytes, s);
     const auto saved_T = h->tuned_T;
     const auto saved_vl = h->tuned_vl;
+    const auto saved_tc = h->tuned_tc;
     // candidates are timed with L2 flushed (solves stream more than L2 holds)
     const size_t flush_bytes = (size_t)256 << 20;
     void* flush = nullptr;
@@ -57,8 +58,11 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     int best_T = tile_for(h, nrhs);
     int best_vl = 2;
     dwf_status st = DWF_OK;
-    // lanes per thread: FP32 tries both, the others have one kernel
-    const std::vector<int> vls = prec == DWF_FP32 ? std::vector<int>{2, 1} : std::vector<int>{0};
+    // lanes per thread: FP32 tries both; BF16 the SIMT kernel (0) and the
+    // tensor-core one (-1); FP64 has one kernel
+    const std::vector<int> vls = prec == DWF_FP32   ? std::vector<int>{2, 1}
+                                 : prec == DWF_BF16 ? std::vector<int>{0, -1}
+                                                    : std::vector<int>{0};
     for (int vl : vls)
     for (int T : cands) {
         // the tile table is shared by every precision of an operator chain
@@ -73,7 +77,8 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         c.nrhs = nrhs;
         c.scale = 1.0;
         c.T = T;
-        c.VL = vl;
+        c.VL = vl > 0 ? vl : 0;
+        c.tc = vl < 0 ? 1 : 0;
         std::vector<float> ts;
         for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
             cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
@@ -81,6 +86,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
             if (chain) {
                 h->tuned_T[nrhs] = T;
                 if (vl > 0) h->tuned_vl[nrhs] = vl;
+                if (prec == DWF_BF16) h->tuned_tc[nrhs] = vl < 0 ? 1 : 0;
                 st = op_mpc(h, t2 + bytes, t2, 0, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
                 if (st == DWF_OK)
                     st = op_mpc(h, t2, t2 + bytes, 1, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
@@ -105,9 +111,11 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     cudaStreamDestroy(s);
     h->tuned_T = saved_T;
     h->tuned_vl = saved_vl;
+    h->tuned_tc = saved_tc;
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
     if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;
+    if (prec == DWF_BF16) h->tuned_tc[nrhs] = best_vl < 0 ? 1 : 0;
     if (best) *best = best_T;
     return DWF_OK;
 }
@@ -139,6 +147,10 @@ dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int 
     if (link == DWF_FP32) {
         auto it = h->tuned_vl.find(nrhs);
         c.VL = it == h->tuned_vl.end() ? 2 : it->second;
+    }
+    if (link == DWF_BF16) {
+        auto it = h->tuned_tc.find(nrhs);
+        c.tc = it == h->tuned_tc.end() ? 0 : it->second;
     }
     return launch_hop(h, c, s);
 }

@@ -89,6 +89,7 @@ def lib():
             "dwf_launch_count": [C.POINTER(C.c_uint64)],
             "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
             "dwf_set_tile": [vp, i, i, i],
+            "dwf_set_hop_kernel": [vp, i, i],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
@@ -302,6 +303,10 @@ class Handle:
     def set_tile(self, nrhs=1, tile_sites=32, lanes_per_thread=2):
         """Fix the tile size and FP32 hop lanes per thread for this nrhs."""
         _check(lib().dwf_set_tile(self._h, nrhs, tile_sites, lanes_per_thread))
+
+    def set_hop_kernel(self, nrhs=1, kernel=1):
+        """BF16-operator hop for this nrhs: 0 = FP32 SIMT, 1 = tensor cores."""
+        _check(lib().dwf_set_hop_kernel(self._h, nrhs, kernel))
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))

@@ -196,3 +196,33 @@ def test_autotuned_solve_still_exact():
     st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32)
     xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
     assert O.true_residual(U, xf, b, MOBIUS) <= 1e-10
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_tensor_core_hop(case, dagger):
+    """The BF16 operator on the tensor cores (dwf_set_hop_kernel = 1): every
+    hop-based entry point against the FP64 oracle at the BF16 tolerances,
+    and within the BF16 tolerance of the SIMT BF16 kernel."""
+    dims, Ls, prm, boxes, nrhs, U, masks, psi, h = case
+    po = [[O.parity_part(f, 1) for f in row] for row in psi]
+    src1 = LY.to_cb(po, dims, boxes, 1)
+    want_mpc = LY.to_cb([[O.mpc_in(U, f, prm, masks[b], dagger) for f in po[b]]
+                         for b in range(len(po))], dims, boxes, 1)
+    want_eo = LY.to_cb([[O.eo_block_in(U, f, prm, masks[b], 0, dagger) for f in psi[b]]
+                        for b in range(len(psi))], dims, boxes, 0)
+    src_eo = LY.to_cb(psi, dims, boxes, 1)
+    got = {}
+    try:
+        for kern in (1, 0):
+            h.set_hop_kernel(nrhs, kern)
+            out = h.empty_cb(1, nrhs, G.BF16)
+            h.mpc(out, _gpu(src1, G.BF16), dagger, G.BF16, nrhs)
+            eo = h.empty_cb(0, nrhs, G.BF16)
+            h.dslash_eo(eo, _gpu(src_eo, G.BF16), 0, dagger, G.BF16, nrhs)
+            torch.cuda.synchronize()
+            got[kern] = (_host(out), _host(eo))
+    finally:
+        h.set_hop_kernel(nrhs, 0)
+    assert LY.rel_l2(got[1][0], want_mpc) <= TOL_MPC[G.BF16]
+    assert LY.rel_l2(got[1][1], want_eo) <= TOL[G.BF16]
+    assert LY.rel_l2(got[1][0], got[0][0]) <= TOL_MPC[G.BF16]

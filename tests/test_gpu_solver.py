@@ -128,3 +128,21 @@ def test_reliable_update_threshold_is_honoured():
         assert st[0]["status"] == 0 and O.true_residual(U, xf, b, MOBIUS) <= 1e-10
         upd[delta] = st[0]["reliable_updates"]
     assert upd[0.003] < upd[0.3], upd
+
+
+def test_bf16_tensor_core_solve():
+    """Mixed CGNE with the BF16 operator on the tensor cores reaches 1e-10
+    by the oracle (the FP64 reliable updates absorb the BF16 rounding of the
+    projected half spinors)."""
+    dims, Ls = (4, 4, 4, 8), 8
+    rng = np.random.default_rng(43)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    b = inputs.gaussian_source(dims, Ls, rng=rng)
+    h = G.Handle(dims, Ls, G.Action(MOBIUS.M5, MOBIUS.mf, MOBIUS.b5, MOBIUS.c5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.set_hop_kernel(1, 1)
+    bf = torch.view_as_real(torch.from_numpy(LY.to_full([[b]], dims, None))).cuda().contiguous()
+    x = torch.zeros_like(bf)
+    st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.BF16)
+    xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
+    assert st[0]["status"] == 0 and O.true_residual(U, xf, b, MOBIUS) <= 1e-10
