@@ -407,6 +407,15 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         const int* s_nbr_t = reinterpret_cast<const int*>(smem + b * buf_bytes + link_bytes);
         double tile_norm = 0.0;
         for (int sl = sg; sg < G && sl < count; sl += G) {
+            if (EPI == EPI_MOO) {
+                // the M_oo input of this site's lanes, into L1 while the eight
+                // directions run: the epilogue's loads then hit L1 instead of
+                // paying twelve dependent trips to L2 / HBM
+                const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + ((int64_t)(begin + sl) * 12 * N5 + lane0) * 2;
+#pragma unroll
+                for (int c = 0; c < 12; ++c)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(xb + (int64_t)c * N5 * 2));
+            }
             R ar[12][VL], ai[12][VL];
             const Sin* in = reinterpret_cast<const Sin*>(a.in);
             const int* nb = s_nbr_t + sl * 8;

@@ -301,9 +301,17 @@ dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
             DWF_CUDA(cudaMemsetAsync(w.x_lo, 0, no * sv, s));
         }
         DWF_TRY(true_residual(h, w, v, s));
-        DWF_TRY(op_mpc(h, w.t64d, w.t64c, 1, DWF_FP64, DWF_FP64, nrhs, w.t64a, w.t64b, nullptr, nullptr, s));
-        if (pv == DWF_FP64) DWF_CUDA(cudaMemcpyAsync(w.r, w.t64d, no * 16, cudaMemcpyDeviceToDevice, s));
-        else DWF_TRY(launch_convert(w.r, pv, w.t64d, DWF_FP64, no, s));
+        if (pv == DWF_FP64) {
+            DWF_TRY(op_mpc(h, w.t64d, w.t64c, 1, DWF_FP64, DWF_FP64, nrhs, w.t64a, w.t64b, nullptr, nullptr, s));
+            DWF_CUDA(cudaMemcpyAsync(w.r, w.t64d, no * 16, cudaMemcpyDeviceToDevice, s));
+        } else {
+            // r = M_pc^+ res with the FP32 operator: res = b' - M_pc x is exact to
+            // FP64 (it alone decides convergence), and r only restarts the FP32
+            // recursion, whose own rounding is of the same size -- half of the
+            // update's FP64 hops saved.  FP64-sized scratch holds the FP32 fields.
+            DWF_TRY(launch_convert(w.t64d, DWF_FP32, w.t64c, DWF_FP64, no, s));
+            DWF_TRY(op_mpc(h, w.r, w.t64d, 1, DWF_FP32, DWF_FP32, nrhs, w.t64a, w.t64b, nullptr, nullptr, s));
+        }
         DWF_TRY(norm2_sys(h, w, 1, w.r, pv, v.dbl(S_TMP), s));
         // the search direction is kept across an update (Sleijpen & van der
         // Vorst), except with the BF16 operator, whose ~1e-2 rounding breaks
