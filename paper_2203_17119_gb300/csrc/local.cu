@@ -348,10 +348,10 @@ __device__ __forceinline__ void mat_partial(const LocalMatArgs& a, double nrm, d
                      a.partial + (size_t)tile * nr);
 }
 
-template <class Sin, class Sin2, class Sout, class Svec>
-__global__ void __launch_bounds__(256, 4) k_local_sparse(const LocalMatArgs a) {
+template <class Sin, class Sin2, class Sout, class Svec, bool FIXC>
+__global__ void __launch_bounds__(FIXC ? 512 : 256, FIXC ? 2 : 4) k_local_sparse(const LocalMatArgs a) {
     extern __shared__ __align__(16) float smem_f[];
-    __shared__ double s_red[256];
+    __shared__ double s_red[512];
     const int Ls = a.Ls, LsP = a.LsP, nrhs = a.nrhs, N5 = Ls * nrhs, T = blockDim.x;
     const int tid = threadIdx.x;
     const int s = tid % Ls, row0 = tid / Ls, drow = T / Ls;
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256, 4) k_local_sparse(const LocalMatArgs a) {
             for (int j = 0; j < kMatEPT; ++j) {
                 if (tid + j * T >= n) continue;
                 const int row = row0 + j * drow;
-                const int c = (cq + j * dcq) % 12;
+                const int c = FIXC ? cq0 % 12 : (cq + j * dcq) % 12;   // FIXC: fixed per thread
                 const bool down = (c < 6) != (a.dagger != 0);   // S_- (else S_+)
                 const int nb = down ? nb_dn : nb_up;
                 const float tw = down ? tw_dn : tw_up;
@@ -467,10 +467,13 @@ __global__ void __launch_bounds__(256, 4) k_local_sparse(const LocalMatArgs a) {
     }
 }
 
-template <class Sin, class Sout, int LSM>
-__global__ void __launch_bounds__(256, LSM <= 16 ? 3 : 2) k_local_dense(const LocalMatArgs a) {
+// FIXC: the block size is a multiple of 12 Ls nrhs, so a thread's spin-colour
+// row c, hence its chirality, is fixed too and it keeps one matrix row.
+template <class Sin, class Sout, int LSM, bool FIXC>
+__global__ void __launch_bounds__(FIXC ? 512 : 256, FIXC ? 2 : (LSM <= 16 ? 3 : 2))
+    k_local_dense(const LocalMatArgs a) {
     extern __shared__ __align__(16) float smem_f[];
-    __shared__ double s_red[256];
+    __shared__ double s_red[512];
     const int Ls = a.Ls, LsP = a.LsP, nrhs = a.nrhs, N5 = Ls * nrhs, T = blockDim.x;
     const int tid = threadIdx.x;
     const int s = tid % Ls, row0 = tid / Ls, drow = T / Ls;
@@ -479,11 +482,16 @@ __global__ void __launch_bounds__(256, LSM <= 16 ? 3 : 2) k_local_dense(const Lo
     float2* xs = reinterpret_cast<float2*>(smem_f);
     const bool part = a.partial != nullptr;
     const int m = a.op == L_MINV ? 2 : 3;
-    float cm[LSM], cp[LSM];   // this thread's matrix rows, S_- and S_+, scale folded in
+    // this thread's matrix rows, S_- and S_+ (FIXC: only its chirality's), scale folded in
+    constexpr int NROW = FIXC ? 1 : 2;
+    float cf[NROW][LSM];
+    const bool down0 = ((cq0 % 12) < 6) != (a.dagger != 0);   // FIXC: the thread's shift
 #pragma unroll
-    for (int t = 0; t < LSM; ++t) {
-        cm[t] = t < Ls ? a.scale * a.mats[((size_t)m * 2 + 0) * Ls * Ls + s * Ls + t] : 0.f;
-        cp[t] = t < Ls ? a.scale * a.mats[((size_t)m * 2 + 1) * Ls * Ls + s * Ls + t] : 0.f;
+    for (int q = 0; q < NROW; ++q) {
+        const int sh = FIXC ? (down0 ? 0 : 1) : q;
+#pragma unroll
+        for (int t = 0; t < LSM; ++t)
+            cf[q][t] = t < Ls ? a.scale * a.mats[((size_t)m * 2 + sh) * Ls * Ls + s * Ls + t] : 0.f;
     }
     for (int r = tid; r < chunk / Ls; r += T)   // pad column read by the paired loads
         if (LsP != Ls) xs[r * LsP + Ls] = make_float2(0.f, 0.f);
@@ -514,25 +522,25 @@ __global__ void __launch_bounds__(256, LSM <= 16 ? 3 : 2) k_local_dense(const Lo
 #pragma unroll
             for (int j = 0; j < kDenseEPT; ++j) {
                 if (tid + j * T >= n) continue;
-                const int c = (cq + j * dcq) % 12;
-                const bool down = (c < 6) != (a.dagger != 0);
                 const float4* xrow = reinterpret_cast<const float4*>(xs + (row0 + j * drow) * LsP);
                 float yr = 0.f, yi = 0.f;
-                if (down) {
+                const bool down = FIXC ? true : (((cq + j * dcq) % 12) < 6) != (a.dagger != 0);
+                const int q0 = FIXC ? 0 : (down ? 0 : 1);
+                if (FIXC || q0 == 0) {
 #pragma unroll
                     for (int t = 0; t < LSM; t += 2)
                         if (t < Ls) {
                             const float4 q = xrow[t / 2];
-                            yr = fmaf(cm[t], q.x, yr); yi = fmaf(cm[t], q.y, yi);
-                            yr = fmaf(cm[t + 1], q.z, yr); yi = fmaf(cm[t + 1], q.w, yi);
+                            yr = fmaf(cf[0][t], q.x, yr); yi = fmaf(cf[0][t], q.y, yi);
+                            yr = fmaf(cf[0][t + 1], q.z, yr); yi = fmaf(cf[0][t + 1], q.w, yi);
                         }
                 } else {
 #pragma unroll
                     for (int t = 0; t < LSM; t += 2)
                         if (t < Ls) {
                             const float4 q = xrow[t / 2];
-                            yr = fmaf(cp[t], q.x, yr); yi = fmaf(cp[t], q.y, yi);
-                            yr = fmaf(cp[t + 1], q.z, yr); yi = fmaf(cp[t + 1], q.w, yi);
+                            yr = fmaf(cf[NROW - 1][t], q.x, yr); yi = fmaf(cf[NROW - 1][t], q.y, yi);
+                            yr = fmaf(cf[NROW - 1][t + 1], q.z, yr); yi = fmaf(cf[NROW - 1][t + 1], q.w, yi);
                         }
                 }
                 float orr[1] = {yr}, oi[1] = {yi};
@@ -593,29 +601,49 @@ static cudaError_t mat_attr(K kern) {
 }
 
 dwf_status init_local_mat_kernels() {
-    DWF_CUDA(mat_attr(k_local_sparse<float, float, float, float>));
-    DWF_CUDA(mat_attr(k_local_sparse<float, float, bf16, float>));
-    DWF_CUDA(mat_attr(k_local_sparse<bf16, bf16, bf16, float>));
-    DWF_CUDA(mat_attr(k_local_sparse<bf16, bf16, float, float>));
-    DWF_CUDA(mat_attr(k_local_sparse<float, bf16, float, float>));
-    DWF_CUDA(mat_attr(k_local_dense<float, float, 16>));
-    DWF_CUDA(mat_attr(k_local_dense<float, float, 32>));
-    DWF_CUDA(mat_attr(k_local_dense<float, bf16, 16>));
-    DWF_CUDA(mat_attr(k_local_dense<float, bf16, 32>));
-    DWF_CUDA(mat_attr(k_local_dense<bf16, bf16, 16>));
-    DWF_CUDA(mat_attr(k_local_dense<bf16, bf16, 32>));
-    DWF_CUDA(mat_attr(k_local_dense<bf16, float, 16>));
-    DWF_CUDA(mat_attr(k_local_dense<bf16, float, 32>));
+#define DWF_SPARSE_ATTR(A, B, C, D)                         \
+    DWF_CUDA(mat_attr(k_local_sparse<A, B, C, D, false>));  \
+    DWF_CUDA(mat_attr(k_local_sparse<A, B, C, D, true>));
+    DWF_SPARSE_ATTR(float, float, float, float)
+    DWF_SPARSE_ATTR(float, float, bf16, float)
+    DWF_SPARSE_ATTR(bf16, bf16, bf16, float)
+    DWF_SPARSE_ATTR(bf16, bf16, float, float)
+    DWF_SPARSE_ATTR(float, bf16, float, float)
+#undef DWF_SPARSE_ATTR
+#define DWF_DENSE_ATTR(A, B)                                                     \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 12, false>));                          \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 16, false>));                          \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 32, false>));                          \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 12, true>));                           \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 16, true>));                           \
+    DWF_CUDA(mat_attr(k_local_dense<A, B, 32, true>));
+    DWF_DENSE_ATTR(float, float)
+    DWF_DENSE_ATTR(float, bf16)
+    DWF_DENSE_ATTR(bf16, bf16)
+    DWF_DENSE_ATTR(bf16, float)
+#undef DWF_DENSE_ATTR
     return DWF_OK;
 }
 
-// Block size: the largest multiple of lcm(32, Ls * nrhs) up to 256, or -1
-// (then the rows kernel serves).
-static int mat_threads(int N5) {
+// Block size: a multiple of lcm(32, 12 Ls nrhs) up to 512 when one exists
+// (*fixc: every thread keeps one spin-colour row and chirality), else the
+// largest multiple of lcm(32, Ls nrhs) up to 256, or -1 (then the rows
+// kernel serves).
+static int lcm32(int n, int cap) {
     int l = 32;
-    while (l % N5 && l <= 256) l += 32;
-    if (l > 256) return -1;
-    return l * (256 / l);
+    while (l % n && l <= cap) l += 32;
+    return l <= cap ? l : -1;
+}
+
+static int mat_threads(int N5, bool* fixc = nullptr) {
+    const int l12 = lcm32(12 * N5, 512);
+    if (l12 > 0) {
+        if (fixc) *fixc = true;
+        return l12 * std::max(1, 256 / l12);
+    }
+    if (fixc) *fixc = false;
+    const int l = lcm32(N5, 256);
+    return l > 0 ? l * (256 / l) : -1;
 }
 
 static LocalMatArgs mat_args(dwf_handle* h, const LocalCall& c, const TileSet& ts) {
@@ -666,16 +694,22 @@ static dwf_status launch_mat(dwf_handle* h, const LocalCall& c, const TileSet& t
     const int nt = ts.ntiles[c.parity];
     if (nt == 0) return DWF_OK;
     const int Ls = h->p.Ls;
-    const int T = mat_threads(Ls * c.nrhs);
+    bool fixc = false;
+    const int T = mat_threads(Ls * c.nrhs, &fixc);
     const LocalMatArgs a = mat_args(h, c, ts);
     void (*kern)(const LocalMatArgs);
     size_t smem;
     if (c.op == L_MINV || c.op == L_BMINV) {
         smem = (size_t)T * kDenseEPT / Ls * a.LsP * sizeof(float2);
-        kern = Ls <= 16 ? k_local_dense<Sin, Sout, 16> : k_local_dense<Sin, Sout, 32>;
+        if (fixc)
+            kern = Ls <= 12 ? k_local_dense<Sin, Sout, 12, true>
+                 : Ls <= 16 ? k_local_dense<Sin, Sout, 16, true> : k_local_dense<Sin, Sout, 32, true>;
+        else
+            kern = Ls <= 12 ? k_local_dense<Sin, Sout, 12, false>
+                 : Ls <= 16 ? k_local_dense<Sin, Sout, 16, false> : k_local_dense<Sin, Sout, 32, false>;
     } else {
         smem = (size_t)(c.op == L_POST ? 2 : 1) * T * kMatEPT / Ls * a.LsP * sizeof(float2);
-        kern = k_local_sparse<Sin, Sin2, Sout, Svec>;
+        kern = fixc ? k_local_sparse<Sin, Sin2, Sout, Svec, true> : k_local_sparse<Sin, Sin2, Sout, Svec, false>;
     }
     int grid = 0;
     dwf_status st = persistent_grid((const void*)kern, T, smem, nt, &grid);
