@@ -85,30 +85,35 @@ __device__ void beta_step(SysView v, int i, double delta) {
         v.flg(F_NEED)[i] = 1;   // frozen by the next alpha step until the FP64 update
 }
 
-// One block per system: the deterministic sum of its tiles' partials (the
-// same order as k_reduce_sys), then the CG scalar step of that system --
-// STEP 0: <p, A p> and alpha, STEP 1: |r|^2 and beta.
+// One block per system: the deterministic sum of its tiles' partials, then
+// the CG scalar step of that system -- STEP 0: <p, A p> and alpha, STEP 1:
+// |r|^2 and beta.
 template <int STEP>
-__global__ void k_reduce_step(const double* __restrict__ partial, const int* __restrict__ box_tb,
-                              int nrhs, SysView v, double delta) {
-    __shared__ double sh[256];
+__global__ void __launch_bounds__(1024) k_reduce_step(const double* __restrict__ partial,
+                                                      const int* __restrict__ box_tb, int nrhs,
+                                                      SysView v, double delta) {
+    __shared__ double sh[32];
     const int sys = blockIdx.x;
     const int box = sys / nrhs, r = sys % nrhs;
     const int t0 = box_tb[box], t1 = box_tb[box + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fixed association: thread-strided sums, then warp and block shuffle trees
     double acc = 0.0;
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) acc += partial[(size_t)t * nrhs + r];
-    sh[threadIdx.x] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) sh[warp] = acc;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
+    if (warp != 0) return;
+    acc = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane != 0) return;
     if (STEP == 0) {
-        v.dbl(S_PAP)[sys] = sh[0];
+        v.dbl(S_PAP)[sys] = acc;
         alpha_step(v, sys);
     } else {
-        v.dbl(S_TMP)[sys] = sh[0];
+        v.dbl(S_TMP)[sys] = acc;
         beta_step(v, sys, delta);
     }
 }
@@ -201,14 +206,14 @@ static dwf_status cg_iteration(dwf_handle* h, SolverWS& w, SysView v, dwf_prec p
     // t = M_pc p from t1 = (b5 + c5 S5) p, |t|^2 = <p, A p>
     DWF_TRY(op_mpc_pre(h, w.t, w.p, w.tmp3, pv, po, nrhs, w.tmp1, w.tmp2, w.part, s));
     const int* box_tb = get_tiles(h, tile_for(h, nrhs)).d_box_tile_begin[1];
-    k_reduce_step<0><<<v.nsys, 256, 0, s>>>(w.part, box_tb, nrhs, v, delta);
+    k_reduce_step<0><<<v.nsys, 1024, 0, s>>>(w.part, box_tb, nrhs, v, delta);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     // A p = M_pc^+ t fused with x += alpha p, r -= alpha A p, |r|^2
     void* xv = (pv == DWF_FP64) ? (void*)w.x64 : w.x_lo;
     CgFuse cg{xv, w.r, w.p, v.dbl(S_ALPHA), v.flg(F_RUN)};
     DWF_TRY(op_mpc(h, nullptr, w.t, 1, pv, po, nrhs, w.tmp1, w.tmp2, w.part, &cg, s));
-    k_reduce_step<1><<<v.nsys, 256, 0, s>>>(w.part, box_tb, nrhs, v, delta);
+    k_reduce_step<1><<<v.nsys, 1024, 0, s>>>(w.part, box_tb, nrhs, v, delta);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     // p = r + beta p fused with the next iteration's t1 = (b5 + c5 S5) p
