@@ -260,6 +260,14 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
  * values out of range. */
 dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel);
 
+/* Tile order of the hop for every later call with this nrhs: each CTA of
+ * the persistent grid takes `chunk` consecutive tiles (neighbouring lattice
+ * rows, whose y-neighbour spinors it then re-reads from L1) before striding
+ * by the grid; 1 = plain striding.  Larger chunks trade L1 reuse against the
+ * load balance of the last round.  dwf_autotune picks 1 or 8.  Same results.
+ * DWF_ERR_ARG unless 1 <= chunk <= 64. */
+dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);

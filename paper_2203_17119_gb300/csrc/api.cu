@@ -163,6 +163,16 @@ dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel) {
     return DWF_OK;
 }
 
+dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max || chunk < 1 || chunk > 64) {
+        set_error("dwf_set_hop_chunk: nrhs in [1, nrhs_max], chunk in [1, 64]");
+        return DWF_ERR_ARG;
+    }
+    h->tuned_chunk[nrhs] = chunk;
+    return DWF_OK;
+}
+
 dwf_status dwf_launch_count(uint64_t* n) {
     if (n == nullptr) {
         set_error("dwf_launch_count: null pointer");

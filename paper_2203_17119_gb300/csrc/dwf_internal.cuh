@@ -142,6 +142,8 @@ struct dwf_handle {
     std::map<int, int> tuned_vl;
     // BF16-operator hop kernel: nrhs -> 0 (SIMT) or 1 (tensor cores)
     std::map<int, int> tuned_tc;
+    // hop tile order: nrhs -> consecutive tiles per CTA before striding by the grid
+    std::map<int, int> tuned_chunk;
 };
 
 namespace dwf {
@@ -171,6 +173,7 @@ struct HopCall {
     int T;                   // tile size (0 = tuned/default)
     int VL = 0;              // lanes per thread (FP32 links: 1 or 2; 0 = default)
     int tc = 0;              // BF16 links: 1 = tensor-core kernel (hop_tc.cu)
+    int chunk = 0;           // consecutive tiles per CTA before striding (0 = 1)
 };
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
 dwf_status launch_hop_tc(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s);

@@ -35,6 +35,8 @@ struct HopArgs {
     const int* nbr;      // [site][8]
     const int4* tiles;
     int T, N5, Ls, nrhs, ntiles;
+    int chunk;           // consecutive tiles a CTA takes before striding: neighbouring rows of
+                         // the lattice on one SM, so y-neighbours are re-read from L1
     double scale, d, e, mf;
     double* partial;
     int* err;
@@ -360,6 +362,9 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     double* s_red = reinterpret_cast<double*>(bar + 3);       // [2][nwarps][nrhs]
     const int nt = a.ntiles;
     const int nwarps = (int)(blockDim.x >> 5), warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // k-th tile of this CTA: chunks of `chunk` consecutive tiles, strided by the grid
+    const int ck = a.chunk;
+    auto tile_of = [&](int k) { return ((k / ck) * (int)gridDim.x + (int)blockIdx.x) * ck + k % ck; };
 
     auto issue = [&](int tile, int b) {
         const int4 t = a.tiles[tile];
@@ -378,8 +383,8 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         mbar_init(&bar[1], 1);
         done[0] = done[1] = 0;
         fence_mbar_init();
-        if ((int)blockIdx.x < nt) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < nt) issue(blockIdx.x + gridDim.x, 1);
+        if (tile_of(0) < nt) issue(tile_of(0), 0);
+        if (tile_of(1) < nt) issue(tile_of(1), 1);
     }
     __syncthreads();
 
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const bool part = EPI == EPI_MOO && a.partial != nullptr;
 
     int k = 0;
-    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x, ++k) {
+    for (int tile = tile_of(0); tile < nt; tile = tile_of(++k)) {
         const int b = k & 1;
         const uint32_t ph = (uint32_t)((k >> 1) & 1);
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], ph))) {
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                         a.partial[(size_t)tile * a.nrhs + r] = sum;
                     }
                 done[b] = 0;
-                const int next2 = tile + 2 * (int)gridDim.x;
+                const int next2 = tile_of(k + 2);
                 if (next2 < nt) issue(next2, b);
             }
         }
@@ -504,6 +509,7 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     a.mf = h->p.mf;
     a.partial = c.partial;
     a.err = h->d_err;
+    a.chunk = c.chunk > 0 ? c.chunk : 1;
     const int TPS = a.N5 / VL;
     // site groups per CTA: as many as fit in 256 threads, at most T
     int groups = 256 / TPS;

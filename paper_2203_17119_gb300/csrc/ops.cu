@@ -50,6 +50,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     const auto saved_T = h->tuned_T;
     const auto saved_vl = h->tuned_vl;
     const auto saved_tc = h->tuned_tc;
+    const auto saved_chunk = h->tuned_chunk;
     // candidates are timed with L2 flushed (solves stream more than L2 holds)
     const size_t flush_bytes = (size_t)256 << 20;
     void* flush = nullptr;
@@ -63,6 +64,9 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     const std::vector<int> vls = prec == DWF_FP32   ? std::vector<int>{2, 1}
                                  : prec == DWF_BF16 ? std::vector<int>{0, -1}
                                                     : std::vector<int>{0};
+    const int chunks[] = {1, 8};
+    int best_chunk = 1;
+    for (int ck : chunks)
     for (int vl : vls)
     for (int T : cands) {
         // the tile table is shared by every precision of an operator chain
@@ -79,12 +83,14 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         c.T = T;
         c.VL = vl > 0 ? vl : 0;
         c.tc = vl < 0 ? 1 : 0;
+        c.chunk = ck;
         std::vector<float> ts;
         for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
             cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
             if (chain) {
                 h->tuned_T[nrhs] = T;
+                h->tuned_chunk[nrhs] = ck;
                 if (vl > 0) h->tuned_vl[nrhs] = vl;
                 if (prec == DWF_BF16) h->tuned_tc[nrhs] = vl < 0 ? 1 : 0;
                 st = op_mpc(h, t2 + bytes, t2, 0, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
@@ -102,7 +108,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         if (st != DWF_OK) break;
         std::sort(ts.begin(), ts.end());
         const float med = ts[ts.size() / 2];
-        if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; }
+        if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; best_chunk = ck; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -112,8 +118,10 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     h->tuned_T = saved_T;
     h->tuned_vl = saved_vl;
     h->tuned_tc = saved_tc;
+    h->tuned_chunk = saved_chunk;
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
+    h->tuned_chunk[nrhs] = best_chunk;
     if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;
     if (prec == DWF_BF16) h->tuned_tc[nrhs] = best_vl < 0 ? 1 : 0;
     if (best) *best = best_T;
@@ -151,6 +159,10 @@ dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int 
     if (link == DWF_BF16) {
         auto it = h->tuned_tc.find(nrhs);
         c.tc = it == h->tuned_tc.end() ? 0 : it->second;
+    }
+    {
+        auto it = h->tuned_chunk.find(nrhs);
+        c.chunk = it == h->tuned_chunk.end() ? 1 : it->second;
     }
     return launch_hop(h, c, s);
 }

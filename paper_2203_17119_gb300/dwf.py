@@ -90,6 +90,7 @@ def lib():
             "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
             "dwf_set_tile": [vp, i, i, i],
             "dwf_set_hop_kernel": [vp, i, i],
+            "dwf_set_hop_chunk": [vp, i, i],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
@@ -307,6 +308,10 @@ class Handle:
     def set_hop_kernel(self, nrhs=1, kernel=1):
         """BF16-operator hop for this nrhs: 0 = FP32 SIMT, 1 = tensor cores."""
         _check(lib().dwf_set_hop_kernel(self._h, nrhs, kernel))
+
+    def set_hop_chunk(self, nrhs=1, chunk=1):
+        """Consecutive tiles per CTA of the hop before striding by the grid."""
+        _check(lib().dwf_set_hop_chunk(self._h, nrhs, chunk))
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))

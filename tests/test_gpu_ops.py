@@ -158,12 +158,14 @@ def test_pack_unpack_layout(case, prec):
     assert LY.rel_l2(got, canon) <= TOL[prec]
 
 
-@pytest.mark.parametrize("tile,vl", [(4, 1), (8, 2), (48, 1), (64, 2)])
-def test_tile_and_lane_variants(tile, vl):
-    """Every (tile size, lanes per thread) choice the autotuner can make gives
-    the same operator: hop-based dslash_eo and M_pc in FP32 and FP64."""
+@pytest.mark.parametrize("tile,vl,chunk", [(4, 1, 1), (8, 2, 1), (48, 1, 1), (64, 2, 1),
+                                            (4, 2, 8), (8, 1, 3)])
+def test_tile_and_lane_variants(tile, vl, chunk):
+    """Every (tile size, lanes per thread, tile order) choice the autotuner can
+    make gives the same operator: hop-based dslash_eo and M_pc in FP32 and FP64."""
     dims, Ls, prm, boxes, nrhs, U, masks, psi, h = _setup("mobius_boxes_odd_wrap")
     h.set_tile(nrhs, tile, vl)
+    h.set_hop_chunk(nrhs, chunk)
     po = [[O.parity_part(f, 1) for f in row] for row in psi]
     src = LY.to_cb(po, dims, boxes, 1)
     want = LY.to_cb([[O.mpc_in(U, f, prm, masks[b]) for f in po[b]] for b in range(len(po))],
