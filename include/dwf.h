@@ -272,6 +272,32 @@ dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk);
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);
 
+/* Multi-shift CG: for every shift sigma_s >= 0 solve
+ * (M_pc^+ M_pc + sigma_s) x_s = b on the odd checkerboard of every box and
+ * right-hand side, all shifts from one Krylov space (CG on the smallest
+ * shift, the shifted systems by the published collinear-residual
+ * recurrences).  These are the rational functions of the normal operators of
+ * D and D_Omega in the DD-RHMC action (Sec. 2.3.1): sum_s a_s x_s.
+ * x: device, nshift odd cb FP64 fields back to back, in the order of `shifts`
+ *    (written; the initial contents are ignored).
+ * b: device odd cb FP64 field (nrhs right-hand sides per box).
+ * shifts: host array of nshift finite values >= 0, any order.
+ * sp: tol (per shift and system, relative to |b|), maxiter, max_seconds and
+ *     inner_prec = DWF_FP64 (FP64 operator) or DWF_FP32 (FP32 operator with
+ *     FP64 vectors and scalars to 1e-6, then, for tol < 1e-6, rounds of
+ *     defect correction per shift: the FP64 residual b - (A + sigma_s) x_s,
+ *     a single-shift FP32 solve of it to 1e-6, x_s += correction;
+ *     stats.reliable_updates counts the rounds); the other fields are
+ *     ignored.
+ * stats: host [nshift][nbox * nrhs]; true_resid = |b - (A + sigma_s) x_s| / |b|
+ *     recomputed with the FP64 operator.
+ * Allocates its workspace for the call.  Returns the first non-OK status
+ * (DWF_ERR_NOT_CONVERGED, DWF_ERR_TIMEOUT, DWF_ERR_NAN) with x the last
+ * iterate; DWF_ERR_ARG on bad arguments. */
+dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
+                                int nshift, int nrhs, const dwf_solver_params* sp,
+                                dwf_solver_stats* stats, void* stream);
+
 /* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
  * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
  * itself stalls for Moebius DWF, whose Schur operator has the origin in its

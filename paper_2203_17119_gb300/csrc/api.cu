@@ -252,6 +252,13 @@ dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dw
     return gcr_solve(h, x, b, nrhs, K, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
+                                int nshift, int nrhs, const dwf_solver_params* sp,
+                                dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    return multishift_solve(h, x, b, shifts, nshift, nrhs, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_check_device(dwf_handle* h) {
     DWF_TRY(check_handle(h));
     int e = 0;

@@ -183,6 +183,9 @@ dwf_status init_local_kernels();
 dwf_status init_local_mat_kernels();
 void build_fived_mats(const FiveD& f, std::vector<float>& out);
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
+dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
+                            int nshift, int nrhs, const dwf_solver_params* sp,
+                            dwf_solver_stats* stats, cudaStream_t s);
 
 struct LocalCall {
     LocalOp op;

@@ -93,6 +93,8 @@ def lib():
             "dwf_set_hop_chunk": [vp, i, i],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+            "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
+                                     C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
             "dwf_nn_destroy": [vp],
             "dwf_nn_set_weights": [vp, vp, C.c_size_t],
@@ -300,6 +302,22 @@ class Handle:
         if not allow_fail:
             _check(rc)
         return [s.as_dict() for s in st], rc
+
+    def multishift_solve(self, x, b, shifts, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64,
+                         max_seconds=0.0, stream=None, allow_fail=False):
+        """(M_pc^+ M_pc + sigma_s) x_s = b for every shift: ``b`` an odd cb FP64
+        field, ``x`` a FP64 tensor of shape (len(shifts), *cb_shape(1, nrhs)).
+        Returns ([per shift: [per system: stats dict]], status)."""
+        sh = (C.c_double * len(shifts))(*[float(v) for v in shifts])
+        sp = SolverParams(tol, maxiter, 0.0, 0, 0, inner, max_seconds, 0, None, 0, 0)
+        nsys = max(len(self.boxes), 1) * nrhs
+        st = (SolverStats * (nsys * len(shifts)))()
+        rc = lib().dwf_multishift_solve(self._h, _ptr(x), _ptr(b), sh, len(shifts), nrhs,
+                                        C.byref(sp), st, _stream(stream))
+        if not allow_fail:
+            _check(rc)
+        d = [s.as_dict() for s in st]
+        return [d[k * nsys:(k + 1) * nsys] for k in range(len(shifts))], rc
 
     def set_tile(self, nrhs=1, tile_sites=32, lanes_per_thread=2):
         """Fix the tile size and FP32 hop lanes per thread for this nrhs."""
