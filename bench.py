@@ -129,7 +129,14 @@ def run_ours(args, rank, world):
     o, e = BAND_BOX
     sub = src[o[3]:o[3] + e[3], o[2]:o[2] + e[2], o[1]:o[1] + e[1], o[0]:o[0] + e[0]]
     canonO = torch.from_numpy(np.ascontiguousarray(sub).reshape(-1)).to(dev)
-    tiles = {"D": hD.autotune(1, G.FP32), "D_Omega": hO.autotune(1, G.FP32)}
+    if args.config:   # a fixed kernel configuration (e.g. to replay a tuned run under a profiler)
+        for hh in (hD, hO):
+            hh.set_tile(1, args.config[0], args.config[1])
+            hh.set_hop_chunk(1, args.config[2])
+    else:
+        hD.autotune(1, G.FP32)
+        hO.autotune(1, G.FP32)
+    tiles = {"D": list(hD.tuning(1)[:3]), "D_Omega": list(hO.tuning(1)[:3])}
     bD, bO = hD.pack(canonD), hO.pack(canonO)
     xD, xO = torch.zeros_like(bD), torch.zeros_like(bO)
     sitesD = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
@@ -310,7 +317,7 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS,
                    "inner": "FP32 operator + FP32 vectors; FP64 reliable updates/reductions/x",
                    "l2": "working set > L2 (FP64 + FP32 solver state ~0.6 GB per solve)",
-                   "parallelism": f"replicas x{world}", "autotuned_tile_sites": tiles},
+                   "parallelism": f"replicas x{world}", "tile_sites_lanes_chunk": tiles},
         "time_to_solution_ms": {k: round(v, 3) for k, v in mixed_ms.items()},
         "iters": {"D": last[0]["iters"], "D_Omega": last[1]["iters"]},
         "reliable_updates": {"D": last[0]["reliable_updates"], "D_Omega": last[1]["reliable_updates"]},
@@ -551,6 +558,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-big-hop", action="store_true", help="skip the 32^4 x 16 hop line")
+    ap.add_argument("--config", nargs=3, type=int, metavar=("TILE", "VL", "CHUNK"),
+                    help="default workload: fixed kernel configuration instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

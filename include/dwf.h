@@ -268,6 +268,12 @@ dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel);
  * DWF_ERR_ARG unless 1 <= chunk <= 64. */
 dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk);
 
+/* The kernel configuration later calls with this nrhs use (set by
+ * dwf_autotune or the dwf_set_* calls; defaults 32 sites, 2 lanes, chunk 1,
+ * SIMT): any output pointer may be NULL.  DWF_ERR_ARG on a bad nrhs. */
+dwf_status dwf_get_tuning(const dwf_handle* h, int nrhs, int* tile_sites, int* lanes_per_thread,
+                          int* chunk, int* tensor_cores);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);

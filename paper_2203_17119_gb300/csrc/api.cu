@@ -4,6 +4,8 @@
 #include <cstdio>
 
 #include "dev_common.cuh"
+#include <map>
+
 #include "dwf_internal.cuh"
 
 namespace dwf {
@@ -170,6 +172,24 @@ dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk) {
         return DWF_ERR_ARG;
     }
     h->tuned_chunk[nrhs] = chunk;
+    return DWF_OK;
+}
+
+dwf_status dwf_get_tuning(const dwf_handle* h, int nrhs, int* tile_sites, int* lanes_per_thread,
+                          int* chunk, int* tensor_cores) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("dwf_get_tuning: nrhs in [1, nrhs_max]");
+        return DWF_ERR_ARG;
+    }
+    auto get = [&](const std::map<int, int>& m, int dflt) {
+        auto it = m.find(nrhs);
+        return it == m.end() ? dflt : it->second;
+    };
+    if (tile_sites) *tile_sites = get(h->tuned_T, 32);
+    if (lanes_per_thread) *lanes_per_thread = get(h->tuned_vl, 2);
+    if (chunk) *chunk = get(h->tuned_chunk, 1);
+    if (tensor_cores) *tensor_cores = get(h->tuned_tc, 0);
     return DWF_OK;
 }
 

@@ -66,9 +66,18 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
                                                     : std::vector<int>{0};
     const int chunks[] = {1, 8};
     int best_chunk = 1;
+    int n_sm = 152;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
     for (int ck : chunks)
     for (int vl : vls)
     for (int T : cands) {
+        // chunked tile order only with >= 4 chunks per resident CTA (two per SM):
+        // fewer leave the last round unbalanced, by more than L1 reuse gains
+        if (ck > 1 && (h->nsite[0] / T) / ck < 4 * 2 * n_sm) continue;
         // the tile table is shared by every precision of an operator chain
         // (FP64 reliable updates included): size the check for FP64 links
         const size_t smem = hop_smem(T, 8, 8, nrhs);

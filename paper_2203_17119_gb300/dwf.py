@@ -91,6 +91,8 @@ def lib():
             "dwf_set_tile": [vp, i, i, i],
             "dwf_set_hop_kernel": [vp, i, i],
             "dwf_set_hop_chunk": [vp, i, i],
+            "dwf_get_tuning": [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int)],
             "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
@@ -330,6 +332,12 @@ class Handle:
     def set_hop_chunk(self, nrhs=1, chunk=1):
         """Consecutive tiles per CTA of the hop before striding by the grid."""
         _check(lib().dwf_set_hop_chunk(self._h, nrhs, chunk))
+
+    def tuning(self, nrhs=1):
+        """(tile sites, lanes per thread, chunk, tensor cores) used for this nrhs."""
+        v = [C.c_int() for _ in range(4)]
+        _check(lib().dwf_get_tuning(self._h, nrhs, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))
