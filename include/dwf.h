@@ -304,6 +304,30 @@ dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const
                                 int nshift, int nrhs, const dwf_solver_params* sp,
                                 dwf_solver_stats* stats, void* stream);
 
+/* Luescher's projector of Sec. 2.1 onto the spinor components of Omega on
+ * which the hops from Omega into Omega-bar act (the row space of the block
+ * D_partialbar of D): out = P in on the sites of the box `omega`, zero
+ * elsewhere.  Per site P is the projector onto the span of
+ * (b5 + c5 S5^+) [(1 +- gamma_mu) spinors x all s] over the neighbours
+ * x +- mu outside Omega, colour-blind (built on the host in FP64 per
+ * pattern of outside neighbours).  h: a whole-lattice handle; in, out:
+ * distinct device full FP64 fields, nrhs right-hand sides.
+ * DWF_ERR_UNSUPPORTED if a site outside Omega touches two sites of Omega
+ * (then P is not site-local: use a band of width >= 2). */
+dwf_status dwf_boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
+                                int nrhs, void* stream);
+
+/* R^-1 = P - P D^-1 D_partialbar (Sec. 2.1), the inverse of the boundary
+ * operator R = P - P D_Omega^-1 D_partial D_Omega-bar^-1 D_partialbar on the
+ * range of P, which carries the DD-HMC pseudofermion of det chi = det R:
+ * out = u - P D^-1 (D u restricted to Omega-bar), u = P in.  D^-1 by
+ * dwf_cgne_solve with `sp` (stats: nrhs entries of that solve).  Same
+ * handle, field and Omega rules as dwf_boundary_project; allocates three
+ * full FP64 fields for the call. */
+dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
+                             int nrhs, const dwf_solver_params* sp, dwf_solver_stats* stats,
+                             void* stream);
+
 /* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
  * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
  * itself stalls for Moebius DWF, whose Schur operator has the origin in its

@@ -279,6 +279,19 @@ dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const
     return multishift_solve(h, x, b, shifts, nshift, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
+                                int nrhs, void* stream) {
+    DWF_TRY(check_handle(h));
+    return boundary_project(h, omega, out, in, nrhs, (cudaStream_t)stream);
+}
+
+dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
+                             int nrhs, const dwf_solver_params* sp, dwf_solver_stats* stats,
+                             void* stream) {
+    DWF_TRY(check_handle(h));
+    return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_check_device(dwf_handle* h) {
     DWF_TRY(check_handle(h));
     int e = 0;

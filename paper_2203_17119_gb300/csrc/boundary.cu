@@ -1,0 +1,358 @@
+// The boundary operator of Sec. 2.1 and the inverse the DD-HMC pseudofermion
+// action uses:
+//
+//   R^-1 = P - P D^-1 D_partialbar,
+//
+// on the space projected by P (Luescher's projector): the spinor components of
+// Omega on which D_partialbar, the hops from Omega to Omega-bar, act.  P is the
+// orthogonal projector onto the row space of D_partialbar.  D_partialbar's
+// column block at a site x of Omega is a sum of terms
+// -1/2 (1 -+ gamma_mu) U (b5 + c5 S5) over the neighbours of x outside Omega
+// ((1 - gamma_mu) for x - mu, (1 + gamma_mu) for x + mu), so its row space is
+// colour-blind and, in the (spin, s) space of the site, the span of
+// B^+ [range(1 -+ gamma_mu) x C^Ls] over those neighbours, B^+ = b5 + c5 S5^+.
+// It depends on the site only through which neighbours leave Omega: one
+// 4 Ls x 4 Ls projector per crossing pattern, built on the host in FP64
+// (Gram-Schmidt of those columns), one pattern index per site.
+//
+// R^-1 psi: u = P psi, v = D u restricted to Omega-bar (= D_partialbar u),
+// y = D^-1 v (the mixed-precision CGNE of the whole lattice), out = u - P y.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+namespace {
+
+using cd = std::complex<double>;
+
+// Chiral-basis gamma_mu (mu = 0..3 <-> x..t), 4 x 4 row-major.
+std::array<cd, 16> gamma_mu(int mu) {
+    std::array<cd, 16> g{};
+    const cd I(0, 1);
+    // sigma_1, sigma_2, sigma_3
+    const cd sig[3][4] = {{0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            cd up, lo;
+            if (mu < 3) {
+                up = -I * sig[mu][r * 2 + c];
+                lo = I * sig[mu][r * 2 + c];
+            } else {
+                up = lo = (r == c) ? 1.0 : 0.0;
+            }
+            g[r * 4 + (c + 2)] = up;   // upper right block
+            g[(r + 2) * 4 + c] = lo;   // lower left block
+        }
+    return g;
+}
+
+// Projector (4 Ls x 4 Ls, row-major, index spin * Ls + s) onto the span of
+// B^+ [range(1 + sgn gamma_mu) x C^Ls] over the crossings of `mask` (bit k:
+// neighbour k = mu (+mu) or 4 + mu (-mu) lies outside Omega).
+std::vector<cd> pattern_projector(int mask, int Ls, double b5, double c5, double mf) {
+    const int n = 4 * Ls;
+    // B^+ = b5 + c5 (P_+ S_+ + P_- S_-) on (spin, s): upper spins shift s+1, lower s-1
+    auto Bdag = [&](const std::vector<cd>& v) {
+        std::vector<cd> w(n);
+        for (int sp = 0; sp < 4; ++sp)
+            for (int s = 0; s < Ls; ++s) {
+                cd sh;
+                if (sp < 2) sh = s < Ls - 1 ? v[sp * Ls + s + 1] : -mf * v[sp * Ls + 0];
+                else sh = s > 0 ? v[sp * Ls + s - 1] : -mf * v[sp * Ls + Ls - 1];
+                w[sp * Ls + s] = b5 * v[sp * Ls + s] + c5 * sh;
+            }
+        return w;
+    };
+    std::vector<std::vector<cd>> Q;
+    for (int k = 0; k < 8; ++k) {
+        if (!(mask >> k & 1)) continue;
+        const int mu = k & 3;
+        const double sgn = k < 4 ? 1.0 : -1.0;   // x + mu: (1 + gamma), x - mu: (1 - gamma)
+        const auto g = gamma_mu(mu);
+        for (int col = 0; col < 4; ++col)
+            for (int s = 0; s < Ls; ++s) {
+                std::vector<cd> v(n, 0.0);
+                for (int sp = 0; sp < 4; ++sp) v[sp * Ls + s] = (sp == col ? 1.0 : 0.0) + sgn * g[sp * 4 + col];
+                std::vector<cd> w = Bdag(v);
+                // modified Gram-Schmidt, twice for stability
+                for (int pass = 0; pass < 2; ++pass)
+                    for (const auto& q : Q) {
+                        cd dot = 0;
+                        for (int i = 0; i < n; ++i) dot += std::conj(q[i]) * w[i];
+                        for (int i = 0; i < n; ++i) w[i] -= dot * q[i];
+                    }
+                double nn = 0;
+                for (int i = 0; i < n; ++i) nn += std::norm(w[i]);
+                nn = std::sqrt(nn);
+                if (nn > 1e-10 * (std::fabs(b5) + std::fabs(c5) + 1.0)) {
+                    for (int i = 0; i < n; ++i) w[i] /= nn;
+                    Q.push_back(w);
+                }
+            }
+    }
+    std::vector<cd> P((size_t)n * n, 0.0);
+    for (const auto& q : Q)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) P[(size_t)i * n + j] += q[i] * std::conj(q[j]);
+    return P;
+}
+
+// out = P_pat(site) in on Omega's sites (pat >= 0), 0 elsewhere (pat < 0);
+// in / out full fields [parity block][site][12][N5] complex (FP64).
+__global__ void k_boundary_project(const double2* __restrict__ in, double2* __restrict__ out,
+                                   const int* __restrict__ pat, const double2* __restrict__ P,
+                                   int64_t nsites, int Ls, int nrhs) {
+    const int n4 = 4 * Ls, N5 = Ls * nrhs;
+    const int64_t total = nsites * 3 * nrhs * n4;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(id % n4);                 // spin * Ls + s
+        const int64_t rest = id / n4;
+        const int r = (int)(rest % nrhs);
+        const int colour = (int)((rest / nrhs) % 3);
+        const int64_t site = rest / (nrhs * 3);
+        const int sp = row / Ls, s = row % Ls;
+        const int p = pat[site];
+        double2 acc = make_double2(0.0, 0.0);
+        if (p >= 0) {
+            const double2* Pr = P + ((size_t)p * n4 + row) * n4;
+            const double2* src = in + site * 12 * N5;
+            for (int j = 0; j < n4; ++j) {
+                const int sj = j / Ls, tj = j % Ls;
+                const double2 a = Pr[j];
+                const double2 v = src[(sj * 3 + colour) * N5 + r * Ls + tj];
+                acc.x += a.x * v.x - a.y * v.y;
+                acc.y += a.x * v.y + a.y * v.x;
+            }
+        }
+        out[site * 12 * N5 + (sp * 3 + colour) * N5 + r * Ls + s] = acc;
+    }
+}
+
+// zero the sites whose flag equals `drop` (flag: 1 in Omega, 0 outside)
+__global__ void k_mask(double2* __restrict__ f, const int* __restrict__ in_omega, int64_t nsites,
+                       int per_site, int drop) {
+    const int64_t total = nsites * per_site;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x)
+        if (in_omega[id / per_site] == drop) f[id] = make_double2(0.0, 0.0);
+}
+
+// out = a - out
+__global__ void k_rsub(double2* __restrict__ out, const double2* __restrict__ a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 o = out[i], x = a[i];
+        out[i] = make_double2(x.x - o.x, x.y - o.y);
+    }
+}
+
+struct BoundaryTables {
+    std::vector<int> pat, in_omega;   // per full-field site (parity 0 block, then parity 1)
+    std::vector<cd> P;                 // [npat][4Ls][4Ls]
+    int npat = 0;
+};
+
+dwf_status build_tables(const dwf_handle* h, const dwf_box& om, BoundaryTables& tb) {
+    const int* L = h->p.dims;
+    for (int mu = 0; mu < 4; ++mu)
+        if (om.extent[mu] < 1 || om.extent[mu] > L[mu]) {
+            set_error("boundary: Omega extent out of range");
+            return DWF_ERR_ARG;
+        }
+    auto inside = [&](const int* x) {
+        for (int mu = 0; mu < 4; ++mu) {
+            const int d = ((x[mu] - om.origin[mu]) % L[mu] + L[mu]) % L[mu];
+            if (d >= om.extent[mu]) return false;
+        }
+        return true;
+    };
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    std::map<int, int> masks;
+    std::vector<int> site_mask;
+    // full-field site order: parity 0 sites in lexicographic order, then parity 1
+    for (int q = 0; q < 2; ++q)
+        for (int64_t l = 0; l < V; ++l) {
+            int x[4] = {(int)(l % L[0]), (int)((l / L[0]) % L[1]), (int)((l / ((int64_t)L[0] * L[1])) % L[2]),
+                        (int)(l / ((int64_t)L[0] * L[1] * L[2]))};
+            if (((x[0] + x[1] + x[2] + x[3]) & 1) != q) continue;
+            if (!inside(x)) {
+                tb.in_omega.push_back(0);
+                site_mask.push_back(-1);
+                continue;
+            }
+            int m = 0;
+            for (int k = 0; k < 8; ++k) {
+                int y[4] = {x[0], x[1], x[2], x[3]};
+                const int mu = k & 3;
+                y[mu] = (y[mu] + (k < 4 ? 1 : -1) + L[mu]) % L[mu];
+                if (!inside(y)) m |= 1 << k;
+            }
+            tb.in_omega.push_back(1);
+            site_mask.push_back(m);
+            if (m && !masks.count(m)) {
+                const int id = (int)masks.size();
+                masks[m] = id;
+            }
+        }
+    // P is the direct sum of the per-site projectors only when no site of
+    // Omega-bar touches two sites of Omega (a convex box, band width >= 2)
+    for (int64_t l = 0; l < V; ++l) {
+        int x[4] = {(int)(l % L[0]), (int)((l / L[0]) % L[1]), (int)((l / ((int64_t)L[0] * L[1])) % L[2]),
+                    (int)(l / ((int64_t)L[0] * L[1] * L[2]))};
+        if (inside(x)) continue;
+        int cnt = 0;
+        for (int k = 0; k < 8; ++k) {
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            const int mu = k & 3;
+            y[mu] = (y[mu] + (k < 4 ? 1 : -1) + L[mu]) % L[mu];
+            if (inside(y)) ++cnt;
+        }
+        if (cnt > 1) {
+            set_error("boundary: a site outside Omega touches %d sites of Omega (the projector is "
+                      "site-local only for a band of width >= 2 around a box)", cnt);
+            return DWF_ERR_UNSUPPORTED;
+        }
+    }
+    tb.npat = (int)masks.size();
+    const int n4 = 4 * h->p.Ls;
+    tb.P.assign((size_t)std::max(tb.npat, 1) * n4 * n4, 0.0);
+    for (const auto& kv : masks) {
+        const auto Pm = pattern_projector(kv.first, h->p.Ls, h->p.b5, h->p.c5, h->p.mf);
+        std::copy(Pm.begin(), Pm.end(), tb.P.begin() + (size_t)kv.second * n4 * n4);
+    }
+    tb.pat.resize(site_mask.size());
+    for (size_t i = 0; i < site_mask.size(); ++i)
+        tb.pat[i] = site_mask[i] > 0 ? masks[site_mask[i]] : -1;
+    return DWF_OK;
+}
+
+struct DevTables {
+    int* pat = nullptr;
+    int* in_omega = nullptr;
+    double2* P = nullptr;
+    ~DevTables() {
+        cudaFree(pat);
+        cudaFree(in_omega);
+        cudaFree(P);
+    }
+};
+
+dwf_status upload(const BoundaryTables& tb, DevTables& dt) {
+    DWF_CUDA(cudaMalloc(&dt.pat, tb.pat.size() * sizeof(int)));
+    DWF_CUDA(cudaMalloc(&dt.in_omega, tb.in_omega.size() * sizeof(int)));
+    DWF_CUDA(cudaMalloc(&dt.P, tb.P.size() * sizeof(double2)));
+    DWF_CUDA(cudaMemcpy(dt.pat, tb.pat.data(), tb.pat.size() * sizeof(int), cudaMemcpyHostToDevice));
+    DWF_CUDA(cudaMemcpy(dt.in_omega, tb.in_omega.data(), tb.in_omega.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+    DWF_CUDA(cudaMemcpy(dt.P, tb.P.data(), tb.P.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    return DWF_OK;
+}
+
+dwf_status project(const dwf_handle* h, const DevTables& dt, const double* in, double* out, int nrhs,
+                   cudaStream_t s) {
+    const int64_t ns = h->nsite[0] + h->nsite[1];
+    const int64_t total = ns * 3 * nrhs * 4 * h->p.Ls;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    k_boundary_project<<<grid, 256, 0, s>>>(reinterpret_cast<const double2*>(in),
+                                             reinterpret_cast<double2*>(out), dt.pat, dt.P, ns,
+                                             h->p.Ls, nrhs);
+    note_launch();
+    DWF_CUDA(cudaGetLastError());
+    return DWF_OK;
+}
+
+dwf_status check_whole(const dwf_handle* h, const void* out, const void* in, int nrhs) {
+    if (h->dirichlet) {
+        set_error("boundary: needs a whole-lattice handle (Omega is given separately)");
+        return DWF_ERR_ARG;
+    }
+    if (out == nullptr || in == nullptr || out == in || nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("boundary: bad arguments (distinct device fields, 1 <= nrhs <= nrhs_max)");
+        return DWF_ERR_ARG;
+    }
+    if (!h->have_gauge) {
+        set_error("boundary: no gauge field loaded");
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
+}
+
+}  // namespace
+
+dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                            cudaStream_t s) {
+    DWF_TRY(check_whole(h, out, in, nrhs));
+    if (omega == nullptr) { set_error("boundary: null Omega"); return DWF_ERR_ARG; }
+    BoundaryTables tb;
+    DWF_TRY(build_tables(h, *omega, tb));
+    DevTables dt;
+    DWF_TRY(upload(tb, dt));
+    DWF_TRY(project(h, dt, in, out, nrhs, s));
+    DWF_CUDA(cudaStreamSynchronize(s));   // the tables are freed on return
+    return DWF_OK;
+}
+
+dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                         const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s) {
+    DWF_TRY(check_whole(h, out, in, nrhs));
+    if (omega == nullptr || sp == nullptr || stats == nullptr) {
+        set_error("boundary: null Omega, solver parameters or stats");
+        return DWF_ERR_ARG;
+    }
+    BoundaryTables tb;
+    DWF_TRY(build_tables(h, *omega, tb));
+    DevTables dt;
+    DWF_TRY(upload(tb, dt));
+    const int64_t ns = h->nsite[0] + h->nsite[1];
+    const size_t elems = (size_t)ns * 12 * h->p.Ls * nrhs;   // complex
+    if (tb.npat == 0) {   // no hop leaves Omega: P = 0 and R^-1 = 0
+        for (int r = 0; r < nrhs; ++r) stats[r] = dwf_solver_stats{};
+        DWF_CUDA(cudaMemsetAsync(out, 0, elems * 16, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        return DWF_OK;
+    }
+    double *u = nullptr, *v = nullptr, *y = nullptr;
+    DWF_CUDA(cudaMalloc(&u, elems * 16));
+    DWF_CUDA(cudaMalloc(&v, elems * 16));
+    DWF_CUDA(cudaMalloc(&y, elems * 16));
+    dwf_status st = DWF_OK;
+    auto run = [&]() -> dwf_status {
+        // u = P in ; v = D u on Omega-bar
+        DWF_TRY(project(h, dt, in, u, nrhs, s));
+        DWF_TRY(op_apply_d(h, v, u, 0, DWF_FP64, nrhs, h->d_tmp, s));
+        const int per_site = 12 * h->p.Ls * nrhs;
+        const int64_t total = ns * per_site;
+        const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        k_mask<<<grid, 256, 0, s>>>(reinterpret_cast<double2*>(v), dt.in_omega, ns, per_site, 1);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        // y = D^-1 v
+        DWF_CUDA(cudaMemsetAsync(y, 0, elems * 16, s));
+        const dwf_status ss = cgne_solve(h, y, v, nrhs, sp, stats, s);
+        if (ss != DWF_OK) return ss;
+        // out = u - P y
+        DWF_TRY(project(h, dt, y, out, nrhs, s));
+        const int g2 = (int)std::min<int64_t>(((int64_t)elems + 255) / 256, 152 * 16);
+        k_rsub<<<g2, 256, 0, s>>>(reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(u),
+                                  (int64_t)elems);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        return DWF_OK;
+    };
+    st = run();
+    cudaStreamSynchronize(s);
+    cudaFree(u);
+    cudaFree(v);
+    cudaFree(y);
+    return st;
+}
+
+}  // namespace dwf

@@ -183,6 +183,10 @@ dwf_status init_local_kernels();
 dwf_status init_local_mat_kernels();
 void build_fived_mats(const FiveD& f, std::vector<float>& out);
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
+dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                            cudaStream_t s);
+dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                         const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
 dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
                             int nshift, int nrhs, const dwf_solver_params* sp,
                             dwf_solver_stats* stats, cudaStream_t s);

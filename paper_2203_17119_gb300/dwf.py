@@ -97,6 +97,9 @@ def lib():
             "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
                                      C.POINTER(SolverStats), vp],
+            "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
+            "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
+                                  C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
             "dwf_nn_destroy": [vp],
             "dwf_nn_set_weights": [vp, vp, C.c_size_t],
@@ -320,6 +323,25 @@ class Handle:
             _check(rc)
         d = [s.as_dict() for s in st]
         return [d[k * nsys:(k + 1) * nsys] for k in range(len(shifts))], rc
+
+    @staticmethod
+    def _box(omega):
+        o, e = omega
+        return Box((C.c_int * 4)(*o), (C.c_int * 4)(*e))
+
+    def boundary_project(self, out, inp, omega, nrhs=1, stream=None):
+        """out = P in: Luescher's projector for the box ``omega`` = (origin, extent)."""
+        _check(lib().dwf_boundary_project(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp),
+                                          nrhs, _stream(stream)))
+        return out
+
+    def boundary_rinv(self, out, inp, omega, nrhs=1, tol=1e-10, inner=FP32, stream=None):
+        """out = R^-1 in = P in - P D^-1 D_partialbar P in; returns the D solve's stats."""
+        sp = SolverParams(tol, 100000, 0.0, 16, 0, inner, 0.0, 8, None, 0, 0)
+        st = (SolverStats * nrhs)()
+        _check(lib().dwf_boundary_rinv(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
+                                       C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
 
     def set_tile(self, nrhs=1, tile_sites=32, lanes_per_thread=2):
         """Fix the tile size and FP32 hop lanes per thread for this nrhs."""
