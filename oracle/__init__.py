@@ -14,8 +14,10 @@ Modules:
   cut-link form), per-site evaluation for sampled checks.
 * ``oracle.dense``    -- dense matrices of the above on tiny lattices, for
   brute-force inverses, determinants and the block identities of Sec. 2.1.
-* ``oracle.krylov``   -- textbook CG, mixed-precision-free reference of the
-  flexible GCR iteration.
+* ``oracle.multishift`` -- multi-shift CG for the rational functions of the
+  normal operators (Sec. 2.3.1).
+* ``oracle.force``    -- the link derivative of Re <X, D Y>, the insertion
+  of delta D that the DD-HMC forces of Sec. 2.3 are built from.
 * ``oracle.nn``       -- the parallel-transport convolutional preconditioner
   (forward, analytic backward, Adam).
 

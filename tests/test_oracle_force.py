@@ -1,0 +1,112 @@
+"""Pins of the link-force oracle (CPU).
+
+D is affine in the links (U and U^+ enter linearly), so for the tangent
+perturbation U -> U + i H U of any set of links the change of Re <X, D Y> is
+exactly linear: f(U + i H U) - f(U) = sum over the perturbed links of
+Re tr[i H F].  That fixes every term of the force independently of its own
+formula (the D used is the oracle's operator, itself pinned elsewhere).
+Further: F is traceless anti-Hermitian, transforms covariantly under gauge
+transformations, the adjoint bilinear Re <X, D^+ Y> has the force of
+(Y, X), and the active-link mask zeroes the links it leaves out."""
+
+import numpy as np
+import pytest
+
+from oracle import dwf as O
+from oracle.force import box_links, force_bilinear
+from paper_2203_17119_gb300 import inputs
+
+SHAMIR = O.DWFParams(M5=1.8, mf=0.1)
+MOBIUS = O.DWFParams(M5=1.8, mf=0.01, b5=1.5, c5=0.5)
+DIMS, LS = (4, 4, 2, 2), 4
+
+
+def _hermitian_traceless(rng, shape=()):
+    A = rng.standard_normal(shape + (3, 3)) + 1j * rng.standard_normal(shape + (3, 3))
+    H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+    return H - (np.trace(H, axis1=-2, axis2=-1) / 3.0)[..., None, None] * np.eye(3)
+
+
+def _setup(seed):
+    rng = np.random.default_rng(seed)
+    U = inputs.gauge_field(DIMS, "haar", rng=rng)
+    X = inputs.gaussian_source(DIMS, LS, rng=rng)
+    Y = inputs.gaussian_source(DIMS, LS, rng=rng)
+    return rng, U, X, Y
+
+
+def _f(U, X, Y, prm, dagger=False):
+    return float(np.real(np.vdot(X, O.apply_D(U, Y, prm, dagger))))
+
+
+@pytest.mark.parametrize("prm", [SHAMIR, MOBIUS], ids=["shamir", "mobius"])
+def test_single_link_perturbations_are_exact(prm):
+    rng, U, X, Y = _setup(1)
+    F = force_bilinear(U, X, Y, prm)
+    f0 = _f(U, X, Y, prm)
+    for _ in range(6):
+        t, z, y, x = (int(rng.integers(n)) for n in DIMS[::-1])
+        mu = int(rng.integers(4))
+        H = _hermitian_traceless(rng)
+        U2 = U.copy()
+        U2[t, z, y, x, mu] = U[t, z, y, x, mu] + 1j * H @ U[t, z, y, x, mu]
+        want = _f(U2, X, Y, prm) - f0
+        got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
+        assert abs(got - want) <= 1e-11 * max(1.0, abs(want)), (t, z, y, x, mu)
+
+
+@pytest.mark.parametrize("prm", [SHAMIR, MOBIUS], ids=["shamir", "mobius"])
+def test_all_links_at_once(prm):
+    rng, U, X, Y = _setup(2)
+    F = force_bilinear(U, X, Y, prm)
+    H = _hermitian_traceless(rng, U.shape[:-2])
+    want = _f(U + 1j * H @ U, X, Y, prm) - _f(U, X, Y, prm)
+    got = float(np.real(np.einsum("...ab,...ba->...", 1j * H, F).sum()))
+    assert abs(got - want) <= 1e-10 * abs(want)
+
+
+def test_traceless_antihermitian():
+    _, U, X, Y = _setup(3)
+    F = force_bilinear(U, X, Y, MOBIUS)
+    assert np.abs(F + np.conj(np.swapaxes(F, -1, -2))).max() <= 1e-13
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() <= 1e-13
+    assert np.abs(F).max() > 0.1
+
+
+def test_gauge_covariance():
+    rng, U, X, Y = _setup(4)
+    G = inputs.gauge_field(DIMS, "haar", rng=rng)[..., 0, :, :]    # one SU(3) per site
+    Ug = U.copy()
+    for mu in range(4):
+        Gf = np.roll(G, -1, axis=O.AXIS[mu])
+        Ug[..., mu, :, :] = G @ U[..., mu, :, :] @ np.conj(np.swapaxes(Gf, -1, -2))
+    Xg = np.einsum("tzyxab,tzyxsib->tzyxsia", G, X)
+    Yg = np.einsum("tzyxab,tzyxsib->tzyxsia", G, Y)
+    F = force_bilinear(U, X, Y, MOBIUS)
+    Fg = force_bilinear(Ug, Xg, Yg, MOBIUS)
+    Gd = np.conj(np.swapaxes(G, -1, -2))
+    want = np.einsum("tzyxab,tzyxmbc,tzyxcd->tzyxmad", G, F, Gd)
+    assert np.abs(Fg - want).max() <= 1e-12 * np.abs(F).max()
+
+
+def test_adjoint_bilinear_swaps_fields():
+    rng, U, X, Y = _setup(5)
+    F = force_bilinear(U, Y, X, MOBIUS)
+    H = _hermitian_traceless(rng, U.shape[:-2])
+    want = _f(U + 1j * H @ U, X, Y, MOBIUS, True) - _f(U, X, Y, MOBIUS, True)
+    got = float(np.real(np.einsum("...ab,...ba->...", 1j * H, F).sum()))
+    assert abs(got - want) <= 1e-10 * abs(want)
+
+
+def test_rhs_sum_and_active_mask():
+    rng, U, X, Y = _setup(6)
+    X2 = inputs.gaussian_source(DIMS, LS, rng=rng)
+    Y2 = inputs.gaussian_source(DIMS, LS, rng=rng)
+    F = force_bilinear(U, [X, X2], [Y, Y2], MOBIUS)
+    assert np.abs(F - force_bilinear(U, X, Y, MOBIUS) - force_bilinear(U, X2, Y2, MOBIUS)).max() <= 1e-12
+    box = ((1, 0, 0, 0), (2, 4, 2, 2))
+    act = box_links(DIMS, box)
+    # x-links leave the box from x = 2; links in y, z, t stay inside
+    assert act[..., 0].sum() == 16 and act[..., 1].sum() == 32 and act[..., 3].sum() == 32
+    Fm = force_bilinear(U, [X, X2], [Y, Y2], MOBIUS, active=act)
+    assert np.array_equal(Fm[act], F[act]) and np.abs(Fm[~act]).max() == 0.0
