@@ -475,6 +475,73 @@ def run_multishift(args):
                       "max_true_resid": max(s[0]["true_resid"] for s in st)}))
 
 
+def run_force(args):
+    """Link force of Re <X, D Y> (--force [f64|f32] [L] [Ls]) on an L^4 x Ls
+    Moebius lattice (default the 16^4 x 12 workload): the whole dwf_force call
+    (the two site-local B = b5 + c5 S5 launches and the force kernel), CUDA
+    events per call, L2 flushed between calls; the oracle's time per site on an
+    8^4 sample beside it."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    prec_name = args.force[0] if args.force else "f64"
+    L = int(args.force[1]) if len(args.force) > 1 else DIMS[0]
+    Ls = int(args.force[2]) if len(args.force) > 2 else LS
+    prec = G.PREC[prec_name]
+    word = {G.FP64: 8, G.FP32: 4}[prec]
+    dims = (L, L, L, L)
+    rng = np.random.default_rng(SEED)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
+    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    n = 2 * 12 * Ls * L ** 4
+    X = torch.randn(n, dtype=torch.float64, device="cuda").to(G._DTYPE[prec])
+    Y = torch.randn(n, dtype=torch.float64, device="cuda").to(G._DTYPE[prec])
+    out = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
+    del U
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        h.force(out, X, Y, prec=prec)
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.force(out, X, Y, prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    V = L ** 4
+    # per site: X and Y once, four forward links, four FP64 forces written
+    nbytes = V * (2 * 24 * Ls * word + 4 * 18 * word + 4 * 18 * 8)
+    # per site, direction and lane: four half-spinor projections (12 flops
+    # each) and two rank-2 outer products (2 x 9 complex multiply-adds)
+    flops = V * 4 * Ls * (4 * 12 + 2 * 2 * 9 * 8)
+    peak = 6800.0
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    from oracle import dwf as O
+    from oracle.force import force_bilinear
+    sd = (8, 8, 8, 8)
+    Us = inputs.gauge_field(sd, "exp", eps=EPS, rng=rng)
+    Xs, Ys = (inputs.gaussian_source(sd, Ls, rng=rng) for _ in range(2))
+    prm = O.DWFParams(M5=M5, mf=MF, b5=B5, c5=C5)
+    t = time.time()
+    force_bilinear(Us, Xs, Ys, prm)
+    oracle_s_per_site = (time.time() - t) / 8 ** 4
+    print(json.dumps({"kernel": "force", "lattice": list(dims), "Ls": Ls, "prec": prec_name,
+                      "ms": ms, "gflops": flops / (ms * 1e-3) / 1e9,
+                      "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
+                      "algorithmic_bytes": nbytes, "flops": flops,
+                      "oracle_ms_scaled": oracle_s_per_site * V * 1e3,
+                      "oracle_sample": "8^4 x Ls, one call, time per site scaled to the lattice"}))
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -545,6 +612,8 @@ def main():
                     help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--multishift", nargs="+", metavar="ARG",
                     help="NSHIFT [f64|f32]: multi-shift CG against single-shift solves")
+    ap.add_argument("--force", nargs="*", metavar="ARG",
+                    help="link force of Re <X, D Y>: [f64|f32] [L] [Ls]")
     ap.add_argument("--hop", nargs="+", metavar="ARG",
                     help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
     ap.add_argument("--no-autotune", action="store_true")
@@ -567,6 +636,9 @@ def main():
     rank = env_int("RANK", 0)
     if args.multishift:
         run_multishift(args)
+        return
+    if args.force is not None:
+        run_force(args)
         return
     if args.hop:
         run_hop(args)

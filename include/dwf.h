@@ -328,6 +328,26 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
                              int nrhs, const dwf_solver_params* sp, dwf_solver_stats* stats,
                              void* stream);
 
+/* Link force of the bilinear sum_r Re <X_r, D Y_r>: the insertion of
+ * delta D between two solved fields that the DD-HMC forces of Sec. 2.3 are
+ * built from (the variation of R^-1 = P - P D^-1 D_partialbar and of the
+ * actions built on it).  For every link U_mu(x), out[lex][mu] (a 3 x 3
+ * complex matrix, canonical gauge layout) is the traceless anti-Hermitian F
+ * with  d/d eps Re <X, D(exp(i eps H) U) Y> |_0 = Re tr[i H F]  for every
+ * traceless Hermitian H:
+ *   F = -1/2 TA(U_mu(x) M),  M = sum_lanes Z(x+mu) ((1 - g_mu) X(x))^+
+ *                                  + [Z(x) ((1 + g_mu) X(x+mu))^+]^+,
+ * Z = (b5 + c5 S5) Y, TA(A) = (A - A^+)/2 - tr(A - A^+)/6.  The adjoint
+ * bilinear Re <X, D^+ Y> has the force of (Y, X).  X, Y: device full fields
+ * of precision `prec` (FP64: FP64 arithmetic; FP32: FP32 links and
+ * arithmetic), nrhs right-hand sides summed.  `active` (nullable): only links
+ * with both ends in that box get a force, the others 0 (the links the DD-HMC
+ * holds fixed).  accumulate: out += F instead of out = F.  h: a whole-lattice
+ * handle; fields that vanish outside a box give that box's Dirichlet force.
+ * Uses the handle's scratch fields; allocates nothing. */
+dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
+                     const dwf_box* active, int accumulate, void* stream);
+
 /* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
  * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
  * itself stalls for Moebius DWF, whose Schur operator has the origin in its

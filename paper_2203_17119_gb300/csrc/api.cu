@@ -292,6 +292,12 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
     return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
+                     const dwf_box* active, int accumulate, void* stream) {
+    DWF_TRY(check_handle(h));
+    return force_bilinear(h, out, X, Y, prec, nrhs, active, accumulate, (cudaStream_t)stream);
+}
+
 dwf_status dwf_check_device(dwf_handle* h) {
     DWF_TRY(check_handle(h));
     int e = 0;

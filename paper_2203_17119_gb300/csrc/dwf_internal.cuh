@@ -187,6 +187,8 @@ dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, co
                             cudaStream_t s);
 dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                          const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
+dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
+                          const dwf_box* active, int accumulate, cudaStream_t s);
 dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
                             int nshift, int nrhs, const dwf_solver_params* sp,
                             dwf_solver_stats* stats, cudaStream_t s);

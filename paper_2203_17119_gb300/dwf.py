@@ -98,6 +98,7 @@ def lib():
             "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
                                      C.POINTER(SolverStats), vp],
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
+            "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
             "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
                                   C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
@@ -342,6 +343,15 @@ class Handle:
         _check(lib().dwf_boundary_rinv(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
                                        C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
+
+    def force(self, out, X, Y, prec=FP64, nrhs=1, active=None, accumulate=False, stream=None):
+        """out[lex, mu] = link force of sum_r Re <X_r, D Y_r> (traceless
+        anti-Hermitian 3 x 3, FP64 canonical gauge layout); ``active`` an
+        optional box (origin, extent) outside which links get 0."""
+        box = C.byref(self._box(active)) if active is not None else None
+        _check(lib().dwf_force(self._h, _ptr(out), _ptr(X), _ptr(Y), prec, nrhs, box, int(accumulate),
+                               _stream(stream)))
+        return out
 
     def set_tile(self, nrhs=1, tile_sites=32, lanes_per_thread=2):
         """Fix the tile size and FP32 hop lanes per thread for this nrhs."""
