@@ -38,8 +38,16 @@ struct Cx {
 };
 
 template <class S, class R>
-__device__ __forceinline__ Cx<R> ld(const S* p) {
-    return Cx<R>{(R)p[0], (R)p[1]};
+__device__ __forceinline__ Cx<R> ld(const S* p);
+template <>
+__device__ __forceinline__ Cx<float> ld<float, float>(const float* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return Cx<float>{v.x, v.y};
+}
+template <>
+__device__ __forceinline__ Cx<double> ld<double, double>(const double* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return Cx<double>{v.x, v.y};
 }
 
 // upper half spinor of (1 + SG g_mu) v from the four spin rows v[4] (one colour)
@@ -62,7 +70,7 @@ __device__ __forceinline__ void half(const S* __restrict__ base, int N5, int lan
     for (int c = 0; c < 3; ++c) {
         Cx<R> v[4];
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp) v[sp] = ld<S, R>(base + ((int64_t)(sp * 3 + c) * N5 + lane) * 2);
+        for (int sp = 0; sp < 4; ++sp) v[sp] = ld<S, R>(base + ((sp * 3 + c) * N5 + lane) * 2);
         Cx<R> p[2];
         proj<MU, SG, R>(v, p);
         o[0][c] = p[0];
@@ -92,6 +100,58 @@ __device__ __forceinline__ bool in_box(const ForceArgs& a, const int* x) {
         if (d >= a.ext[mu]) return false;
     }
     return true;
+}
+
+// F = -1/2 TA(U_t(x) M) for link t of site i of parity p, written to (or
+// added into) the canonical force array; links outside the active box get 0.
+template <class SL, class R>
+__device__ __forceinline__ void link_out(const ForceArgs& a, int p, int64_t i, int t, const Cx<R> (&Mt)[3][3]) {
+    const SL* U = reinterpret_cast<const SL*>(a.links[p]) + (i * 8 + t) * 18;
+    Cx<R> F[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const R ur = (R)U[(r * 3 + k) * 2], ui = (R)U[(r * 3 + k) * 2 + 1];
+                re += ur * Mt[k][c].re - ui * Mt[k][c].im;
+                im += ur * Mt[k][c].im + ui * Mt[k][c].re;
+            }
+            F[r][c] = Cx<R>{re, im};
+        }
+    const int64_t g = a.gidx[p][i * 8 + t];   // lex * 4 + mu
+    if (g < 0) return;
+    bool active = true;
+    if (a.use_box) {
+        const int64_t lex = g >> 2;
+        int x[4] = {(int)(lex % a.L[0]), (int)((lex / a.L[0]) % a.L[1]),
+                    (int)((lex / ((int64_t)a.L[0] * a.L[1])) % a.L[2]),
+                    (int)(lex / ((int64_t)a.L[0] * a.L[1] * a.L[2]))};
+        active = in_box(a, x);
+        x[t] = (x[t] + 1) % a.L[t];
+        active = active && in_box(a, x);
+    }
+    double* o = a.out + g * 18;
+    // -1/2 TA(F) = -1/4 (F - F^+) + tr(F - F^+)/12, in the arithmetic precision
+    const R tr = (F[0][0].im + F[1][1].im + F[2][2].im) * (R)(1.0 / 3.0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R re = (R)-0.25 * (F[r][c].re - F[c][r].re);
+            R im = (R)-0.25 * (F[r][c].im + F[c][r].im);
+            if (r == c) im += (R)0.5 * tr;
+            if (!active) re = im = (R)0;
+            if (a.accumulate) {
+                o[(r * 3 + c) * 2] += re;
+                o[(r * 3 + c) * 2 + 1] += im;
+            } else {
+                o[(r * 3 + c) * 2] = re;
+                o[(r * 3 + c) * 2 + 1] = im;
+            }
+        }
 }
 
 template <int MU, class S, class R>
@@ -149,7 +209,7 @@ __device__ __forceinline__ void dir_matrix(const ForceArgs& a, int p, int64_t i,
 }
 
 template <class S, class SL, class R>
-__global__ void __launch_bounds__(256) k_force(const ForceArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force(const ForceArgs a) {
     const int64_t nthreads = a.ns * 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // every thread of a warp runs the same number of iterations (the
@@ -179,57 +239,10 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs a) {
         DWF_FORCE_DIR(3)
 #undef DWF_FORCE_DIR
         if (!live) continue;
-        // F = -1/2 TA(U_t(x) M_t)
-        const SL* U = reinterpret_cast<const SL*>(a.links[p]) + (i * 8 + t) * 18;
-        Cx<R> F[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                R re = 0, im = 0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const R ur = (R)U[(r * 3 + k) * 2], ui = (R)U[(r * 3 + k) * 2 + 1];
-                    re += ur * Mt[k][c].re - ui * Mt[k][c].im;
-                    im += ur * Mt[k][c].im + ui * Mt[k][c].re;
-                }
-                F[r][c] = Cx<R>{re, im};
-            }
-        const int64_t g = a.gidx[p][i * 8 + t];   // lex * 4 + mu
-        bool active = g >= 0;
-        if (active && a.use_box) {
-            const int64_t lex = g >> 2;
-            int x[4] = {(int)(lex % a.L[0]), (int)((lex / a.L[0]) % a.L[1]),
-                        (int)((lex / ((int64_t)a.L[0] * a.L[1])) % a.L[2]),
-                        (int)(lex / ((int64_t)a.L[0] * a.L[1] * a.L[2]))};
-            active = in_box(a, x);
-            x[t] = (x[t] + 1) % a.L[t];
-            active = active && in_box(a, x);
-        }
-        if (g < 0) continue;
-        double* o = a.out + g * 18;
-        // TA(F) = (F - F^+)/2 - tr(F - F^+)/6; diagonal imaginary parts
-        const double tr = (double)F[0][0].im + (double)F[1][1].im + (double)F[2][2].im;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double re = 0.5 * ((double)F[r][c].re - (double)F[c][r].re);
-                double im = 0.5 * ((double)F[r][c].im + (double)F[c][r].im);
-                if (r == c) im -= tr / 3.0;
-                re *= -0.5;
-                im *= -0.5;
-                if (!active) re = im = 0.0;
-                if (a.accumulate) {
-                    o[(r * 3 + c) * 2] += re;
-                    o[(r * 3 + c) * 2 + 1] += im;
-                } else {
-                    o[(r * 3 + c) * 2] = re;
-                    o[(r * 3 + c) * 2 + 1] = im;
-                }
-            }
+        link_out<SL, R>(a, p, i, t, Mt);
     }
 }
+
 
 }  // namespace
 
