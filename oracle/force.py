@@ -81,3 +81,62 @@ def box_links(dims, box) -> np.ndarray:
     for mu in range(4):
         out[..., mu] = m & np.roll(m, -1, axis=O.AXIS[mu])
     return out
+
+
+# ------------------------------------------------------------------
+# Force of the DD-HMC boundary pseudofermion action (Sec. 2.1, 2.3)
+#
+#   S = |R^-1 phi|^2,   R^-1 = P - P D^-1 D_partialbar,
+#
+# with P the projector onto the row space of D_partialbar (independent of the
+# links: the row space of (1 -+ g_mu) U B is that of (1 -+ g_mu) B for unitary
+# U).  With u = P phi, v = D u restricted to Omega-bar, y = D^-1 v and
+# chi = R^-1 phi = u - P y (in the range of P):
+#
+#   dS = -2 Re <chi, dy>,  dy = -D^-1 dD y + D^-1 (dD u restricted to Omega-bar),
+#
+# so with zeta = D^-+ chi the force is 2 F(zeta, y) - 2 F(zeta on Omega-bar, u),
+# two insertions of dD between solved fields (F = force_bilinear).
+# Dense linear algebra: tiny lattices only.
+
+def _dense_D(U, shape, p):
+    from oracle import dense as Dn
+    return Dn.dense_matrix(lambda f: O.apply_D(U, f, p), shape)
+
+
+def boundary_pieces_dense(U, phi, p: O.DWFParams, box):
+    """(u, y, chi, zeta, P, masks) of the boundary action for the box Omega."""
+    from oracle import dense as Dn
+    dims = O.lattice_dims(U)
+    Ls = phi.shape[4]
+    shape = phi.shape
+    D = _dense_D(U, shape, p)
+    ids = O.box_id_field(dims, [box])
+    om = Dn.site_mask_to_dofs(ids == 0, Ls * 12)
+    ob = Dn.site_mask_to_dofs(ids < 0, Ls * 12)
+    _, P_O = Dn.rowspace_projector(D[np.ix_(ob, om)])
+    n = D.shape[0]
+    P = np.zeros((n, n), dtype=np.complex128)
+    P[np.ix_(om, om)] = P_O
+    u = P @ phi.reshape(-1)
+    v = np.zeros(n, dtype=np.complex128)
+    v[ob] = (D @ u)[ob]
+    y = np.linalg.solve(D, v)
+    chi = u - P @ y
+    zeta = np.linalg.solve(np.conj(D.T), chi)
+    return {"u": u.reshape(shape), "y": y.reshape(shape), "chi": chi.reshape(shape),
+            "zeta": zeta.reshape(shape), "P": P, "omega_bar": ids < 0}
+
+
+def boundary_action_dense(U, phi, p: O.DWFParams, box) -> float:
+    """S = |R^-1 phi|^2 with dense P and D^-1."""
+    pc = boundary_pieces_dense(U, phi, p, box)
+    return float(np.vdot(pc["chi"], pc["chi"]).real)
+
+
+def boundary_action_force_dense(U, phi, p: O.DWFParams, box, active=None) -> np.ndarray:
+    """Link force of S = |R^-1 phi|^2: d/d eps S(exp(i eps H) U) = Re tr[i H F]."""
+    pc = boundary_pieces_dense(U, phi, p, box)
+    zeta_b = O.restrict(pc["zeta"], pc["omega_bar"])
+    return (2.0 * force_bilinear(U, pc["zeta"], pc["y"], p, active)
+            - 2.0 * force_bilinear(U, zeta_b, pc["u"], p, active))

@@ -110,3 +110,61 @@ def test_rhs_sum_and_active_mask():
     assert act[..., 0].sum() == 16 and act[..., 1].sum() == 32 and act[..., 3].sum() == 32
     Fm = force_bilinear(U, [X, X2], [Y, Y2], MOBIUS, active=act)
     assert np.array_equal(Fm[act], F[act]) and np.abs(Fm[~act]).max() == 0.0
+
+
+# ---------------------------------------------------------------- boundary action
+from oracle.force import boundary_action_dense, boundary_action_force_dense  # noqa: E402
+
+SLAB = (4, 2, 2, 2)
+
+
+def _expm_i(H, eps):
+    w, V = np.linalg.eigh(H)
+    return (V * np.exp(1j * eps * w)) @ np.conj(V.T)
+
+
+@pytest.mark.parametrize("prm", [SHAMIR, MOBIUS], ids=["shamir", "mobius"])
+def test_boundary_action_force_matches_finite_differences(prm):
+    """Central differences of S(exp(i eps H) U) = |R^-1 phi|^2 (dense R^-1)
+    against Re tr[i H F] at links inside, across and outside Omega."""
+    rng = np.random.default_rng(31)
+    U = inputs.gauge_field(SLAB, "haar", rng=rng)
+    phi = inputs.gaussian_source(SLAB, 4, rng=rng)
+    box = O.band_box(SLAB, 2, dirs=(0,))          # Omega: x in {1, 2}
+    F = boundary_action_force_dense(U, phi, prm, box)
+    eps = 1e-5
+    # (t, z, y, x, mu): an x-link inside Omega, x-links across both faces, a
+    # link in Omega-bar, a y-link in Omega
+    for (t, z, y, x, mu) in [(0, 0, 0, 1, 0), (1, 0, 1, 0, 0), (0, 1, 0, 2, 0), (1, 1, 1, 3, 1), (0, 1, 1, 2, 1)]:
+        H = _hermitian_traceless(rng)
+        Up, Um = U.copy(), U.copy()
+        Up[t, z, y, x, mu] = _expm_i(H, eps) @ U[t, z, y, x, mu]
+        Um[t, z, y, x, mu] = _expm_i(H, -eps) @ U[t, z, y, x, mu]
+        fd = (boundary_action_dense(Up, phi, prm, box) - boundary_action_dense(Um, phi, prm, box)) / (2 * eps)
+        got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
+        assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
+
+
+def test_adjoint_solve_through_gamma5_r5():
+    """D^-+ = G B D^-1 G B^-+ with G = gamma_5 R_5 (R_5: s -> Ls - 1 - s) and
+    B = b5 + c5 S5: the Moebius gamma_5 R_5 Hermiticity of D B^-1, the route
+    the library takes to the adjoint solve of the boundary force."""
+    from oracle import dense as Dn
+    rng = np.random.default_rng(32)
+    dims, Ls = (2, 2, 2, 2), 4
+    U = inputs.gauge_field(dims, "haar", rng=rng)
+    chi = inputs.gaussian_source(dims, Ls, rng=rng)
+    shape = chi.shape
+    _, g5 = O.gammas()
+
+    def G(f):
+        return np.einsum("ij,tzyxsja->tzyxsia", g5, f[..., ::-1, :, :])
+
+    for prm in (SHAMIR, MOBIUS):
+        D = Dn.dense_matrix(lambda f: O.apply_D(U, f, prm), shape)
+        B = Dn.dense_matrix(lambda f: O.five_b(f, prm), shape)
+        want = np.linalg.solve(np.conj(D.T), chi.reshape(-1))
+        w = np.linalg.solve(np.conj(B.T), chi.reshape(-1)).reshape(shape)
+        w = np.linalg.solve(D, G(w).reshape(-1)).reshape(shape)
+        got = G((B @ w.reshape(-1)).reshape(shape)).reshape(-1)
+        assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
