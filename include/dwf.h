@@ -348,6 +348,22 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
 dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                      const dwf_box* active, int accumulate, void* stream);
 
+/* Link force of the DD-HMC boundary pseudofermion action S = |R^-1 phi|^2
+ * (Sec. 2.1, 2.3; R^-1 as in dwf_boundary_rinv), summed over the nrhs
+ * right-hand sides: out[lex][mu] (canonical gauge layout, 3 x 3 complex,
+ * traceless anti-Hermitian) with d/d eps S(exp(i eps H) U) |_0 = Re tr[i H F]
+ * for every traceless Hermitian H.  With u = P phi, y = D^-1 (D u on
+ * Omega-bar), chi = R^-1 phi and zeta = D^-+ chi:
+ *     F = 2 F(zeta, y) - 2 F(zeta on Omega-bar, u)   (F(X, Y) as in dwf_force).
+ * D^-+ comes from D^-1 by the gamma_5 R_5 Hermiticity of D (b5 + c5 S5)^-1.
+ * Two solves with `sp`; stats: 2 * nrhs entries (the D^-1 v solve, then the
+ * adjoint one).  `active` and `accumulate` as in dwf_force.  Same handle,
+ * field and Omega rules as dwf_boundary_project; allocates four full FP64
+ * fields for the call. */
+dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
+                              const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                              dwf_solver_stats* stats, void* stream);
+
 /* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
  * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
  * itself stalls for Moebius DWF, whose Schur operator has the origin in its

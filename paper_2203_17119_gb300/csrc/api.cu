@@ -292,6 +292,13 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
     return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
+                              const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                              dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                      const dwf_box* active, int accumulate, void* stream) {
     DWF_TRY(check_handle(h));

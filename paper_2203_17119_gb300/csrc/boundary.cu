@@ -154,6 +154,34 @@ __global__ void k_rsub(double2* __restrict__ out, const double2* __restrict__ a,
     }
 }
 
+// out = gamma_5 R_5 in: spins 2, 3 negated, s -> Ls - 1 - s (full FP64 fields)
+__global__ void k_gamma5_r5(const double2* __restrict__ in, double2* __restrict__ out, int64_t nsites,
+                            int Ls, int nrhs) {
+    const int N5 = Ls * nrhs;
+    const int64_t total = nsites * 12 * N5;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(id % N5);
+        const int c = (int)((id / N5) % 12);
+        const int r = l / Ls, sidx = l - r * Ls;
+        const double2 v = in[id - l + r * Ls + (Ls - 1 - sidx)];
+        out[id] = c < 6 ? v : make_double2(-v.x, -v.y);
+    }
+}
+
+// out = factor * in where the site flag differs from `drop`, 0 elsewhere
+__global__ void k_scale_mask(const double2* __restrict__ in, double2* __restrict__ out,
+                             const int* __restrict__ in_omega, int64_t nsites, int per_site, int drop,
+                             double factor) {
+    const int64_t total = nsites * per_site;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = in[id];
+        out[id] = in_omega[id / per_site] == drop ? make_double2(0.0, 0.0)
+                                                  : make_double2(factor * v.x, factor * v.y);
+    }
+}
+
 struct BoundaryTables {
     std::vector<int> pat, in_omega;   // per full-field site (parity 0 block, then parity 1)
     std::vector<cd> P;                 // [npat][4Ls][4Ls]
@@ -285,6 +313,36 @@ dwf_status check_whole(const dwf_handle* h, const void* out, const void* in, int
     return DWF_OK;
 }
 
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+// B^-+ (per parity, FP64 closed form with d = b5, e = c5) or B (site-local)
+dwf_status five_b_full(dwf_handle* h, double* out, const double* in, int nrhs, bool inverse_adjoint,
+                       cudaStream_t s) {
+    const size_t off1 = cb_elems(h, 0, nrhs) * 2;   // doubles
+    FiveD fb = h->f5[0];
+    fb.d = h->p.b5;
+    fb.e = h->p.c5;
+    fb.a = -fb.e / fb.d;
+    fb.inv_d = 1.0 / fb.d;
+    double aL = 1.0;
+    for (int i = 0; i < h->p.Ls; ++i) aL *= fb.a;
+    fb.inv_den = 1.0 / (fb.d * (1.0 + h->p.mf * aL));
+    for (int p = 0; p < 2; ++p) {
+        LocalCall c{};
+        c.op = inverse_adjoint ? L_MINV : L_B;
+        c.in = in + (p ? off1 : 0);
+        c.out = out + (p ? off1 : 0);
+        c.parity = p;
+        c.dagger = inverse_adjoint ? 1 : 0;
+        c.prec_in = c.prec_in2 = c.prec_out = DWF_FP64;
+        c.nrhs = nrhs;
+        c.scale = 1.0;
+        c.f5 = inverse_adjoint ? &fb : nullptr;
+        DWF_TRY(launch_local(h, c, s));
+    }
+    return DWF_OK;
+}
+
 }  // namespace
 
 dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
@@ -352,6 +410,96 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
     cudaFree(u);
     cudaFree(v);
     cudaFree(y);
+    return st;
+}
+
+}  // namespace dwf
+
+namespace dwf {
+
+// Force of S = |R^-1 phi|^2 (Sec. 2.1, 2.3): with u = P phi, y = D^-1 (D u on
+// Omega-bar), chi = u - P y and zeta = D^-+ chi,
+//     F = 2 F(zeta, y) - 2 F(zeta on Omega-bar, u),
+// F(X, Y) the link force of Re <X, D Y> (force.cu).  The adjoint solve goes
+// through the gamma_5 R_5 Hermiticity of D B^-1 (B = b5 + c5 S5):
+// D^-+ = G B D^-1 G B^-+, G = gamma_5 R_5: one more solve with D and three
+// site-local passes.
+dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
+                          const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                          dwf_solver_stats* stats, cudaStream_t s) {
+    DWF_TRY(check_whole(h, out, phi, nrhs));
+    if (omega == nullptr || sp == nullptr || stats == nullptr) {
+        set_error("boundary: null Omega, solver parameters or stats");
+        return DWF_ERR_ARG;
+    }
+    BoundaryTables tb;
+    DWF_TRY(build_tables(h, *omega, tb));
+    const int64_t ns = h->nsite[0] + h->nsite[1];
+    const size_t elems = (size_t)ns * 12 * h->p.Ls * nrhs;   // complex
+    const int64_t nlinks = (int64_t)h->p.dims[0] * h->p.dims[1] * h->p.dims[2] * h->p.dims[3] * 4;
+    if (tb.npat == 0) {   // no hop leaves Omega: S = 0
+        for (int r = 0; r < 2 * nrhs; ++r) stats[r] = dwf_solver_stats{};
+        if (!accumulate) DWF_CUDA(cudaMemsetAsync(out, 0, (size_t)nlinks * 18 * sizeof(double), s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        return DWF_OK;
+    }
+    DevTables dt;
+    DWF_TRY(upload(tb, dt));
+    double *u = nullptr, *v = nullptr, *y = nullptr, *w = nullptr;
+    DWF_CUDA(cudaMalloc(&u, elems * 16));
+    DWF_CUDA(cudaMalloc(&v, elems * 16));
+    DWF_CUDA(cudaMalloc(&y, elems * 16));
+    DWF_CUDA(cudaMalloc(&w, elems * 16));
+    const int per_site = 12 * h->p.Ls * nrhs;
+    const int g = grid_for((int64_t)elems);
+    auto run = [&]() -> dwf_status {
+        // u = P phi; v = D u on Omega-bar; y = D^-1 v
+        DWF_TRY(project(h, dt, phi, u, nrhs, s));
+        DWF_TRY(op_apply_d(h, v, u, 0, DWF_FP64, nrhs, h->d_tmp, s));
+        k_mask<<<g, 256, 0, s>>>(reinterpret_cast<double2*>(v), dt.in_omega, ns, per_site, 1);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        DWF_CUDA(cudaMemsetAsync(y, 0, elems * 16, s));
+        dwf_status st = cgne_solve(h, y, v, nrhs, sp, stats, s);
+        if (st != DWF_OK) return st;
+        // chi = u - P y (into v)
+        DWF_TRY(project(h, dt, y, v, nrhs, s));
+        k_rsub<<<g, 256, 0, s>>>(reinterpret_cast<double2*>(v), reinterpret_cast<const double2*>(u),
+                                 (int64_t)elems);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        // zeta = G B D^-1 G B^-+ chi
+        DWF_TRY(five_b_full(h, w, v, nrhs, true, s));
+        k_gamma5_r5<<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(w), reinterpret_cast<double2*>(v), ns,
+                                      h->p.Ls, nrhs);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        DWF_CUDA(cudaMemsetAsync(w, 0, elems * 16, s));
+        st = cgne_solve(h, w, v, nrhs, sp, stats + nrhs, s);
+        if (st != DWF_OK) return st;
+        DWF_TRY(five_b_full(h, v, w, nrhs, false, s));
+        k_gamma5_r5<<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(v), reinterpret_cast<double2*>(w), ns,
+                                      h->p.Ls, nrhs);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        // v = -2 zeta on Omega-bar, w = 2 zeta; F = F(w, y) + F(v, u)
+        k_scale_mask<<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(w), reinterpret_cast<double2*>(v),
+                                       dt.in_omega, ns, per_site, 1, -2.0);
+        note_launch();
+        k_scale_mask<<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(w), reinterpret_cast<double2*>(w),
+                                       dt.in_omega, ns, per_site, 2, 2.0);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        DWF_TRY(force_bilinear(h, out, w, y, DWF_FP64, nrhs, active, accumulate, s));
+        DWF_TRY(force_bilinear(h, out, v, u, DWF_FP64, nrhs, active, 1, s));
+        return DWF_OK;
+    };
+    const dwf_status st = run();
+    cudaStreamSynchronize(s);
+    cudaFree(u);
+    cudaFree(v);
+    cudaFree(y);
+    cudaFree(w);
     return st;
 }
 

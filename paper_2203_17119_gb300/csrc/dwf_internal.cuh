@@ -185,6 +185,9 @@ void build_fived_mats(const FiveD& f, std::vector<float>& out);
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
 dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                             cudaStream_t s);
+dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
+                          const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                          dwf_solver_stats* stats, cudaStream_t s);
 dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                          const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
 dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
@@ -209,6 +212,7 @@ struct LocalCall {
     const int* run;          // per-system run flags (device, nullable)
     double* partial;         // per tile, per rhs |result|^2 (nullable)
     int T;
+    const FiveD* f5 = nullptr;   // FP64 only: fifth-dimension coefficients other than the handle's
 };
 dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s);
 

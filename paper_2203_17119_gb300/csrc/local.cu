@@ -695,7 +695,7 @@ dwf_status init_local_kernels() {
 template <class Sin, class Sin2, class Sout, class Svec, class R>
 static dwf_status launch_lt(dwf_handle* h, const LocalCall& c, const TileSet& ts, cudaStream_t s) {
     LocalArgs a;
-    const FiveD& f = h->f5[0];
+    const FiveD& f = c.f5 ? *c.f5 : h->f5[0];
     a.op = c.op;
     a.in = c.in;
     a.in2 = c.in2;
@@ -737,6 +737,7 @@ dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s) {
     const TileSet& ts = get_tiles(h, c.T > 0 ? c.T : 16);
     const dwf_prec pi = c.prec_in, po = c.prec_out;
     const dwf_prec p2 = c.in2 ? c.prec_in2 : pi;
+    if (c.f5 != nullptr && (pi != DWF_FP64 || po != DWF_FP64)) return DWF_ERR_UNSUPPORTED;
     if (pi == DWF_FP64 || po == DWF_FP64) {
         if (pi != DWF_FP64 || po != DWF_FP64 || p2 != DWF_FP64) return DWF_ERR_UNSUPPORTED;
         return launch_lt<double, double, double, double, double>(h, c, ts, s);

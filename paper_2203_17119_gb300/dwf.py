@@ -99,6 +99,8 @@ def lib():
                                      C.POINTER(SolverStats), vp],
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
+            "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
+                                   C.POINTER(SolverStats), vp],
             "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
                                   C.POINTER(SolverStats), vp],
             "dwf_nn_create": [C.POINTER(vp), i],
@@ -342,6 +344,17 @@ class Handle:
         st = (SolverStats * nrhs)()
         _check(lib().dwf_boundary_rinv(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
                                        C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
+
+    def boundary_force(self, out, phi, omega, nrhs=1, active=None, accumulate=False, tol=1e-10,
+                       inner=FP32, stream=None):
+        """out[lex, mu] = link force of |R^-1 phi|^2 for the box ``omega``;
+        returns the stats of the two solves (2 * nrhs dicts)."""
+        sp = SolverParams(tol, 100000, 0.0, 16, 0, inner, 0.0, 8, None, 0, 0)
+        st = (SolverStats * (2 * nrhs))()
+        box = C.byref(self._box(active)) if active is not None else None
+        _check(lib().dwf_boundary_force(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(phi), nrhs, box,
+                                        int(accumulate), C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
 
     def force(self, out, X, Y, prec=FP64, nrhs=1, active=None, accumulate=False, stream=None):
