@@ -542,6 +542,49 @@ def run_force(args):
                       "oracle_sample": "8^4 x Ls, one call, time per site scaled to the lattice"}))
 
 
+def run_boundary(args):
+    """DD-HMC boundary operator at the default workload (--boundary [f32|f64]):
+    Omega = the interior 14^4 box of the width-2 band.  Times the projector P,
+    R^-1 phi (one D solve) and the force of |R^-1 phi|^2 (two solves, two force
+    insertions), each after one warm-up call, solves to 1e-10 with the given
+    inner precision."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    prec_name = args.boundary[0] if args.boundary else "f32"
+    prec = G.PREC[prec_name]
+    rng = np.random.default_rng(SEED)
+    U = inputs.gauge_field(DIMS, "exp", eps=EPS, rng=rng)
+    h = G.Handle(DIMS, LS, G.Action(M5, MF, B5, C5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.autotune(1, G.FP32)
+    phi = h.pack(torch.from_numpy(inputs.gaussian_source(DIMS, LS, rng=rng).reshape(-1)).cuda())
+    out = torch.empty_like(phi)
+    force = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
+    del U
+    res = {}
+
+    def timed(name, fn):
+        fn()
+        torch.cuda.synchronize()
+        t = time.time()
+        r = fn()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = (time.time() - t) * 1e3
+        return r
+
+    timed("project", lambda: h.boundary_project(out, phi, BAND_BOX))
+    st = timed("rinv", lambda: h.boundary_rinv(out, phi, BAND_BOX, tol=1e-10, inner=prec))
+    res["rinv_iters"] = st[0]["iters"]
+    res["rinv_true_resid"] = st[0]["true_resid"]
+    st = timed("force", lambda: h.boundary_force(force, phi, BAND_BOX, tol=1e-10, inner=prec))
+    res["force_iters"] = [s["iters"] for s in st]
+    res["force_true_resid"] = max(s["true_resid"] for s in st)
+    print(json.dumps({"workload": "DD-HMC boundary operator, " + WORKLOAD.split(";")[0]
+                      + f", Omega = {BAND_BOX}", "inner": prec_name, **res}))
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -612,6 +655,8 @@ def main():
                     help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--multishift", nargs="+", metavar="ARG",
                     help="NSHIFT [f64|f32]: multi-shift CG against single-shift solves")
+    ap.add_argument("--boundary", nargs="*", metavar="ARG",
+                    help="boundary operator P, R^-1 and the boundary-action force: [f32|f64]")
     ap.add_argument("--force", nargs="*", metavar="ARG",
                     help="link force of Re <X, D Y>: [f64|f32] [L] [Ls]")
     ap.add_argument("--hop", nargs="+", metavar="ARG",
@@ -639,6 +684,9 @@ def main():
         return
     if args.force is not None:
         run_force(args)
+        return
+    if args.boundary is not None:
+        run_boundary(args)
         return
     if args.hop:
         run_hop(args)

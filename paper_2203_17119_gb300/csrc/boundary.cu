@@ -72,13 +72,13 @@ std::vector<cd> pattern_projector(int mask, int Ls, double b5, double c5, double
         return w;
     };
     std::vector<std::vector<cd>> Q;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 8 && (int)Q.size() < n; ++k) {
         if (!(mask >> k & 1)) continue;
         const int mu = k & 3;
         const double sgn = k < 4 ? 1.0 : -1.0;   // x + mu: (1 + gamma), x - mu: (1 - gamma)
         const auto g = gamma_mu(mu);
         for (int col = 0; col < 4; ++col)
-            for (int s = 0; s < Ls; ++s) {
+            for (int s = 0; s < Ls && (int)Q.size() < n; ++s) {   // a full basis spans everything
                 std::vector<cd> v(n, 0.0);
                 for (int sp = 0; sp < 4; ++sp) v[sp * Ls + s] = (sp == col ? 1.0 : 0.0) + sgn * g[sp * 4 + col];
                 std::vector<cd> w = Bdag(v);
@@ -284,6 +284,36 @@ dwf_status upload(const BoundaryTables& tb, DevTables& dt) {
     return DWF_OK;
 }
 
+// The tables of the last Omega, kept on the handle (building them is host
+// work of O(volume) plus a Gram-Schmidt per crossing pattern).
+struct BoundaryCache {
+    int key[8];
+    BoundaryTables tb;
+    DevTables dt;
+};
+
+dwf_status cached_tables(dwf_handle* h, const dwf_box& om, const BoundaryTables** tb, const DevTables** dt) {
+    auto* c = static_cast<BoundaryCache*>(h->boundary_cache);
+    const int key[8] = {om.origin[0], om.origin[1], om.origin[2], om.origin[3],
+                        om.extent[0], om.extent[1], om.extent[2], om.extent[3]};
+    if (c == nullptr || !std::equal(key, key + 8, c->key)) {
+        delete c;
+        h->boundary_cache = nullptr;
+        c = new BoundaryCache();
+        std::copy(key, key + 8, c->key);
+        dwf_status st = build_tables(h, om, c->tb);
+        if (st == DWF_OK) st = upload(c->tb, c->dt);
+        if (st != DWF_OK) {
+            delete c;
+            return st;
+        }
+        h->boundary_cache = c;
+    }
+    *tb = &c->tb;
+    *dt = &c->dt;
+    return DWF_OK;
+}
+
 dwf_status project(const dwf_handle* h, const DevTables& dt, const double* in, double* out, int nrhs,
                    cudaStream_t s) {
     const int64_t ns = h->nsite[0] + h->nsite[1];
@@ -349,13 +379,10 @@ dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, co
                             cudaStream_t s) {
     DWF_TRY(check_whole(h, out, in, nrhs));
     if (omega == nullptr) { set_error("boundary: null Omega"); return DWF_ERR_ARG; }
-    BoundaryTables tb;
-    DWF_TRY(build_tables(h, *omega, tb));
-    DevTables dt;
-    DWF_TRY(upload(tb, dt));
-    DWF_TRY(project(h, dt, in, out, nrhs, s));
-    DWF_CUDA(cudaStreamSynchronize(s));   // the tables are freed on return
-    return DWF_OK;
+    const BoundaryTables* tb = nullptr;
+    const DevTables* dt = nullptr;
+    DWF_TRY(cached_tables(h, *omega, &tb, &dt));
+    return project(h, *dt, in, out, nrhs, s);
 }
 
 dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
@@ -365,10 +392,11 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
         set_error("boundary: null Omega, solver parameters or stats");
         return DWF_ERR_ARG;
     }
-    BoundaryTables tb;
-    DWF_TRY(build_tables(h, *omega, tb));
-    DevTables dt;
-    DWF_TRY(upload(tb, dt));
+    const BoundaryTables* tbp = nullptr;
+    const DevTables* dtp = nullptr;
+    DWF_TRY(cached_tables(h, *omega, &tbp, &dtp));
+    const BoundaryTables& tb = *tbp;
+    const DevTables& dt = *dtp;
     const int64_t ns = h->nsite[0] + h->nsite[1];
     const size_t elems = (size_t)ns * 12 * h->p.Ls * nrhs;   // complex
     if (tb.npat == 0) {   // no hop leaves Omega: P = 0 and R^-1 = 0
@@ -432,8 +460,11 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
         set_error("boundary: null Omega, solver parameters or stats");
         return DWF_ERR_ARG;
     }
-    BoundaryTables tb;
-    DWF_TRY(build_tables(h, *omega, tb));
+    const BoundaryTables* tbp = nullptr;
+    const DevTables* dtp = nullptr;
+    DWF_TRY(cached_tables(h, *omega, &tbp, &dtp));
+    const BoundaryTables& tb = *tbp;
+    const DevTables& dt = *dtp;
     const int64_t ns = h->nsite[0] + h->nsite[1];
     const size_t elems = (size_t)ns * 12 * h->p.Ls * nrhs;   // complex
     const int64_t nlinks = (int64_t)h->p.dims[0] * h->p.dims[1] * h->p.dims[2] * h->p.dims[3] * 4;
@@ -443,8 +474,6 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
         DWF_CUDA(cudaStreamSynchronize(s));
         return DWF_OK;
     }
-    DevTables dt;
-    DWF_TRY(upload(tb, dt));
     double *u = nullptr, *v = nullptr, *y = nullptr, *w = nullptr;
     DWF_CUDA(cudaMalloc(&u, elems * 16));
     DWF_CUDA(cudaMalloc(&v, elems * 16));
@@ -503,4 +532,11 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
     return st;
 }
 
+}  // namespace dwf
+
+namespace dwf {
+void free_boundary_cache(dwf_handle* h) {
+    delete static_cast<BoundaryCache*>(h->boundary_cache);
+    h->boundary_cache = nullptr;
+}
 }  // namespace dwf

@@ -434,6 +434,7 @@ dwf_status destroy(dwf_handle* h) {
     free_solver_ws(h);
     free_nn_ws(h);
     free_gcr_ws(h);
+    free_boundary_cache(h);
     delete h;
     return DWF_OK;
 }

@@ -144,6 +144,8 @@ struct dwf_handle {
     std::map<int, int> tuned_tc;
     // hop tile order: nrhs -> consecutive tiles per CTA before striding by the grid
     std::map<int, int> tuned_chunk;
+    // boundary operator tables of the last Omega (boundary.cu)
+    void* boundary_cache = nullptr;
 };
 
 namespace dwf {
@@ -185,6 +187,7 @@ void build_fived_mats(const FiveD& f, std::vector<float>& out);
 dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
 dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                             cudaStream_t s);
+void free_boundary_cache(dwf_handle* h);
 dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
                           const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                           dwf_solver_stats* stats, cudaStream_t s);
