@@ -364,6 +364,19 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
                               const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream);
 
+/* Chebyshev filter of the normal Schur operator: the recursively built
+ * filter functions of Sec. 4 for a fast multigrid set-up of the local
+ * solves.  out = T_order(z(A)) in with A = M_pc^+ M_pc (on a box handle each
+ * box's Dirichlet operator D_Omega) and z(lam) = (hi + lo - 2 lam)/(hi - lo):
+ * modes of A in [lo, hi] keep |factor| <= 1, modes below lo grow like
+ * cosh(order arccosh z).  Three-term recurrence, `order` applications of A.
+ * in, out: distinct odd cb fields of precision `prec` (FP64 or FP32, which is
+ * also the operator's), nrhs right-hand sides.  Errors: DWF_ERR_ARG for
+ * order < 0, hi <= lo or another precision.  Allocates three cb fields for
+ * the call and ends with a stream sync. */
+dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int order, double lo, double hi,
+                                dwf_prec prec, int nrhs, void* stream);
+
 /* Flexible GCR(restart) with the right preconditioner K (NULL = none) on the
  * normal equations M_pc^+ M_pc x_o = M_pc^+ b'_o (restarted GCR on M_pc
  * itself stalls for Moebius DWF, whose Schur operator has the origin in its

@@ -299,6 +299,12 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
     return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int order, double lo, double hi,
+                                dwf_prec prec, int nrhs, void* stream) {
+    DWF_TRY(check_handle(h));
+    return chebyshev_filter(h, out, in, order, lo, hi, prec, nrhs, (cudaStream_t)stream);
+}
+
 dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                      const dwf_box* active, int accumulate, void* stream) {
     DWF_TRY(check_handle(h));

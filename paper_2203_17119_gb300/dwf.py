@@ -99,6 +99,7 @@ def lib():
                                      C.POINTER(SolverStats), vp],
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
+            "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
             "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
                                    C.POINTER(SolverStats), vp],
             "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
@@ -356,6 +357,12 @@ class Handle:
         _check(lib().dwf_boundary_force(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(phi), nrhs, box,
                                         int(accumulate), C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
+
+    def chebyshev_filter(self, out, inp, order, lo, hi, prec=FP64, nrhs=1, stream=None):
+        """out = T_order(z(A)) in, A = M_pc^+ M_pc, z(lam) = (hi + lo - 2 lam)/(hi - lo)."""
+        _check(lib().dwf_chebyshev_filter(self._h, _ptr(out), _ptr(inp), int(order), float(lo), float(hi),
+                                          prec, nrhs, _stream(stream)))
+        return out
 
     def force(self, out, X, Y, prec=FP64, nrhs=1, active=None, accumulate=False, stream=None):
         """out[lex, mu] = link force of sum_r Re <X_r, D Y_r> (traceless
