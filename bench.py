@@ -547,7 +547,7 @@ def run_boundary(args):
     Omega = the interior 14^4 box of the width-2 band.  Times the projector P,
     R^-1 phi (one D solve) and the force of |R^-1 phi|^2 (two solves, two force
     insertions), each after one warm-up call, solves to 1e-10 with the given
-    inner precision."""
+    inner precision; then R phi once (two FP64 Dirichlet CGNR solves)."""
     import numpy as np
     import torch
     from paper_2203_17119_gb300 import dwf as G
@@ -581,6 +581,14 @@ def run_boundary(args):
     st = timed("force", lambda: h.boundary_force(force, phi, BAND_BOX, tol=1e-10, inner=prec))
     res["force_iters"] = [s["iters"] for s in st]
     res["force_true_resid"] = max(s["true_resid"] for s in st)
+    # R itself: two FP64 Dirichlet CGNR solves (Omega-bar, then Omega), timed once
+    torch.cuda.synchronize()
+    t = time.time()
+    st = h.boundary_r(out, phi, BAND_BOX, tol=1e-10)
+    torch.cuda.synchronize()
+    res["r_ms"] = (time.time() - t) * 1e3
+    res["r_iters"] = [s["iters"] for s in st]
+    res["r_true_resid"] = max(s["true_resid"] for s in st)
     print(json.dumps({"workload": "DD-HMC boundary operator, " + WORKLOAD.split(";")[0]
                       + f", Omega = {BAND_BOX}", "inner": prec_name, **res}))
 

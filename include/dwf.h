@@ -348,6 +348,19 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
 dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                      const dwf_box* active, int accumulate, void* stream);
 
+/* The boundary operator itself (Sec. 2.1), the map of the pseudofermion
+ * heat bath phi = R eta:
+ *   R = P - P D_Omega^-1 D_partial D_Omega-bar^-1 D_partialbar   (on the range of P),
+ * out = u - P D_Omega^-1 (D b on Omega), b = D_Omega-bar^-1 (D u on Omega-bar),
+ * u = P in.  The two Dirichlet solves (on the band Omega-bar, which is not a
+ * box, and on Omega) run as FP64 CGNR on P_S D P_S to sp->tol (maxiter
+ * sp->maxiter; the other fields of sp are ignored); stats: 2 * nrhs entries
+ * (the Omega-bar solve, then the Omega solve).  Same handle, field and Omega
+ * rules as dwf_boundary_project; allocates seven full FP64 fields for the
+ * call.  DWF_ERR_NOT_CONVERGED if a solve misses 2 * tol. */
+dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
+
 /* Link force of the DD-HMC boundary pseudofermion action S = |R^-1 phi|^2
  * (Sec. 2.1, 2.3; R^-1 as in dwf_boundary_rinv), summed over the nrhs
  * right-hand sides: out[lex][mu] (canonical gauge layout, 3 x 3 complex,

@@ -292,6 +292,12 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
     return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    return boundary_r(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
                               const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream) {

@@ -19,6 +19,7 @@
 // y = D^-1 v (the mixed-precision CGNE of the whole lattice), out = u - P y.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -405,10 +406,11 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
         DWF_CUDA(cudaStreamSynchronize(s));
         return DWF_OK;
     }
-    double *u = nullptr, *v = nullptr, *y = nullptr;
-    DWF_CUDA(cudaMalloc(&u, elems * 16));
-    DWF_CUDA(cudaMalloc(&v, elems * 16));
-    DWF_CUDA(cudaMalloc(&y, elems * 16));
+    double* scratch = nullptr;   // u, v, y: three full FP64 fields
+    DWF_CUDA(cudaMalloc(&scratch, 3 * elems * 16));
+    double* u = scratch;
+    double* v = scratch + 2 * elems;
+    double* y = scratch + 4 * elems;
     dwf_status st = DWF_OK;
     auto run = [&]() -> dwf_status {
         // u = P in ; v = D u on Omega-bar
@@ -435,9 +437,7 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
     };
     st = run();
     cudaStreamSynchronize(s);
-    cudaFree(u);
-    cudaFree(v);
-    cudaFree(y);
+    cudaFree(scratch);
     return st;
 }
 
@@ -474,11 +474,12 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
         DWF_CUDA(cudaStreamSynchronize(s));
         return DWF_OK;
     }
-    double *u = nullptr, *v = nullptr, *y = nullptr, *w = nullptr;
-    DWF_CUDA(cudaMalloc(&u, elems * 16));
-    DWF_CUDA(cudaMalloc(&v, elems * 16));
-    DWF_CUDA(cudaMalloc(&y, elems * 16));
-    DWF_CUDA(cudaMalloc(&w, elems * 16));
+    double* scratch = nullptr;   // u, v, y, w: four full FP64 fields
+    DWF_CUDA(cudaMalloc(&scratch, 4 * elems * 16));
+    double* u = scratch;
+    double* v = scratch + 2 * elems;
+    double* y = scratch + 4 * elems;
+    double* w = scratch + 6 * elems;
     const int per_site = 12 * h->p.Ls * nrhs;
     const int g = grid_for((int64_t)elems);
     auto run = [&]() -> dwf_status {
@@ -525,10 +526,7 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
     };
     const dwf_status st = run();
     cudaStreamSynchronize(s);
-    cudaFree(u);
-    cudaFree(v);
-    cudaFree(y);
-    cudaFree(w);
+    cudaFree(scratch);
     return st;
 }
 
@@ -539,4 +537,226 @@ void free_boundary_cache(dwf_handle* h) {
     delete static_cast<BoundaryCache*>(h->boundary_cache);
     h->boundary_cache = nullptr;
 }
+}  // namespace dwf
+
+namespace dwf {
+
+namespace {
+
+// per right-hand side partial sums of Re <a, b> over full FP64 fields:
+// grid (nblk, nrhs), block (b, r) sums the rows of rhs r it strides over
+__global__ void k_dot_rhs(const double2* __restrict__ a, const double2* __restrict__ b, int64_t nrows, int Ls,
+                          int nrhs, double* __restrict__ partial) {
+    __shared__ double red[256];
+    const int r = blockIdx.y;
+    double acc = 0.0;
+    const int64_t n = nrows * Ls;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / Ls;
+        const int sidx = (int)(e - row * Ls);
+        const int64_t i = (row * nrhs + r) * Ls + sidx;
+        const double2 x = a[i], y = b[i];
+        acc += x.x * y.x + x.y * y.y;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(size_t)r * gridDim.x + blockIdx.x] = red[0];
+}
+
+// y = a_r x + b_r y per right-hand side (scalars from a device array [2][nrhs])
+__global__ void k_axpby_rhs(const double2* __restrict__ x, double2* __restrict__ y, const double* __restrict__ ab,
+                            int64_t n, int Ls, int nrhs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)((i / Ls) % nrhs);
+        const double al = ab[r], be = ab[nrhs + r];
+        const double2 u = x[i], v = y[i];
+        y[i] = make_double2(al * u.x + be * v.x, al * u.y + be * v.y);
+    }
+}
+
+constexpr int kDotBlocks = 256;
+
+struct MaskedCG {
+    dwf_handle* h;
+    const int* flag;   // per full-field site: 1 in Omega, 0 outside
+    int keep;          // the site set S: flag == keep
+    int nrhs;
+    int64_t ns, elems;
+    double* part;      // [nrhs][kDotBlocks]
+    double* ab;        // [2][nrhs]
+    std::vector<double> hpart;
+    cudaStream_t s;
+
+    dwf_status mask(double* f) {
+        k_mask<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<double2*>(f), flag, ns, (int)(elems / ns),
+                                               1 - keep);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        return DWF_OK;
+    }
+    // out = P_S D(^+) P_S in (in supported on S)
+    dwf_status apply(double* out, const double* in, int dagger) {
+        DWF_TRY(op_apply_d(h, out, in, dagger, DWF_FP64, nrhs, h->d_tmp, s));
+        return mask(out);
+    }
+    dwf_status dot(const double* a, const double* b, std::vector<double>& out) {
+        k_dot_rhs<<<dim3(kDotBlocks, nrhs), 256, 0, s>>>(reinterpret_cast<const double2*>(a),
+                                                         reinterpret_cast<const double2*>(b), ns * 12,
+                                                         h->p.Ls, nrhs, part);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        DWF_CUDA(cudaMemcpyAsync(hpart.data(), part, hpart.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        out.assign(nrhs, 0.0);
+        for (int r = 0; r < nrhs; ++r)
+            for (int k = 0; k < kDotBlocks; ++k) out[r] += hpart[(size_t)r * kDotBlocks + k];
+        return DWF_OK;
+    }
+    dwf_status axpby(const double* x, double* y, const std::vector<double>& a, const std::vector<double>& b) {
+        std::vector<double> hab(2 * nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+            hab[r] = a[r];
+            hab[nrhs + r] = b[r];
+        }
+        DWF_CUDA(cudaMemcpyAsync(ab, hab.data(), hab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        k_axpby_rhs<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<const double2*>(x),
+                                                    reinterpret_cast<double2*>(y), ab, elems, h->p.Ls, nrhs);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        DWF_CUDA(cudaStreamSynchronize(s));   // hab is reused by the next call
+        return DWF_OK;
+    }
+};
+
+// x = (P_S D P_S)^-1 b on the site set S by CGNR (FP64, one CG per right-hand
+// side in shared launches); b supported on S.  work: four full fields.
+dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, double tol, int maxiter,
+                        dwf_solver_stats* stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = m.nrhs;
+    const int64_t e2 = 2 * m.elems;
+    double* r = work;
+    double* z = work + e2;
+    double* p = work + 2 * e2;
+    double* w = work + 3 * e2;
+    std::vector<double> bn2, zz, zz_new, ww, rr, one(nrhs, 1.0), zero(nrhs, 0.0), al(nrhs), mal(nrhs), be(nrhs);
+    DWF_TRY(m.dot(b, b, bn2));
+    DWF_CUDA(cudaMemsetAsync(x, 0, m.elems * 16, m.s));
+    DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_TRY(m.apply(z, r, 1));
+    DWF_CUDA(cudaMemcpyAsync(p, z, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_TRY(m.dot(z, z, zz));
+    std::vector<int> done(nrhs, 0), iters(nrhs, 0);
+    int it = 0;
+    for (; it < maxiter; ++it) {
+        DWF_TRY(m.dot(r, r, rr));
+        bool all = true;
+        for (int k = 0; k < nrhs; ++k) {
+            if (!done[k] && rr[k] <= tol * tol * bn2[k]) {
+                done[k] = 1;
+                iters[k] = it;
+            }
+            all = all && done[k];
+        }
+        if (all) break;
+        DWF_TRY(m.apply(w, p, 0));
+        DWF_TRY(m.dot(w, w, ww));
+        for (int k = 0; k < nrhs; ++k) {
+            al[k] = (done[k] || ww[k] == 0.0) ? 0.0 : zz[k] / ww[k];
+            mal[k] = -al[k];
+        }
+        DWF_TRY(m.axpby(p, x, al, one));    // x += alpha p
+        DWF_TRY(m.axpby(w, r, mal, one));   // r -= alpha w
+        DWF_TRY(m.apply(z, r, 1));          // z = (P D P)^+ r
+        DWF_TRY(m.dot(z, z, zz_new));
+        for (int k = 0; k < nrhs; ++k) be[k] = (done[k] || zz[k] == 0.0) ? 0.0 : zz_new[k] / zz[k];
+        DWF_TRY(m.axpby(z, p, one, be));    // p = z + beta p
+        zz = zz_new;
+    }
+    // true residual |b - P D P x| / |b|
+    DWF_TRY(m.apply(w, x, 0));
+    DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_TRY(m.axpby(w, r, std::vector<double>(nrhs, -1.0), one));
+    DWF_TRY(m.dot(r, r, rr));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    dwf_status worst = DWF_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        dwf_solver_stats st{};
+        st.iters = done[k] ? iters[k] : it;
+        st.op_applies = 2 * st.iters + 2;
+        st.true_resid = bn2[k] > 0 ? std::sqrt(rr[k] / bn2[k]) : 0.0;
+        st.seconds = secs;
+        const dwf_status sk = st.true_resid <= 2 * tol ? DWF_OK : DWF_ERR_NOT_CONVERGED;
+        st.status = (int)sk;
+        if (sk != DWF_OK) worst = sk;
+        stats[k] = st;
+    }
+    return worst;
+}
+
+}  // namespace
+
+// R psi = P psi - P D_Omega^-1 D_partial D_Omega-bar^-1 D_partialbar P psi (Sec. 2.1): the
+// boundary operator whose inverse dwf_boundary_rinv applies; the two Dirichlet
+// solves (on Omega-bar, the band, and on Omega) by FP64 CGNR on P_S D P_S.
+dwf_status boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
+                      const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s) {
+    DWF_TRY(check_whole(h, out, in, nrhs));
+    if (omega == nullptr || sp == nullptr || stats == nullptr || !(sp->tol > 0.0) || sp->maxiter < 1) {
+        set_error("boundary: null Omega, solver parameters or stats, or tol <= 0 / maxiter < 1");
+        return DWF_ERR_ARG;
+    }
+    const BoundaryTables* tbp = nullptr;
+    const DevTables* dtp = nullptr;
+    DWF_TRY(cached_tables(h, *omega, &tbp, &dtp));
+    const DevTables& dt = *dtp;
+    const int64_t ns = h->nsite[0] + h->nsite[1];
+    const int64_t elems = ns * 12 * h->p.Ls * nrhs;   // complex
+    if (tbp->npat == 0) {
+        for (int r = 0; r < 2 * nrhs; ++r) stats[r] = dwf_solver_stats{};
+        DWF_CUDA(cudaMemsetAsync(out, 0, elems * 16, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        return DWF_OK;
+    }
+    double* scratch = nullptr;   // u, a, b, 4 CG work fields, and the reduction buffers
+    const size_t fb = (size_t)elems * 16;
+    DWF_CUDA(cudaMalloc(&scratch, 7 * fb + ((size_t)kDotBlocks + 2) * nrhs * sizeof(double)));
+    double* u = scratch;
+    double* a = scratch + 2 * elems;
+    double* b = scratch + 4 * elems;
+    double* work = scratch + 6 * elems;
+    MaskedCG m{h, dt.in_omega, 0, nrhs, ns, elems, scratch + 14 * elems,
+               scratch + 14 * elems + (size_t)kDotBlocks * nrhs, std::vector<double>((size_t)kDotBlocks * nrhs), s};
+    auto run = [&]() -> dwf_status {
+        // u = P psi; a = D u on Omega-bar; b = D_Omega-bar^-1 a
+        DWF_TRY(project(h, dt, in, u, nrhs, s));
+        DWF_TRY(op_apply_d(h, a, u, 0, DWF_FP64, nrhs, h->d_tmp, s));
+        m.keep = 0;
+        DWF_TRY(m.mask(a));
+        dwf_status st = masked_solve(m, b, a, work, sp->tol, sp->maxiter, stats);
+        if (st != DWF_OK) return st;
+        // a = D b on Omega; b = D_Omega^-1 a
+        DWF_TRY(op_apply_d(h, a, b, 0, DWF_FP64, nrhs, h->d_tmp, s));
+        m.keep = 1;
+        DWF_TRY(m.mask(a));
+        st = masked_solve(m, b, a, work, sp->tol, sp->maxiter, stats + nrhs);
+        if (st != DWF_OK) return st;
+        // out = u - P b
+        DWF_TRY(project(h, dt, b, out, nrhs, s));
+        k_rsub<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<double2*>(out),
+                                               reinterpret_cast<const double2*>(u), elems);
+        note_launch();
+        DWF_CUDA(cudaGetLastError());
+        return DWF_OK;
+    };
+    const dwf_status st = run();
+    cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    return st;
+}
+
 }  // namespace dwf

@@ -100,6 +100,7 @@ def lib():
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
             "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
+            "dwf_boundary_r": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
                                    C.POINTER(SolverStats), vp],
             "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
@@ -345,6 +346,15 @@ class Handle:
         st = (SolverStats * nrhs)()
         _check(lib().dwf_boundary_rinv(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
                                        C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
+
+    def boundary_r(self, out, inp, omega, nrhs=1, tol=1e-10, maxiter=20000, stream=None):
+        """out = R in (FP64 Dirichlet solves on Omega-bar and Omega); returns the
+        stats of the two solves (2 * nrhs dicts)."""
+        sp = SolverParams(tol, maxiter, 0.0, 16, 0, FP64, 0.0, 8, None, 0, 0)
+        st = (SolverStats * (2 * nrhs))()
+        _check(lib().dwf_boundary_r(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
+                                    C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
 
     def boundary_force(self, out, phi, omega, nrhs=1, active=None, accumulate=False, tol=1e-10,
