@@ -140,3 +140,85 @@ def boundary_action_force_dense(U, phi, p: O.DWFParams, box, active=None) -> np.
     zeta_b = O.restrict(pc["zeta"], pc["omega_bar"])
     return (2.0 * force_bilinear(U, pc["zeta"], pc["y"], p, active)
             - 2.0 * force_bilinear(U, zeta_b, pc["u"], p, active))
+
+
+# ------------------------------------------------------------------
+# Hasenbusch ratio of boundary operators (Sec. 2.3): light mass R, heavy
+# (Pauli-Villars) mass R_pv,
+#
+#   S = phi^+ R_pv^+ R^-+ R^-1 R_pv phi = |chi|^2,  chi = R^-1 R_pv phi.
+#
+# R_pv = P_pv - P_pv D_O^-1 D_d D_Ob^-1 D_db (PV mass); with u_pv = P_pv phi,
+# b = D_Ob^-1 (D u_pv on Omega-bar), d = D_O^-1 (D b on Omega): R_pv phi = u_pv - P_pv d.
+# dS = 2 Re <chi, dR^-1 w> + 2 Re <xi, dR_pv phi>, w = R_pv phi, xi = R^-+ chi
+#    = chi - (D^+ (zeta on Omega-bar)) on Omega,  zeta = D^-+ chi (light mass),
+# and <xi, dR_pv phi> = <eta, dD (d - b)> + <kappa, dD (b - u_pv)> with the PV
+# local adjoint solves eta = D_O^-+ P_pv xi, kappa = D_Ob^-+ (D^+ eta on Omega-bar):
+# four PV local solves (b, d, eta, kappa) and two light solves (y, zeta).
+def _blocks_dense(U, shape, p, box):
+    from oracle import dense as Dn
+    dims = O.lattice_dims(U)
+    Ls = shape[4]
+    D = _dense_D(U, shape, p)
+    ids = O.box_id_field(dims, [box])
+    om = Dn.site_mask_to_dofs(ids == 0, Ls * 12)
+    ob = Dn.site_mask_to_dofs(ids < 0, Ls * 12)
+    _, P_O = Dn.rowspace_projector(D[np.ix_(ob, om)])
+    n = D.shape[0]
+    P = np.zeros((n, n), dtype=np.complex128)
+    P[np.ix_(om, om)] = P_O
+    return D, P, om, ob
+
+
+def _dirichlet_solve(D, idx, rhs, adjoint=False):
+    """x supported on idx with (D restricted to idx) x = rhs (or its adjoint)."""
+    A = D[np.ix_(idx, idx)]
+    if adjoint:
+        A = np.conj(A.T)
+    x = np.zeros_like(rhs)
+    x[idx] = np.linalg.solve(A, rhs[idx])
+    return x
+
+
+def ratio_pieces_dense(U, phi, p_light: O.DWFParams, p_pv: O.DWFParams, box):
+    shape = phi.shape
+    Dl, Pl, om, ob = _blocks_dense(U, shape, p_light, box)
+    Dp, Pp, _, _ = _blocks_dense(U, shape, p_pv, box)
+    n = Dl.shape[0]
+
+    def restrict(v, idx):
+        out = np.zeros(n, dtype=np.complex128)
+        out[idx] = v[idx]
+        return out
+
+    u_pv = Pp @ phi.reshape(-1)
+    b = _dirichlet_solve(Dp, ob, restrict(Dp @ u_pv, ob))
+    d = _dirichlet_solve(Dp, om, restrict(Dp @ b, om))
+    w = u_pv - Pp @ d
+    u_l = Pl @ w
+    y = np.linalg.solve(Dl, restrict(Dl @ u_l, ob))
+    chi = u_l - Pl @ y
+    zeta = np.linalg.solve(np.conj(Dl.T), chi)
+    xi = chi - restrict(np.conj(Dl.T) @ restrict(zeta, ob), om)
+    eta = _dirichlet_solve(Dp, om, Pp @ xi, adjoint=True)
+    kappa = _dirichlet_solve(Dp, ob, restrict(np.conj(Dp.T) @ eta, ob), adjoint=True)
+    r = {k: v.reshape(shape) for k, v in dict(u_pv=u_pv, b=b, d=d, u_l=u_l, y=y, chi=chi, zeta=zeta,
+                                               eta=eta, kappa=kappa).items()}
+    r["omega_bar"] = O.box_id_field(O.lattice_dims(U), [box]) < 0
+    return r
+
+
+def ratio_action_dense(U, phi, p_light, p_pv, box) -> float:
+    """S = |R^-1 R_pv phi|^2 with dense P, R, R_pv."""
+    pc = ratio_pieces_dense(U, phi, p_light, p_pv, box)
+    return float(np.vdot(pc["chi"], pc["chi"]).real)
+
+
+def ratio_action_force_dense(U, phi, p_light, p_pv, box, active=None) -> np.ndarray:
+    """Link force of the boundary Hasenbusch ratio action."""
+    pc = ratio_pieces_dense(U, phi, p_light, p_pv, box)
+    zeta_b = O.restrict(pc["zeta"], pc["omega_bar"])
+    return (2.0 * force_bilinear(U, pc["zeta"], pc["y"], p_light, active)
+            - 2.0 * force_bilinear(U, zeta_b, pc["u_l"], p_light, active)
+            + 2.0 * force_bilinear(U, pc["eta"], pc["d"] - pc["b"], p_pv, active)
+            + 2.0 * force_bilinear(U, pc["kappa"], pc["b"] - pc["u_pv"], p_pv, active))

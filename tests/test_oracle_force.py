@@ -168,3 +168,29 @@ def test_adjoint_solve_through_gamma5_r5():
         w = np.linalg.solve(D, G(w).reshape(-1)).reshape(shape)
         got = G((B @ w.reshape(-1)).reshape(shape)).reshape(-1)
         assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+
+
+from oracle.force import ratio_action_dense, ratio_action_force_dense  # noqa: E402
+
+
+@pytest.mark.parametrize("light,pv", [(SHAMIR, O.DWFParams(M5=1.8, mf=1.0)),
+                                      (MOBIUS, O.DWFParams(M5=1.8, mf=1.0, b5=1.5, c5=0.5))],
+                         ids=["shamir", "mobius"])
+def test_ratio_action_force_matches_finite_differences(light, pv):
+    """Central differences of |R^-1 R_pv phi|^2 (dense R, R_pv) against the
+    force assembled from four PV local solves and two light solves."""
+    rng = np.random.default_rng(33)
+    U = inputs.gauge_field(SLAB, "haar", rng=rng)
+    phi = inputs.gaussian_source(SLAB, 4, rng=rng)
+    box = O.band_box(SLAB, 2, dirs=(0,))
+    F = ratio_action_force_dense(U, phi, light, pv, box)
+    eps = 1e-5
+    # a y-link inside Omega, an x-link across the face at x = 0 | 1, a y-link in Omega-bar
+    for (t, z, y, x, mu) in [(0, 1, 1, 2, 1), (1, 0, 1, 0, 0), (1, 1, 1, 3, 1)]:
+        H = _hermitian_traceless(rng)
+        Up, Um = U.copy(), U.copy()
+        Up[t, z, y, x, mu] = _expm_i(H, eps) @ U[t, z, y, x, mu]
+        Um[t, z, y, x, mu] = _expm_i(H, -eps) @ U[t, z, y, x, mu]
+        fd = (ratio_action_dense(Up, phi, light, pv, box) - ratio_action_dense(Um, phi, light, pv, box)) / (2 * eps)
+        got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
+        assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
