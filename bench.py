@@ -555,7 +555,7 @@ def run_boundary(args):
     prec_name = args.boundary[0] if args.boundary else "f32"
     prec = G.PREC[prec_name]
     rng = np.random.default_rng(SEED)
-    U = inputs.gauge_field(DIMS, "exp", eps=EPS, rng=rng)
+    U = inputs.gauge_field(DIMS, "exp", eps=EPS, seed=SEED)
     h = G.Handle(DIMS, LS, G.Action(M5, MF, B5, C5))
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     h.autotune(1, G.FP32)
@@ -581,6 +581,13 @@ def run_boundary(args):
     st = timed("force", lambda: h.boundary_force(force, phi, BAND_BOX, tol=1e-10, inner=prec))
     res["force_iters"] = [s["iters"] for s in st]
     res["force_true_resid"] = max(s["true_resid"] for s in st)
+    # the Hasenbusch ratio force against the Pauli-Villars (m_f = 1) boundary operator
+    hp = G.Handle(DIMS, LS, G.Action(M5, 1.0, B5, C5))
+    hp.set_gauge(torch.from_numpy(inputs.gauge_field(DIMS, "exp", eps=EPS, seed=SEED).reshape(-1)).cuda())
+    st = timed("ratio_force", lambda: h.boundary_ratio_force(hp, force, phi, BAND_BOX, tol=1e-10, inner=prec))
+    res["ratio_force_iters"] = [s["iters"] for s in st]
+    res["ratio_force_true_resid"] = max(s["true_resid"] for s in st)
+    del hp
     # R itself: two FP64 Dirichlet CGNR solves (Omega-bar, then Omega), timed once
     torch.cuda.synchronize()
     t = time.time()

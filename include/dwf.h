@@ -377,6 +377,26 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
                               const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream);
 
+/* Link force of the boundary Hasenbusch ratio (Sec. 2.3) between the light
+ * boundary operator R (handle h_light) and its Pauli-Villars counterpart
+ * R_pv (handle h_pv: same lattice, Ls and gauge field, heavier mass):
+ *   S = |R^-1 R_pv phi|^2,  d/d eps S(exp(i eps H) U) |_0 = Re tr[i H F],
+ *   F = 2 F(zeta, y) - 2 F(zeta on Omega-bar, u) + 2 F_pv(eta, d - b) + 2 F_pv(kappa, b - u_pv),
+ * with u_pv = P_pv phi, b = D_Ob^-1 (D u_pv on Omega-bar), d = D_O^-1 (D b on
+ * Omega) (PV; R_pv phi = u_pv - P_pv d), u, y, chi = R^-1 R_pv phi as in
+ * dwf_boundary_force (light), zeta = D^-+ chi, xi = R^-+ chi = chi - (D^+
+ * (zeta on Omega-bar)) on Omega, eta = D_O^-+ P_pv xi and kappa = D_Ob^-+
+ * (D^+ eta on Omega-bar) (PV): the four PV local solves and two light solves
+ * the paper counts.  Light solves: dwf_cgne_solve with `sp`; PV Dirichlet
+ * solves: FP64 CGNR to sp->tol.  stats: 6 * nrhs entries in the order b, d,
+ * y, the adjoint light solve, eta, kappa.  `active` and `accumulate` as in
+ * dwf_force (with the boundary links inactive the crossing terms vanish, as
+ * in the paper).  Same field and Omega rules as dwf_boundary_project;
+ * allocates fifteen full FP64 fields for the call. */
+dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const dwf_box* omega, double* out,
+                                    const double* phi, int nrhs, const dwf_box* active, int accumulate,
+                                    const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
+
 /* Chebyshev filter of the normal Schur operator: the recursively built
  * filter functions of Sec. 4 for a fast multigrid set-up of the local
  * solves.  out = T_order(z(A)) in with A = M_pc^+ M_pc (on a box handle each

@@ -298,6 +298,15 @@ dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, cons
     return boundary_r(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const dwf_box* omega, double* out,
+                                    const double* phi, int nrhs, const dwf_box* active, int accumulate,
+                                    const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h_light));
+    DWF_TRY(check_handle(h_pv));
+    return boundary_ratio_force(h_light, h_pv, omega, out, phi, nrhs, active, accumulate, sp, stats,
+                                (cudaStream_t)stream);
+}
+
 dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
                               const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream) {

@@ -635,7 +635,9 @@ struct MaskedCG {
 // x = (P_S D P_S)^-1 b on the site set S by CGNR (FP64, one CG per right-hand
 // side in shared launches); b supported on S.  work: four full fields.
 dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, double tol, int maxiter,
-                        dwf_solver_stats* stats) {
+                        dwf_solver_stats* stats, bool adjoint = false) {
+    // the operator is P_S D P_S, or its adjoint P_S D^+ P_S
+    const int op = adjoint ? 1 : 0, op_adj = adjoint ? 0 : 1;
     const auto t0 = std::chrono::steady_clock::now();
     const int nrhs = m.nrhs;
     const int64_t e2 = 2 * m.elems;
@@ -647,7 +649,7 @@ dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, d
     DWF_TRY(m.dot(b, b, bn2));
     DWF_CUDA(cudaMemsetAsync(x, 0, m.elems * 16, m.s));
     DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
-    DWF_TRY(m.apply(z, r, 1));
+    DWF_TRY(m.apply(z, r, op_adj));
     DWF_CUDA(cudaMemcpyAsync(p, z, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
     DWF_TRY(m.dot(z, z, zz));
     std::vector<int> done(nrhs, 0), iters(nrhs, 0);
@@ -663,7 +665,7 @@ dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, d
             all = all && done[k];
         }
         if (all) break;
-        DWF_TRY(m.apply(w, p, 0));
+        DWF_TRY(m.apply(w, p, op));
         DWF_TRY(m.dot(w, w, ww));
         for (int k = 0; k < nrhs; ++k) {
             al[k] = (done[k] || ww[k] == 0.0) ? 0.0 : zz[k] / ww[k];
@@ -671,14 +673,14 @@ dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, d
         }
         DWF_TRY(m.axpby(p, x, al, one));    // x += alpha p
         DWF_TRY(m.axpby(w, r, mal, one));   // r -= alpha w
-        DWF_TRY(m.apply(z, r, 1));          // z = (P D P)^+ r
+        DWF_TRY(m.apply(z, r, op_adj));     // z = (operator)^+ r
         DWF_TRY(m.dot(z, z, zz_new));
         for (int k = 0; k < nrhs; ++k) be[k] = (done[k] || zz[k] == 0.0) ? 0.0 : zz_new[k] / zz[k];
         DWF_TRY(m.axpby(z, p, one, be));    // p = z + beta p
         zz = zz_new;
     }
-    // true residual |b - P D P x| / |b|
-    DWF_TRY(m.apply(w, x, 0));
+    // true residual |b - (operator) x| / |b|
+    DWF_TRY(m.apply(w, x, op));
     DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
     DWF_TRY(m.axpby(w, r, std::vector<double>(nrhs, -1.0), one));
     DWF_TRY(m.dot(r, r, rr));
@@ -751,6 +753,164 @@ dwf_status boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const do
                                                reinterpret_cast<const double2*>(u), elems);
         note_launch();
         DWF_CUDA(cudaGetLastError());
+        return DWF_OK;
+    };
+    const dwf_status st = run();
+    cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    return st;
+}
+
+}  // namespace dwf
+
+namespace dwf {
+
+namespace {
+dwf_status copy_field(double* dst, const double* src, int64_t elems, cudaStream_t s) {
+    DWF_CUDA(cudaMemcpyAsync(dst, src, (size_t)elems * 16, cudaMemcpyDeviceToDevice, s));
+    return DWF_OK;
+}
+dwf_status launch_scale_mask(const double* in, double* out, const int* flag, int64_t ns, int64_t elems, int drop,
+                             double factor, cudaStream_t s) {
+    k_scale_mask<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out),
+                                                flag, ns, (int)(elems / ns), drop, factor);
+    note_launch();
+    DWF_CUDA(cudaGetLastError());
+    return DWF_OK;
+}
+dwf_status launch_rsub(double* out, const double* a, int64_t elems, cudaStream_t s) {
+    k_rsub<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(a),
+                                           elems);
+    note_launch();
+    DWF_CUDA(cudaGetLastError());
+    return DWF_OK;
+}
+dwf_status launch_mask(double* f, const int* flag, int64_t ns, int64_t elems, int drop, cudaStream_t s) {
+    k_mask<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<double2*>(f), flag, ns, (int)(elems / ns), drop);
+    note_launch();
+    DWF_CUDA(cudaGetLastError());
+    return DWF_OK;
+}
+dwf_status launch_g5r5(const double* in, double* out, int64_t ns, int Ls, int nrhs, int64_t elems, cudaStream_t s) {
+    k_gamma5_r5<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out),
+                                                ns, Ls, nrhs);
+    note_launch();
+    DWF_CUDA(cudaGetLastError());
+    return DWF_OK;
+}
+}  // namespace
+
+// Force of the boundary Hasenbusch ratio S = |R^-1 R_pv phi|^2 (Sec. 2.3),
+// light operator on hl, Pauli-Villars on hp:
+//   R_pv phi = u_pv - P_pv d,  u_pv = P_pv phi, b = D_Ob^-1 (D u_pv on Omega-bar), d = D_O^-1 (D b on Omega),
+//   chi = R^-1 R_pv phi,  zeta = D^-+ chi,  xi = R^-+ chi = chi - (D^+ (zeta on Omega-bar)) on Omega,
+//   eta = D_O^-+ P_pv xi,  kappa = D_Ob^-+ (D^+ eta on Omega-bar)   (PV),
+//   F = 2 F(zeta, y) - 2 F(zeta on Omega-bar, u) + 2 F_pv(eta, d - b) + 2 F_pv(kappa, b - u_pv),
+// with u, y the light R^-1 pieces: four PV local solves, two light solves.
+dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* omega, double* out, const double* phi,
+                                int nrhs, const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                                dwf_solver_stats* stats, cudaStream_t s) {
+    DWF_TRY(check_whole(hl, out, phi, nrhs));
+    DWF_TRY(check_whole(hp, out, phi, nrhs));
+    if (omega == nullptr || sp == nullptr || stats == nullptr || !(sp->tol > 0.0) || sp->maxiter < 1) {
+        set_error("boundary: null Omega, solver parameters or stats, or tol <= 0 / maxiter < 1");
+        return DWF_ERR_ARG;
+    }
+    for (int mu = 0; mu < 4; ++mu)
+        if (hl->p.dims[mu] != hp->p.dims[mu]) {
+            set_error("boundary: the light and Pauli-Villars handles differ in the lattice");
+            return DWF_ERR_ARG;
+        }
+    if (hl->p.Ls != hp->p.Ls) {
+        set_error("boundary: the light and Pauli-Villars handles differ in Ls");
+        return DWF_ERR_ARG;
+    }
+    const BoundaryTables *tl = nullptr, *tp = nullptr;
+    const DevTables *dl = nullptr, *dp = nullptr;
+    DWF_TRY(cached_tables(hl, *omega, &tl, &dl));
+    DWF_TRY(cached_tables(hp, *omega, &tp, &dp));
+    const int64_t ns = hl->nsite[0] + hl->nsite[1];
+    const int64_t elems = ns * 12 * hl->p.Ls * nrhs;   // complex
+    const int64_t nlinks = (int64_t)hl->p.dims[0] * hl->p.dims[1] * hl->p.dims[2] * hl->p.dims[3] * 4;
+    if (tl->npat == 0) {   // no hop leaves Omega: S = 0
+        for (int r = 0; r < 6 * nrhs; ++r) stats[r] = dwf_solver_stats{};
+        if (!accumulate) DWF_CUDA(cudaMemsetAsync(out, 0, (size_t)nlinks * 18 * sizeof(double), s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        return DWF_OK;
+    }
+    constexpr int NF = 15;
+    double* scratch = nullptr;
+    const size_t red = ((size_t)kDotBlocks + 2) * nrhs * sizeof(double);
+    DWF_CUDA(cudaMalloc(&scratch, NF * (size_t)elems * 16 + red));
+    double* F[NF];
+    for (int k = 0; k < NF; ++k) F[k] = scratch + 2 * elems * k;
+    double *u_pv = F[0], *t1 = F[1], *b = F[2], *d = F[3], *u_l = F[4], *chi = F[5], *y = F[6], *zeta = F[7],
+           *xi = F[8], *eta = F[9], *kappa = F[10], *W0 = F[11], *W1 = F[12], *W2 = F[13], *W3 = F[14];
+    double* work = F[11];   // the masked solves' four work fields W0..W3
+    double* part = scratch + 2 * elems * NF;
+    MaskedCG m{hp, dp->in_omega, 0, nrhs, ns, elems, part, part + (size_t)kDotBlocks * nrhs,
+               std::vector<double>((size_t)kDotBlocks * nrhs), s};
+    const int* flag = dp->in_omega;
+    const int Ls = hl->p.Ls;
+    auto run = [&]() -> dwf_status {
+        // R_pv phi: u_pv, b (Omega-bar solve), d (Omega solve), w = u_pv - P_pv d (in t1)
+        DWF_TRY(project(hp, *dp, phi, u_pv, nrhs, s));
+        DWF_TRY(op_apply_d(hp, t1, u_pv, 0, DWF_FP64, nrhs, hp->d_tmp, s));
+        DWF_TRY(launch_mask(t1, flag, ns, elems, 1, s));
+        dwf_status st = masked_solve(m, b, t1, work, sp->tol, sp->maxiter, stats);
+        if (st != DWF_OK) return st;
+        DWF_TRY(op_apply_d(hp, t1, b, 0, DWF_FP64, nrhs, hp->d_tmp, s));
+        DWF_TRY(launch_mask(t1, flag, ns, elems, 0, s));
+        m.keep = 1;
+        st = masked_solve(m, d, t1, work, sp->tol, sp->maxiter, stats + nrhs);
+        if (st != DWF_OK) return st;
+        DWF_TRY(project(hp, *dp, d, t1, nrhs, s));
+        DWF_TRY(launch_rsub(t1, u_pv, elems, s));                       // t1 = w
+        // light R^-1 w: u_l, y = D^-1 (D u_l on Omega-bar), chi = u_l - P y
+        DWF_TRY(project(hl, *dl, t1, u_l, nrhs, s));
+        DWF_TRY(op_apply_d(hl, chi, u_l, 0, DWF_FP64, nrhs, hl->d_tmp, s));
+        DWF_TRY(launch_mask(chi, flag, ns, elems, 1, s));
+        DWF_CUDA(cudaMemsetAsync(y, 0, (size_t)elems * 16, s));
+        st = cgne_solve(hl, y, chi, nrhs, sp, stats + 2 * nrhs, s);
+        if (st != DWF_OK) return st;
+        DWF_TRY(project(hl, *dl, y, chi, nrhs, s));
+        DWF_TRY(launch_rsub(chi, u_l, elems, s));                       // chi
+        // zeta = G B D^-1 G B^-+ chi (light)
+        DWF_TRY(five_b_full(hl, W0, chi, nrhs, true, s));
+        DWF_TRY(launch_g5r5(W0, W1, ns, Ls, nrhs, elems, s));
+        DWF_CUDA(cudaMemsetAsync(W0, 0, (size_t)elems * 16, s));
+        st = cgne_solve(hl, W0, W1, nrhs, sp, stats + 3 * nrhs, s);
+        if (st != DWF_OK) return st;
+        DWF_TRY(five_b_full(hl, W1, W0, nrhs, false, s));
+        DWF_TRY(launch_g5r5(W1, zeta, ns, Ls, nrhs, elems, s));
+        // xi = chi - (D^+ (zeta on Omega-bar)) on Omega
+        DWF_TRY(launch_scale_mask(zeta, W0, flag, ns, elems, 1, 1.0, s));
+        DWF_TRY(op_apply_d(hl, xi, W0, 1, DWF_FP64, nrhs, hl->d_tmp, s));
+        DWF_TRY(launch_mask(xi, flag, ns, elems, 0, s));
+        DWF_TRY(launch_rsub(xi, chi, elems, s));
+        // eta = D_O^-+ P_pv xi, kappa = D_Ob^-+ (D^+ eta on Omega-bar)   (PV)
+        DWF_TRY(project(hp, *dp, xi, t1, nrhs, s));
+        m.keep = 1;
+        st = masked_solve(m, eta, t1, work, sp->tol, sp->maxiter, stats + 4 * nrhs, true);
+        if (st != DWF_OK) return st;
+        DWF_TRY(op_apply_d(hp, t1, eta, 1, DWF_FP64, nrhs, hp->d_tmp, s));
+        DWF_TRY(launch_mask(t1, flag, ns, elems, 1, s));
+        m.keep = 0;
+        st = masked_solve(m, kappa, t1, work, sp->tol, sp->maxiter, stats + 5 * nrhs, true);
+        if (st != DWF_OK) return st;
+        // the four insertions
+        DWF_TRY(launch_scale_mask(zeta, W0, flag, ns, elems, 2, 2.0, s));     // 2 zeta
+        DWF_TRY(launch_scale_mask(zeta, W1, flag, ns, elems, 1, -2.0, s));    // -2 zeta on Omega-bar
+        DWF_TRY(force_bilinear(hl, out, W0, y, DWF_FP64, nrhs, active, accumulate, s));
+        DWF_TRY(force_bilinear(hl, out, W1, u_l, DWF_FP64, nrhs, active, 1, s));
+        DWF_TRY(copy_field(W2, b, elems, s));
+        DWF_TRY(launch_rsub(W2, d, elems, s));                                  // d - b
+        DWF_TRY(launch_scale_mask(eta, W3, flag, ns, elems, 2, 2.0, s));
+        DWF_TRY(force_bilinear(hp, out, W3, W2, DWF_FP64, nrhs, active, 1, s));
+        DWF_TRY(copy_field(W2, u_pv, elems, s));
+        DWF_TRY(launch_rsub(W2, b, elems, s));                                  // b - u_pv
+        DWF_TRY(launch_scale_mask(kappa, W3, flag, ns, elems, 2, 2.0, s));
+        DWF_TRY(force_bilinear(hp, out, W3, W2, DWF_FP64, nrhs, active, 1, s));
         return DWF_OK;
     };
     const dwf_status st = run();

@@ -188,6 +188,9 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best);
 dwf_status boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                             cudaStream_t s);
 void free_boundary_cache(dwf_handle* h);
+dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* omega, double* out, const double* phi,
+                                int nrhs, const dwf_box* active, int accumulate, const dwf_solver_params* sp,
+                                dwf_solver_stats* stats, cudaStream_t s);
 dwf_status boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                       const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
 dwf_status chebyshev_filter(dwf_handle* h, void* out, const void* in, int order, double lo, double hi,

@@ -101,6 +101,8 @@ def lib():
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
             "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
             "dwf_boundary_r": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+            "dwf_boundary_ratio_force": [vp, vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i,
+                                         C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
                                    C.POINTER(SolverStats), vp],
             "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
@@ -355,6 +357,18 @@ class Handle:
         st = (SolverStats * (2 * nrhs))()
         _check(lib().dwf_boundary_r(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
                                     C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
+
+    def boundary_ratio_force(self, pv, out, phi, omega, nrhs=1, active=None, accumulate=False, tol=1e-10,
+                             inner=FP32, stream=None):
+        """out[lex, mu] = link force of |R^-1 R_pv phi|^2, R on this handle,
+        R_pv on the Pauli-Villars handle ``pv``; returns the stats of the six
+        solves (6 * nrhs dicts: b, d, y, adjoint light, eta, kappa)."""
+        sp = SolverParams(tol, 100000, 0.0, 16, 0, inner, 0.0, 8, None, 0, 0)
+        st = (SolverStats * (6 * nrhs))()
+        box = C.byref(self._box(active)) if active is not None else None
+        _check(lib().dwf_boundary_ratio_force(self._h, pv._h, C.byref(self._box(omega)), _ptr(out), _ptr(phi),
+                                              nrhs, box, int(accumulate), C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
 
     def boundary_force(self, out, phi, omega, nrhs=1, active=None, accumulate=False, tol=1e-10,

@@ -239,3 +239,31 @@ def test_r_inverts_rinv_two_direction_band(prm):
     assert all(s["true_resid"] <= 2e-11 for s in stats)
     h.boundary_project(proj, src, box)
     assert LY.rel_l2(_host(out, dims, Ls)[0][0], _host(proj, dims, Ls)[0][0]) <= 1e-8
+
+
+@pytest.mark.parametrize("light,pv", [(SHAMIR, O.DWFParams(M5=1.8, mf=1.0)),
+                                      (MOBIUS, O.DWFParams(M5=1.8, mf=1.0, b5=1.5, c5=0.5))],
+                         ids=["shamir", "mobius"])
+def test_ratio_force_matches_oracle(light, pv):
+    """Force of |R^-1 R_pv phi|^2 on the slab against the dense oracle (itself
+    pinned by finite differences), then with the boundary links inactive."""
+    from oracle.force import box_links, ratio_action_force_dense
+    dims, Ls = (4, 2, 2, 2), 4
+    rng = np.random.default_rng(43)
+    U = inputs.gauge_field(dims, "haar", rng=rng)
+    phi = inputs.gaussian_source(dims, Ls, rng=rng)
+    box = O.band_box(dims, 2, dirs=(0,))
+    want = ratio_action_force_dense(U, phi, light, pv, box)
+    hl = _handle(dims, Ls, light, U)
+    hp = _handle(dims, Ls, pv, U)
+    src = _dev([[phi]], dims)
+    out = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
+    stats = hl.boundary_ratio_force(hp, out, src, box, tol=1e-12)
+    assert len(stats) == 6 and all(s["true_resid"] <= 1e-11 for s in stats)
+    got = torch.view_as_complex(out.view(-1, 2).cpu()).numpy().reshape(U.shape)
+    assert LY.rel_l2(got, want) <= 1e-9
+    act_box = ((1, 0, 0, 0), (2, 2, 2, 2))
+    act = box_links(dims, act_box)
+    hl.boundary_ratio_force(hp, out, src, box, active=act_box, tol=1e-12)
+    got = torch.view_as_complex(out.view(-1, 2).cpu()).numpy().reshape(U.shape)
+    assert LY.rel_l2(got, want * act[..., None, None]) <= 1e-9
