@@ -353,10 +353,11 @@ dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, d
  *   R = P - P D_Omega^-1 D_partial D_Omega-bar^-1 D_partialbar   (on the range of P),
  * out = u - P D_Omega^-1 (D b on Omega), b = D_Omega-bar^-1 (D u on Omega-bar),
  * u = P in.  The two Dirichlet solves (on the band Omega-bar, which is not a
- * box, and on Omega) run as FP64 CGNR on P_S D P_S to sp->tol (maxiter
- * sp->maxiter; the other fields of sp are ignored); stats: 2 * nrhs entries
- * (the Omega-bar solve, then the Omega solve).  Same handle, field and Omega
- * rules as dwf_boundary_project; allocates seven full FP64 fields for the
+ * box, and on Omega) run as CGNR on P_S D P_S to sp->tol (maxiter
+ * sp->maxiter): in FP64 if sp->inner_prec is DWF_FP64, else FP32 CGNR rounds
+ * with FP64 defect correction; stats: 2 * nrhs entries (the Omega-bar solve,
+ * then the Omega solve).  Same handle, field and Omega
+ * rules as dwf_boundary_project; allocates ten full FP64 fields for the
  * call.  DWF_ERR_NOT_CONVERGED if a solve misses 2 * tol. */
 dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                           const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
@@ -388,11 +389,11 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
  * (zeta on Omega-bar)) on Omega, eta = D_O^-+ P_pv xi and kappa = D_Ob^-+
  * (D^+ eta on Omega-bar) (PV): the four PV local solves and two light solves
  * the paper counts.  Light solves: dwf_cgne_solve with `sp`; PV Dirichlet
- * solves: FP64 CGNR to sp->tol.  stats: 6 * nrhs entries in the order b, d,
+ * solves: CGNR to sp->tol as in dwf_boundary_r.  stats: 6 * nrhs entries in the order b, d,
  * y, the adjoint light solve, eta, kappa.  `active` and `accumulate` as in
  * dwf_force (with the boundary links inactive the crossing terms vanish, as
  * in the paper).  Same field and Omega rules as dwf_boundary_project;
- * allocates fifteen full FP64 fields for the call. */
+ * allocates eighteen full FP64 fields for the call. */
 dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const dwf_box* omega, double* out,
                                     const double* phi, int nrhs, const dwf_box* active, int accumulate,
                                     const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);

@@ -139,12 +139,13 @@ __global__ void k_boundary_project(const double2* __restrict__ in, double2* __re
 }
 
 // zero the sites whose flag equals `drop` (flag: 1 in Omega, 0 outside)
-__global__ void k_mask(double2* __restrict__ f, const int* __restrict__ in_omega, int64_t nsites,
-                       int per_site, int drop) {
+template <class V>   // double2 or float2
+__global__ void k_mask(V* __restrict__ f, const int* __restrict__ in_omega, int64_t nsites, int per_site,
+                       int drop) {
     const int64_t total = nsites * per_site;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
          id += (int64_t)gridDim.x * blockDim.x)
-        if (in_omega[id / per_site] == drop) f[id] = make_double2(0.0, 0.0);
+        if (in_omega[id / per_site] == drop) f[id] = V{0, 0};
 }
 
 // out = a - out
@@ -543,10 +544,12 @@ namespace dwf {
 
 namespace {
 
-// per right-hand side partial sums of Re <a, b> over full FP64 fields:
-// grid (nblk, nrhs), block (b, r) sums the rows of rhs r it strides over
-__global__ void k_dot_rhs(const double2* __restrict__ a, const double2* __restrict__ b, int64_t nrows, int Ls,
-                          int nrhs, double* __restrict__ partial) {
+// per right-hand side partial sums of Re <a, b> over full fields (FP64 or
+// FP32 elements, FP64 sums): grid (nblk, nrhs), block (b, r) sums the rows of
+// rhs r it strides over
+template <class V>
+__global__ void k_dot_rhs(const V* __restrict__ a, const V* __restrict__ b, int64_t nrows, int Ls, int nrhs,
+                          double* __restrict__ partial) {
     __shared__ double red[256];
     const int r = blockIdx.y;
     double acc = 0.0;
@@ -555,8 +558,8 @@ __global__ void k_dot_rhs(const double2* __restrict__ a, const double2* __restri
         const int64_t row = e / Ls;
         const int sidx = (int)(e - row * Ls);
         const int64_t i = (row * nrhs + r) * Ls + sidx;
-        const double2 x = a[i], y = b[i];
-        acc += x.x * y.x + x.y * y.y;
+        const V x = a[i], y = b[i];
+        acc += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -568,18 +571,21 @@ __global__ void k_dot_rhs(const double2* __restrict__ a, const double2* __restri
 }
 
 // y = a_r x + b_r y per right-hand side (scalars from a device array [2][nrhs])
-__global__ void k_axpby_rhs(const double2* __restrict__ x, double2* __restrict__ y, const double* __restrict__ ab,
-                            int64_t n, int Ls, int nrhs) {
+template <class V>
+__global__ void k_axpby_rhs(const V* __restrict__ x, V* __restrict__ y, const double* __restrict__ ab, int64_t n,
+                            int Ls, int nrhs) {
+    using R = decltype(V{}.x);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)((i / Ls) % nrhs);
-        const double al = ab[r], be = ab[nrhs + r];
-        const double2 u = x[i], v = y[i];
-        y[i] = make_double2(al * u.x + be * v.x, al * u.y + be * v.y);
+        const R al = (R)ab[r], be = (R)ab[nrhs + r];
+        const V u = x[i], v = y[i];
+        y[i] = V{al * u.x + be * v.x, al * u.y + be * v.y};
     }
 }
 
 constexpr int kDotBlocks = 256;
 
+// CGNR building blocks on P_S D P_S for fields of one precision (FP64 or FP32)
 struct MaskedCG {
     dwf_handle* h;
     const int* flag;   // per full-field site: 1 in Omega, 0 outside
@@ -590,23 +596,34 @@ struct MaskedCG {
     double* ab;        // [2][nrhs]
     std::vector<double> hpart;
     cudaStream_t s;
+    dwf_prec prec = DWF_FP64;
 
-    dwf_status mask(double* f) {
-        k_mask<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<double2*>(f), flag, ns, (int)(elems / ns),
-                                               1 - keep);
+    size_t field_bytes() const { return (size_t)elems * (prec == DWF_FP64 ? 16 : 8); }
+    void* at(void* base, int k) const { return (char*)base + (size_t)k * field_bytes(); }
+
+    dwf_status mask(void* f) {
+        if (prec == DWF_FP64)
+            k_mask<<<grid_for(elems), 256, 0, s>>>(static_cast<double2*>(f), flag, ns, (int)(elems / ns), 1 - keep);
+        else
+            k_mask<<<grid_for(elems), 256, 0, s>>>(static_cast<float2*>(f), flag, ns, (int)(elems / ns), 1 - keep);
         note_launch();
         DWF_CUDA(cudaGetLastError());
         return DWF_OK;
     }
     // out = P_S D(^+) P_S in (in supported on S)
-    dwf_status apply(double* out, const double* in, int dagger) {
-        DWF_TRY(op_apply_d(h, out, in, dagger, DWF_FP64, nrhs, h->d_tmp, s));
+    dwf_status apply(void* out, const void* in, int dagger) {
+        DWF_TRY(op_apply_d(h, out, in, dagger, prec, nrhs, h->d_tmp, s));
         return mask(out);
     }
-    dwf_status dot(const double* a, const double* b, std::vector<double>& out) {
-        k_dot_rhs<<<dim3(kDotBlocks, nrhs), 256, 0, s>>>(reinterpret_cast<const double2*>(a),
-                                                         reinterpret_cast<const double2*>(b), ns * 12,
-                                                         h->p.Ls, nrhs, part);
+    dwf_status dot(const void* a, const void* b, std::vector<double>& out) {
+        if (prec == DWF_FP64)
+            k_dot_rhs<<<dim3(kDotBlocks, nrhs), 256, 0, s>>>(static_cast<const double2*>(a),
+                                                             static_cast<const double2*>(b), ns * 12, h->p.Ls,
+                                                             nrhs, part);
+        else
+            k_dot_rhs<<<dim3(kDotBlocks, nrhs), 256, 0, s>>>(static_cast<const float2*>(a),
+                                                             static_cast<const float2*>(b), ns * 12, h->p.Ls,
+                                                             nrhs, part);
         note_launch();
         DWF_CUDA(cudaGetLastError());
         DWF_CUDA(cudaMemcpyAsync(hpart.data(), part, hpart.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -616,15 +633,19 @@ struct MaskedCG {
             for (int k = 0; k < kDotBlocks; ++k) out[r] += hpart[(size_t)r * kDotBlocks + k];
         return DWF_OK;
     }
-    dwf_status axpby(const double* x, double* y, const std::vector<double>& a, const std::vector<double>& b) {
+    dwf_status axpby(const void* x, void* y, const std::vector<double>& a, const std::vector<double>& b) {
         std::vector<double> hab(2 * nrhs);
         for (int r = 0; r < nrhs; ++r) {
             hab[r] = a[r];
             hab[nrhs + r] = b[r];
         }
         DWF_CUDA(cudaMemcpyAsync(ab, hab.data(), hab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        k_axpby_rhs<<<grid_for(elems), 256, 0, s>>>(reinterpret_cast<const double2*>(x),
-                                                    reinterpret_cast<double2*>(y), ab, elems, h->p.Ls, nrhs);
+        if (prec == DWF_FP64)
+            k_axpby_rhs<<<grid_for(elems), 256, 0, s>>>(static_cast<const double2*>(x), static_cast<double2*>(y), ab,
+                                                        elems, h->p.Ls, nrhs);
+        else
+            k_axpby_rhs<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(x), static_cast<float2*>(y), ab,
+                                                        elems, h->p.Ls, nrhs);
         note_launch();
         DWF_CUDA(cudaGetLastError());
         DWF_CUDA(cudaStreamSynchronize(s));   // hab is reused by the next call
@@ -632,25 +653,26 @@ struct MaskedCG {
     }
 };
 
-// x = (P_S D P_S)^-1 b on the site set S by CGNR (FP64, one CG per right-hand
-// side in shared launches); b supported on S.  work: four full fields.
-dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, double tol, int maxiter,
-                        dwf_solver_stats* stats, bool adjoint = false) {
+// x = (P_S D P_S)^-1 b (or the adjoint system) on the site set S by CGNR in
+// the precision of m (one CG per right-hand side in shared launches); b
+// supported on S.  work: four fields of that precision.
+dwf_status masked_cgnr(MaskedCG& m, void* x, const void* b, void* work, double tol, int maxiter,
+                       dwf_solver_stats* stats, bool adjoint) {
     // the operator is P_S D P_S, or its adjoint P_S D^+ P_S
     const int op = adjoint ? 1 : 0, op_adj = adjoint ? 0 : 1;
     const auto t0 = std::chrono::steady_clock::now();
     const int nrhs = m.nrhs;
-    const int64_t e2 = 2 * m.elems;
-    double* r = work;
-    double* z = work + e2;
-    double* p = work + 2 * e2;
-    double* w = work + 3 * e2;
-    std::vector<double> bn2, zz, zz_new, ww, rr, one(nrhs, 1.0), zero(nrhs, 0.0), al(nrhs), mal(nrhs), be(nrhs);
+    const size_t fb = m.field_bytes();
+    void* r = m.at(work, 0);
+    void* z = m.at(work, 1);
+    void* p = m.at(work, 2);
+    void* w = m.at(work, 3);
+    std::vector<double> bn2, zz, zz_new, ww, rr, one(nrhs, 1.0), al(nrhs), mal(nrhs), be(nrhs);
     DWF_TRY(m.dot(b, b, bn2));
-    DWF_CUDA(cudaMemsetAsync(x, 0, m.elems * 16, m.s));
-    DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_CUDA(cudaMemsetAsync(x, 0, fb, m.s));
+    DWF_CUDA(cudaMemcpyAsync(r, b, fb, cudaMemcpyDeviceToDevice, m.s));
     DWF_TRY(m.apply(z, r, op_adj));
-    DWF_CUDA(cudaMemcpyAsync(p, z, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_CUDA(cudaMemcpyAsync(p, z, fb, cudaMemcpyDeviceToDevice, m.s));
     DWF_TRY(m.dot(z, z, zz));
     std::vector<int> done(nrhs, 0), iters(nrhs, 0);
     int it = 0;
@@ -679,9 +701,9 @@ dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, d
         DWF_TRY(m.axpby(z, p, one, be));    // p = z + beta p
         zz = zz_new;
     }
-    // true residual |b - (operator) x| / |b|
+    // true residual |b - (operator) x| / |b| in the working precision
     DWF_TRY(m.apply(w, x, op));
-    DWF_CUDA(cudaMemcpyAsync(r, b, m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    DWF_CUDA(cudaMemcpyAsync(r, b, fb, cudaMemcpyDeviceToDevice, m.s));
     DWF_TRY(m.axpby(w, r, std::vector<double>(nrhs, -1.0), one));
     DWF_TRY(m.dot(r, r, rr));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -690,6 +712,67 @@ dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work, d
         dwf_solver_stats st{};
         st.iters = done[k] ? iters[k] : it;
         st.op_applies = 2 * st.iters + 2;
+        st.true_resid = bn2[k] > 0 ? std::sqrt(rr[k] / bn2[k]) : 0.0;
+        st.seconds = secs;
+        const dwf_status sk = st.true_resid <= 2 * tol ? DWF_OK : DWF_ERR_NOT_CONVERGED;
+        st.status = (int)sk;
+        if (sk != DWF_OK) worst = sk;
+        stats[k] = st;
+    }
+    return worst;
+}
+
+// Dirichlet solve on the site set S: FP64 CGNR, or (inner = FP32) FP32 CGNR
+// rounds to 1e-5 of the current residual with FP64 defect correction
+// x += e, r = b - P_S D P_S x until |r| <= tol |b| in FP64.
+// work64: four FP64 fields; work32: six FP32 fields (unused for FP64).
+dwf_status masked_solve(MaskedCG& m, double* x, const double* b, double* work64, void* work32, double tol,
+                        int maxiter, dwf_solver_stats* stats, bool adjoint = false, dwf_prec inner = DWF_FP64) {
+    m.prec = DWF_FP64;
+    if (inner == DWF_FP64) return masked_cgnr(m, x, b, work64, tol, maxiter, stats, adjoint);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nrhs = m.nrhs;
+    const int op = adjoint ? 1 : 0;
+    double* r = work64;
+    double* t = work64 + 2 * m.elems;
+    std::vector<double> bn2, rr, one(nrhs, 1.0), mone(nrhs, -1.0);
+    std::vector<dwf_solver_stats> inner_st(nrhs);
+    std::vector<int> total(nrhs, 0);
+    DWF_TRY(m.dot(b, b, bn2));
+    DWF_CUDA(cudaMemsetAsync(x, 0, (size_t)m.elems * 16, m.s));
+    DWF_CUDA(cudaMemcpyAsync(r, b, (size_t)m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+    int rounds = 0;
+    for (; rounds < 30; ++rounds) {
+        m.prec = DWF_FP64;
+        DWF_TRY(m.dot(r, r, rr));
+        bool all = true;
+        for (int k = 0; k < nrhs; ++k) all = all && rr[k] <= tol * tol * bn2[k];
+        if (all) break;
+        // FP32 correction e with (operator) e = r to 1e-5
+        m.prec = DWF_FP32;
+        void* r32 = m.at(work32, 0);
+        void* e32 = m.at(work32, 1);
+        void* w32 = m.at(work32, 2);
+        DWF_TRY(launch_convert(r32, DWF_FP32, r, DWF_FP64, (size_t)m.elems, m.s));
+        const dwf_status st = masked_cgnr(m, e32, r32, w32, 1e-5, maxiter, inner_st.data(), adjoint);
+        if (st != DWF_OK && st != DWF_ERR_NOT_CONVERGED) return st;
+        for (int k = 0; k < nrhs; ++k) total[k] += inner_st[k].iters;
+        m.prec = DWF_FP64;
+        DWF_TRY(launch_convert(t, DWF_FP64, e32, DWF_FP32, (size_t)m.elems, m.s));
+        DWF_TRY(m.axpby(t, x, one, one));           // x += e
+        DWF_TRY(m.apply(t, x, op));                 // r = b - (operator) x
+        DWF_CUDA(cudaMemcpyAsync(r, b, (size_t)m.elems * 16, cudaMemcpyDeviceToDevice, m.s));
+        DWF_TRY(m.axpby(t, r, mone, one));
+    }
+    m.prec = DWF_FP64;
+    DWF_TRY(m.dot(r, r, rr));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    dwf_status worst = DWF_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        dwf_solver_stats st{};
+        st.iters = total[k];
+        st.reliable_updates = rounds;
+        st.op_applies = 2 * total[k] + 2 * rounds;
         st.true_resid = bn2[k] > 0 ? std::sqrt(rr[k] / bn2[k]) : 0.0;
         st.seconds = secs;
         const dwf_status sk = st.true_resid <= 2 * tol ? DWF_OK : DWF_ERR_NOT_CONVERGED;
@@ -724,28 +807,31 @@ dwf_status boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const do
         DWF_CUDA(cudaStreamSynchronize(s));
         return DWF_OK;
     }
-    double* scratch = nullptr;   // u, a, b, 4 CG work fields, and the reduction buffers
+    // u, a, b, four FP64 and six FP32 solver work fields, the reduction buffers
+    double* scratch = nullptr;
     const size_t fb = (size_t)elems * 16;
-    DWF_CUDA(cudaMalloc(&scratch, 7 * fb + ((size_t)kDotBlocks + 2) * nrhs * sizeof(double)));
+    DWF_CUDA(cudaMalloc(&scratch, 10 * fb + ((size_t)kDotBlocks + 2) * nrhs * sizeof(double)));
     double* u = scratch;
     double* a = scratch + 2 * elems;
     double* b = scratch + 4 * elems;
     double* work = scratch + 6 * elems;
-    MaskedCG m{h, dt.in_omega, 0, nrhs, ns, elems, scratch + 14 * elems,
-               scratch + 14 * elems + (size_t)kDotBlocks * nrhs, std::vector<double>((size_t)kDotBlocks * nrhs), s};
+    void* work32 = scratch + 14 * elems;
+    MaskedCG m{h, dt.in_omega, 0, nrhs, ns, elems, scratch + 20 * elems,
+               scratch + 20 * elems + (size_t)kDotBlocks * nrhs, std::vector<double>((size_t)kDotBlocks * nrhs), s};
+    const dwf_prec inner = sp->inner_prec == DWF_FP64 ? DWF_FP64 : DWF_FP32;
     auto run = [&]() -> dwf_status {
         // u = P psi; a = D u on Omega-bar; b = D_Omega-bar^-1 a
         DWF_TRY(project(h, dt, in, u, nrhs, s));
         DWF_TRY(op_apply_d(h, a, u, 0, DWF_FP64, nrhs, h->d_tmp, s));
         m.keep = 0;
         DWF_TRY(m.mask(a));
-        dwf_status st = masked_solve(m, b, a, work, sp->tol, sp->maxiter, stats);
+        dwf_status st = masked_solve(m, b, a, work, work32, sp->tol, sp->maxiter, stats, false, inner);
         if (st != DWF_OK) return st;
         // a = D b on Omega; b = D_Omega^-1 a
         DWF_TRY(op_apply_d(h, a, b, 0, DWF_FP64, nrhs, h->d_tmp, s));
         m.keep = 1;
         DWF_TRY(m.mask(a));
-        st = masked_solve(m, b, a, work, sp->tol, sp->maxiter, stats + nrhs);
+        st = masked_solve(m, b, a, work, work32, sp->tol, sp->maxiter, stats + nrhs, false, inner);
         if (st != DWF_OK) return st;
         // out = u - P b
         DWF_TRY(project(h, dt, b, out, nrhs, s));
@@ -838,7 +924,7 @@ dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* o
         DWF_CUDA(cudaStreamSynchronize(s));
         return DWF_OK;
     }
-    constexpr int NF = 15;
+    constexpr int NF = 18;   // 15 FP64 fields, then six FP32 solver work fields
     double* scratch = nullptr;
     const size_t red = ((size_t)kDotBlocks + 2) * nrhs * sizeof(double);
     DWF_CUDA(cudaMalloc(&scratch, NF * (size_t)elems * 16 + red));
@@ -846,7 +932,9 @@ dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* o
     for (int k = 0; k < NF; ++k) F[k] = scratch + 2 * elems * k;
     double *u_pv = F[0], *t1 = F[1], *b = F[2], *d = F[3], *u_l = F[4], *chi = F[5], *y = F[6], *zeta = F[7],
            *xi = F[8], *eta = F[9], *kappa = F[10], *W0 = F[11], *W1 = F[12], *W2 = F[13], *W3 = F[14];
-    double* work = F[11];   // the masked solves' four work fields W0..W3
+    double* work = F[11];   // the masked solves' four FP64 work fields W0..W3
+    void* work32 = F[15];
+    const dwf_prec inner = sp->inner_prec == DWF_FP64 ? DWF_FP64 : DWF_FP32;
     double* part = scratch + 2 * elems * NF;
     MaskedCG m{hp, dp->in_omega, 0, nrhs, ns, elems, part, part + (size_t)kDotBlocks * nrhs,
                std::vector<double>((size_t)kDotBlocks * nrhs), s};
@@ -857,12 +945,12 @@ dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* o
         DWF_TRY(project(hp, *dp, phi, u_pv, nrhs, s));
         DWF_TRY(op_apply_d(hp, t1, u_pv, 0, DWF_FP64, nrhs, hp->d_tmp, s));
         DWF_TRY(launch_mask(t1, flag, ns, elems, 1, s));
-        dwf_status st = masked_solve(m, b, t1, work, sp->tol, sp->maxiter, stats);
+        dwf_status st = masked_solve(m, b, t1, work, work32, sp->tol, sp->maxiter, stats, false, inner);
         if (st != DWF_OK) return st;
         DWF_TRY(op_apply_d(hp, t1, b, 0, DWF_FP64, nrhs, hp->d_tmp, s));
         DWF_TRY(launch_mask(t1, flag, ns, elems, 0, s));
         m.keep = 1;
-        st = masked_solve(m, d, t1, work, sp->tol, sp->maxiter, stats + nrhs);
+        st = masked_solve(m, d, t1, work, work32, sp->tol, sp->maxiter, stats + nrhs, false, inner);
         if (st != DWF_OK) return st;
         DWF_TRY(project(hp, *dp, d, t1, nrhs, s));
         DWF_TRY(launch_rsub(t1, u_pv, elems, s));                       // t1 = w
@@ -891,12 +979,12 @@ dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* o
         // eta = D_O^-+ P_pv xi, kappa = D_Ob^-+ (D^+ eta on Omega-bar)   (PV)
         DWF_TRY(project(hp, *dp, xi, t1, nrhs, s));
         m.keep = 1;
-        st = masked_solve(m, eta, t1, work, sp->tol, sp->maxiter, stats + 4 * nrhs, true);
+        st = masked_solve(m, eta, t1, work, work32, sp->tol, sp->maxiter, stats + 4 * nrhs, true, inner);
         if (st != DWF_OK) return st;
         DWF_TRY(op_apply_d(hp, t1, eta, 1, DWF_FP64, nrhs, hp->d_tmp, s));
         DWF_TRY(launch_mask(t1, flag, ns, elems, 1, s));
         m.keep = 0;
-        st = masked_solve(m, kappa, t1, work, sp->tol, sp->maxiter, stats + 5 * nrhs, true);
+        st = masked_solve(m, kappa, t1, work, work32, sp->tol, sp->maxiter, stats + 5 * nrhs, true, inner);
         if (st != DWF_OK) return st;
         // the four insertions
         DWF_TRY(launch_scale_mask(zeta, W0, flag, ns, elems, 2, 2.0, s));     // 2 zeta

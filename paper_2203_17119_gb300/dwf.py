@@ -350,10 +350,11 @@ class Handle:
                                        C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
 
-    def boundary_r(self, out, inp, omega, nrhs=1, tol=1e-10, maxiter=20000, stream=None):
-        """out = R in (FP64 Dirichlet solves on Omega-bar and Omega); returns the
-        stats of the two solves (2 * nrhs dicts)."""
-        sp = SolverParams(tol, maxiter, 0.0, 16, 0, FP64, 0.0, 8, None, 0, 0)
+    def boundary_r(self, out, inp, omega, nrhs=1, tol=1e-10, maxiter=20000, inner=FP32, stream=None):
+        """out = R in (Dirichlet solves on Omega-bar and Omega: FP64 CGNR, or
+        FP32 CGNR with FP64 defect correction); returns the stats of the two
+        solves (2 * nrhs dicts)."""
+        sp = SolverParams(tol, maxiter, 0.0, 16, 0, inner, 0.0, 8, None, 0, 0)
         st = (SolverStats * (2 * nrhs))()
         _check(lib().dwf_boundary_r(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(inp), nrhs,
                                     C.byref(sp), st, _stream(stream)))

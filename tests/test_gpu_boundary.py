@@ -190,9 +190,12 @@ def test_boundary_action_force_matches_oracle(prm):
     assert LY.rel_l2(got2, want + want * act[..., None, None]) <= 1e-9
 
 
-def test_r_matches_dense_oracle_and_inverts_rinv():
-    """R = P - P D_O^-1 D_d D_Ob^-1 D_db on the slab against the dense oracle;
-    then R (R^-1 psi) = P psi (Sec. 2.1) with both library calls."""
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_r_matches_dense_oracle_and_inverts_rinv(inner):
+    """R = P - P D_O^-1 D_d D_Ob^-1 D_db on the slab against the dense oracle
+    (Dirichlet solves by FP64 CGNR, or FP32 CGNR with FP64 defect
+    correction); then R (R^-1 psi) = P psi (Sec. 2.1) with both library calls."""
+    prec = G.FP64 if inner == "fp64" else G.FP32
     dims, Ls = (4, 2, 2, 2), 4
     rng = np.random.default_rng(99)
     U = inputs.gauge_field(dims, "haar", rng=rng)
@@ -209,7 +212,7 @@ def test_r_matches_dense_oracle_and_inverts_rinv():
     h = _handle(dims, Ls, MOBIUS, U, 2)
     src = _dev([psis], dims)
     out = torch.zeros_like(src)
-    stats = h.boundary_r(out, src, box, nrhs=2, tol=1e-12)
+    stats = h.boundary_r(out, src, box, nrhs=2, tol=1e-12, inner=prec)
     assert len(stats) == 4 and all(s["true_resid"] <= 2e-12 for s in stats)
     got = _host(out, dims, Ls)[0]
     for r in range(2):
@@ -219,7 +222,7 @@ def test_r_matches_dense_oracle_and_inverts_rinv():
     # R R^-1 = P
     rinv = torch.zeros_like(src)
     h.boundary_rinv(rinv, src, box, nrhs=2, tol=1e-12)
-    h.boundary_r(out, rinv, box, nrhs=2, tol=1e-12)
+    h.boundary_r(out, rinv, box, nrhs=2, tol=1e-12, inner=prec)
     proj = torch.zeros_like(src)
     h.boundary_project(proj, src, box, nrhs=2)
     assert LY.rel_l2(_host(out, dims, Ls)[0][0], _host(proj, dims, Ls)[0][0]) <= 1e-9
