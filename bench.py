@@ -106,6 +106,22 @@ class Clocks:
 
 
 # ------------------------------------------------------------- our arm
+def job_time_ms(local_ms, world, device=None):
+    """The job's time for the timed steps: the slowest rank's (the ranks meet at
+    a barrier on both sides of the timed region).  world = 1: local_ms."""
+    if world == 1:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, flops_per_rank, job_ms):
+    """Whole-job throughput (TFLOP/s): every rank's work over the slowest rank's time."""
+    return world * flops_per_rank / (job_ms * 1e-3) / 1e12
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -187,11 +203,8 @@ def run_ours(args, rank, world):
     times = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(times)
     tot_flops = sum(flops(s) for s in all_stats)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * tot_flops / (tot_ms * 1e-3) / 1e12
+    tot_ms = job_time_ms(tot_ms, world, dev)
+    value = job_value(world, tot_flops, tot_ms)
     last = all_stats[-1]
 
     # ---- end to end: host (pinned) source in, solution out, per step
