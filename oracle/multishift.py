@@ -83,3 +83,14 @@ def multishift_cg(apply_A, b, shifts, tol=1e-10, maxiter=100000):
         xs[s] = x[i]
         its[s] = int(iters[i])
     return xs, {"iters": its, "base_iters": k}
+
+
+def rational_apply(apply_A, b, a0, shifts, residues, tol=1e-10):
+    """r(A) b = a0 b + sum_i residues_i (A + shifts_i)^-1 b: a rational function
+    in partial fractions (the form the DD-RHMC action of Sec. 2.3.1 uses for
+    the powers of the normal operators), the shifted solves by multi-shift CG."""
+    xs, _ = multishift_cg(apply_A, b, shifts, tol=tol)
+    out = a0 * b
+    for r, x in zip(residues, xs):
+        out = out + r * x
+    return out

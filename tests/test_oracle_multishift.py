@@ -91,3 +91,19 @@ def test_order_of_shifts_does_not_matter(perm):
     for s, x in zip(shifts[perm], xs):
         ref = np.linalg.solve(A + s * np.eye(n), b)
         assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_rational_apply_is_the_partial_fraction_function():
+    """f(x) = (x + 3) / ((x + 1)(x + 2)) = 2/(x + 1) - 1/(x + 2) (+ a0) applied
+    to a Hermitian positive matrix equals f on its eigenvalues."""
+    from oracle.multishift import rational_apply
+    rng = np.random.default_rng(9)
+    n = 50
+    M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = M.conj().T @ M / n + 0.05 * np.eye(n)
+    w, V = np.linalg.eigh(A)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    got = rational_apply(lambda v: A @ v, b, 0.25, [1.0, 2.0], [2.0, -1.0], tol=1e-13)
+    f = 0.25 + (w + 3) / ((w + 1) * (w + 2))
+    want = V @ (f * (V.conj().T @ b))
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
