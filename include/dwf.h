@@ -398,6 +398,20 @@ dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const
                                     const double* phi, int nrhs, const dwf_box* active, int accumulate,
                                     const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
 
+/* Rational function of the normal Schur operator in partial fractions,
+ *   out = a0 in + sum_i residues[i] (M_pc^+ M_pc + shifts[i])^-1 in,
+ * the form the DD-RHMC action of Sec. 2.3.1 takes for the powers of the
+ * normal operators of D (whole-lattice handle) and of D_Omega (box handle),
+ * e.g. the (D_dir^+ D_dir)^(1/4) and (D^+ D)^(-1/2) factors with the
+ * caller's (Remez) coefficients.  One dwf_multishift_solve (same sp, stats
+ * [n][nbox * nrhs]) and n + 1 axpby passes.  in, out: distinct odd cb FP64
+ * fields; shifts, residues: host arrays of n values (shifts >= 0).  Returns
+ * the multi-shift status (out is formed from the last iterates on
+ * DWF_ERR_NOT_CONVERGED); allocates n odd cb FP64 fields for the call. */
+dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
+                              const double* residues, int n, int nrhs, const dwf_solver_params* sp,
+                              dwf_solver_stats* stats, void* stream);
+
 /* Chebyshev filter of the normal Schur operator: the recursively built
  * filter functions of Sec. 4 for a fast multigrid set-up of the local
  * solves.  out = T_order(z(A)) in with A = M_pc^+ M_pc (on a box handle each

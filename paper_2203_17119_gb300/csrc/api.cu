@@ -314,6 +314,13 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
     return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
+                              const double* residues, int n, int nrhs, const dwf_solver_params* sp,
+                              dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    return rational_apply(h, out, in, a0, shifts, residues, n, nrhs, sp, stats, (cudaStream_t)stream);
+}
+
 dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int order, double lo, double hi,
                                 dwf_prec prec, int nrhs, void* stream) {
     DWF_TRY(check_handle(h));

@@ -202,6 +202,9 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
                          const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
 dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                           const dwf_box* active, int accumulate, cudaStream_t s);
+dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
+                          const double* residues, int n, int nrhs, const dwf_solver_params* sp,
+                          dwf_solver_stats* stats, cudaStream_t s);
 dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
                             int nshift, int nrhs, const dwf_solver_params* sp,
                             dwf_solver_stats* stats, cudaStream_t s);

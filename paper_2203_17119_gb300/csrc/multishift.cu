@@ -370,4 +370,32 @@ dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const dou
     return res;
 }
 
+// r(A) b = a0 b + sum_i residues_i (A + shifts_i)^-1 b, A = M_pc^+ M_pc (each
+// box's on a box handle): a rational function in partial fractions, the form
+// the DD-RHMC action takes for the powers of the normal operators of D and
+// D_Omega (Sec. 2.3.1), from one multi-shift solve.
+dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
+                          const double* residues, int n, int nrhs, const dwf_solver_params* sp,
+                          dwf_solver_stats* stats, cudaStream_t s) {
+    if (out == nullptr || in == nullptr || out == in || residues == nullptr || n < 1 || nrhs < 1 ||
+        nrhs > h->nrhs_max) {
+        set_error("rational: bad arguments (distinct fields, n >= 1, 1 <= nrhs <= nrhs_max)");
+        return DWF_ERR_ARG;
+    }
+    const size_t no = cb_elems(h, 1, nrhs);
+    const int T = tile_for(h, nrhs);
+    DevBuf x;
+    DWF_TRY(dev_alloc(x, (size_t)n * no * 16));
+    double* xs = static_cast<double*>(x.p);
+    const dwf_status st = multishift_solve(h, xs, in, shifts, n, nrhs, sp, stats, s);
+    if (st != DWF_OK && st != DWF_ERR_NOT_CONVERGED) return st;
+    DWF_CUDA(cudaMemsetAsync(out, 0, no * 16, s));
+    DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, a0, in, DWF_FP64, nullptr, 1.0, out, DWF_FP64, nullptr, T, s));
+    for (int i = 0; i < n; ++i)
+        DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, residues[i], xs + (size_t)i * no * 2, DWF_FP64, nullptr, 1.0,
+                             out, DWF_FP64, nullptr, T, s));
+    DWF_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
 }  // namespace dwf

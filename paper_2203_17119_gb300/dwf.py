@@ -99,6 +99,8 @@ def lib():
                                      C.POINTER(SolverStats), vp],
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
+            "dwf_rational_apply": [vp, vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), i, i,
+                                   C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
             "dwf_boundary_r": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_boundary_ratio_force": [vp, vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i,
@@ -382,6 +384,21 @@ class Handle:
         _check(lib().dwf_boundary_force(self._h, C.byref(self._box(omega)), _ptr(out), _ptr(phi), nrhs, box,
                                         int(accumulate), C.byref(sp), st, _stream(stream)))
         return [s.as_dict() for s in st]
+
+    def rational_apply(self, out, inp, a0, shifts, residues, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64,
+                       stream=None):
+        """out = a0 in + sum_i residues[i] (M_pc^+ M_pc + shifts[i])^-1 in (odd
+        cb FP64 fields); returns ([per shift: [per system: stats dict]], status)."""
+        n = len(shifts)
+        sh = (C.c_double * n)(*[float(v) for v in shifts])
+        rs = (C.c_double * n)(*[float(v) for v in residues])
+        sp = SolverParams(tol, maxiter, 0.0, 0, 0, inner, 0.0, 0, None, 0, 0)
+        nsys = max(len(self.boxes), 1) * nrhs
+        st = (SolverStats * (nsys * n))()
+        rc = lib().dwf_rational_apply(self._h, _ptr(out), _ptr(inp), float(a0), sh, rs, n, nrhs, C.byref(sp), st,
+                                      _stream(stream))
+        _check(rc)
+        return [[st[k * nsys + i].as_dict() for i in range(nsys)] for k in range(n)], rc
 
     def chebyshev_filter(self, out, inp, order, lo, hi, prec=FP64, nrhs=1, stream=None):
         """out = T_order(z(A)) in, A = M_pc^+ M_pc, z(lam) = (hi + lo - 2 lam)/(hi - lo)."""
