@@ -104,13 +104,15 @@ def _dense_D(U, shape, p):
     return Dn.dense_matrix(lambda f: O.apply_D(U, f, p), shape)
 
 
-def boundary_pieces_dense(U, phi, p: O.DWFParams, box):
-    """(u, y, chi, zeta, P, masks) of the boundary action for the box Omega."""
+def boundary_pieces_dense(U, phi, p: O.DWFParams, box, D=None):
+    """(u, y, chi, zeta, P, masks) of the boundary action for the box Omega
+    (D: the dense operator of U, if already built)."""
     from oracle import dense as Dn
     dims = O.lattice_dims(U)
     Ls = phi.shape[4]
     shape = phi.shape
-    D = _dense_D(U, shape, p)
+    if D is None:
+        D = _dense_D(U, shape, p)
     ids = O.box_id_field(dims, [box])
     om = Dn.site_mask_to_dofs(ids == 0, Ls * 12)
     ob = Dn.site_mask_to_dofs(ids < 0, Ls * 12)
@@ -128,9 +130,9 @@ def boundary_pieces_dense(U, phi, p: O.DWFParams, box):
             "zeta": zeta.reshape(shape), "P": P, "omega_bar": ids < 0}
 
 
-def boundary_action_dense(U, phi, p: O.DWFParams, box) -> float:
+def boundary_action_dense(U, phi, p: O.DWFParams, box, D=None) -> float:
     """S = |R^-1 phi|^2 with dense P and D^-1."""
-    pc = boundary_pieces_dense(U, phi, p, box)
+    pc = boundary_pieces_dense(U, phi, p, box, D)
     return float(np.vdot(pc["chi"], pc["chi"]).real)
 
 
@@ -155,11 +157,12 @@ def boundary_action_force_dense(U, phi, p: O.DWFParams, box, active=None) -> np.
 # and <xi, dR_pv phi> = <eta, dD (d - b)> + <kappa, dD (b - u_pv)> with the PV
 # local adjoint solves eta = D_O^-+ P_pv xi, kappa = D_Ob^-+ (D^+ eta on Omega-bar):
 # four PV local solves (b, d, eta, kappa) and two light solves (y, zeta).
-def _blocks_dense(U, shape, p, box):
+def _blocks_dense(U, shape, p, box, D=None):
     from oracle import dense as Dn
     dims = O.lattice_dims(U)
     Ls = shape[4]
-    D = _dense_D(U, shape, p)
+    if D is None:
+        D = _dense_D(U, shape, p)
     ids = O.box_id_field(dims, [box])
     om = Dn.site_mask_to_dofs(ids == 0, Ls * 12)
     ob = Dn.site_mask_to_dofs(ids < 0, Ls * 12)
@@ -180,10 +183,10 @@ def _dirichlet_solve(D, idx, rhs, adjoint=False):
     return x
 
 
-def ratio_pieces_dense(U, phi, p_light: O.DWFParams, p_pv: O.DWFParams, box):
+def ratio_pieces_dense(U, phi, p_light: O.DWFParams, p_pv: O.DWFParams, box, Dl=None, Dp=None):
     shape = phi.shape
-    Dl, Pl, om, ob = _blocks_dense(U, shape, p_light, box)
-    Dp, Pp, _, _ = _blocks_dense(U, shape, p_pv, box)
+    Dl, Pl, om, ob = _blocks_dense(U, shape, p_light, box, Dl)
+    Dp, Pp, _, _ = _blocks_dense(U, shape, p_pv, box, Dp)
     n = Dl.shape[0]
 
     def restrict(v, idx):
@@ -208,9 +211,9 @@ def ratio_pieces_dense(U, phi, p_light: O.DWFParams, p_pv: O.DWFParams, box):
     return r
 
 
-def ratio_action_dense(U, phi, p_light, p_pv, box) -> float:
+def ratio_action_dense(U, phi, p_light, p_pv, box, Dl=None, Dp=None) -> float:
     """S = |R^-1 R_pv phi|^2 with dense P, R, R_pv."""
-    pc = ratio_pieces_dense(U, phi, p_light, p_pv, box)
+    pc = ratio_pieces_dense(U, phi, p_light, p_pv, box, Dl, Dp)
     return float(np.vdot(pc["chi"], pc["chi"]).real)
 
 

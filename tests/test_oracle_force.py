@@ -123,6 +123,24 @@ def _expm_i(H, eps):
     return (V * np.exp(1j * eps * w)) @ np.conj(V.T)
 
 
+def _dense_after_link_change(D0, U2, prm, shape, site, mu):
+    """D(U2) from D(U) when only U_mu(site) changed: only the columns of the
+    link's two end sites change; they are rebuilt by applying D(U2)."""
+    t, z, y, x = site
+    dims = (shape[3], shape[2], shape[1], shape[0])
+    fwd = [x, y, z, t]
+    fwd[mu] = (fwd[mu] + 1) % dims[mu]
+    D = D0.copy()
+    per_site = shape[4] * 12
+    for (tt, zz, yy, xx) in {(t, z, y, x), (fwd[3], fwd[2], fwd[1], fwd[0])}:
+        lex = ((tt * shape[1] + zz) * shape[2] + yy) * shape[3] + xx
+        for j in range(lex * per_site, (lex + 1) * per_site):
+            e = np.zeros(int(np.prod(shape)), dtype=np.complex128)
+            e[j] = 1.0
+            D[:, j] = O.apply_D(U2, e.reshape(shape), prm).reshape(-1)
+    return D
+
+
 @pytest.mark.parametrize("prm", [SHAMIR, MOBIUS], ids=["shamir", "mobius"])
 def test_boundary_action_force_matches_finite_differences(prm):
     """Central differences of S(exp(i eps H) U) = |R^-1 phi|^2 (dense R^-1)
@@ -132,6 +150,8 @@ def test_boundary_action_force_matches_finite_differences(prm):
     phi = inputs.gaussian_source(SLAB, 4, rng=rng)
     box = O.band_box(SLAB, 2, dirs=(0,))          # Omega: x in {1, 2}
     F = boundary_action_force_dense(U, phi, prm, box)
+    from oracle import dense as Dn
+    D0 = Dn.dense_matrix(lambda f: O.apply_D(U, f, prm), phi.shape)
     eps = 1e-5
     # (t, z, y, x, mu): an x-link inside Omega, x-links across both faces, a
     # link in Omega-bar, a y-link in Omega
@@ -140,7 +160,9 @@ def test_boundary_action_force_matches_finite_differences(prm):
         Up, Um = U.copy(), U.copy()
         Up[t, z, y, x, mu] = _expm_i(H, eps) @ U[t, z, y, x, mu]
         Um[t, z, y, x, mu] = _expm_i(H, -eps) @ U[t, z, y, x, mu]
-        fd = (boundary_action_dense(Up, phi, prm, box) - boundary_action_dense(Um, phi, prm, box)) / (2 * eps)
+        Dp_ = _dense_after_link_change(D0, Up, prm, phi.shape, (t, z, y, x), mu)
+        Dm_ = _dense_after_link_change(D0, Um, prm, phi.shape, (t, z, y, x), mu)
+        fd = (boundary_action_dense(Up, phi, prm, box, Dp_) - boundary_action_dense(Um, phi, prm, box, Dm_)) / (2 * eps)
         got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
         assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
 
@@ -184,6 +206,9 @@ def test_ratio_action_force_matches_finite_differences(light, pv):
     phi = inputs.gaussian_source(SLAB, 4, rng=rng)
     box = O.band_box(SLAB, 2, dirs=(0,))
     F = ratio_action_force_dense(U, phi, light, pv, box)
+    from oracle import dense as Dn
+    Dl0 = Dn.dense_matrix(lambda f: O.apply_D(U, f, light), phi.shape)
+    Dp0 = Dn.dense_matrix(lambda f: O.apply_D(U, f, pv), phi.shape)
     eps = 1e-5
     # a y-link inside Omega, an x-link across the face at x = 0 | 1, a y-link in Omega-bar
     for (t, z, y, x, mu) in [(0, 1, 1, 2, 1), (1, 0, 1, 0, 0), (1, 1, 1, 3, 1)]:
@@ -191,6 +216,11 @@ def test_ratio_action_force_matches_finite_differences(light, pv):
         Up, Um = U.copy(), U.copy()
         Up[t, z, y, x, mu] = _expm_i(H, eps) @ U[t, z, y, x, mu]
         Um[t, z, y, x, mu] = _expm_i(H, -eps) @ U[t, z, y, x, mu]
-        fd = (ratio_action_dense(Up, phi, light, pv, box) - ratio_action_dense(Um, phi, light, pv, box)) / (2 * eps)
+        site = (t, z, y, x)
+        sp = ratio_action_dense(Up, phi, light, pv, box, _dense_after_link_change(Dl0, Up, light, phi.shape, site, mu),
+                                _dense_after_link_change(Dp0, Up, pv, phi.shape, site, mu))
+        sm = ratio_action_dense(Um, phi, light, pv, box, _dense_after_link_change(Dl0, Um, light, phi.shape, site, mu),
+                                _dense_after_link_change(Dp0, Um, pv, phi.shape, site, mu))
+        fd = (sp - sm) / (2 * eps)
         got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
         assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
