@@ -244,6 +244,222 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_force(const For
 }
 
 
+
+// ---------------------------------------------------------------------------
+// FP32, N5 <= 16: sixteen threads per site (one lane each, lanes past N5
+// idle), two sites per warp.  A site's own X and Z rows are loaded once into
+// registers and serve all four directions; each row load of a warp is two
+// contiguous runs of N5 complex.  Per direction the 18 reals of M are summed
+// over the 16 lanes by a reduce-scatter (each halving step keeps half the
+// values and exchanges the other half: 9 + 5 + 3 + 2 shuffles), the lanes
+// park their sums in shared memory, and nine threads form U M and its
+// traceless anti-Hermitian part.
+constexpr int FW_THREADS = 256;
+
+// one halving step of the reduce-scatter: n values (n even) -> n / 2
+template <int N>
+__device__ __forceinline__ void rs_step(float (&v)[N], int (&idx)[N], int bit) {
+    constexpr int H = N / 2;
+    const bool hi = (threadIdx.x & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float mine = hi ? v[H + i] : v[i];
+        const float other = hi ? v[i] : v[H + i];
+        v[i] = mine + __shfl_xor_sync(0xffffffffu, other, bit);
+        idx[i] = hi ? idx[H + i] : idx[i];
+    }
+}
+
+template <int SRC, int DST>
+__device__ __forceinline__ void rs_pad(const float (&a)[SRC], const int (&ia)[SRC], float (&b)[DST], int (&ib)[DST]) {
+#pragma unroll
+    for (int i = 0; i < DST; ++i) {
+        b[i] = i < SRC ? a[i < SRC ? i : 0] : 0.f;
+        ib[i] = i < SRC ? ia[i < SRC ? i : 0] : -1;
+    }
+}
+
+// the upper half spinor of (1 + SG g_mu) v of one lane, all three colours
+template <int MU, int SG>
+__device__ __forceinline__ void half_reg(const float2 (&v)[12], Cx<float> (&o)[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Cx<float> w[4], pr[2];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) w[sp] = Cx<float>{v[sp * 3 + c].x, v[sp * 3 + c].y};
+        proj<MU, SG, float>(w, pr);
+        o[0][c] = pr[0];
+        o[1][c] = pr[1];
+    }
+}
+
+template <int MU>
+__device__ __forceinline__ void dir_lane(const ForceArgs& a, int p, int64_t i, int l, bool on, bool store,
+                                         const float2 (&xo)[12], const float2 (&zo)[12], float* sM, float* sF,
+                                         int g16) {
+    const int N5 = a.N5;
+    const int n = a.nbr[p][i * 8 + MU];
+    float m[18];
+#pragma unroll
+    for (int e = 0; e < 18; ++e) m[e] = 0.f;
+    if (on && n >= 0) {
+        const float2* Xn = reinterpret_cast<const float2*>(a.X[1 - p]) + (int64_t)n * 12 * N5 + l;
+        const float2* Zn = reinterpret_cast<const float2*>(a.Z[1 - p]) + (int64_t)n * 12 * N5 + l;
+        float2 xn[12], zn[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            xn[c] = __ldg(Xn + c * N5);
+            zn[c] = __ldg(Zn + c * N5);
+        }
+        Cx<float> g[2][3], h[2][3];
+        half_reg<MU, -1>(zn, g);   // g = (1 - g_mu) Z(x + mu)
+        half_reg<MU, -1>(xo, h);   // h = (1 - g_mu) X(x)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    m[(r * 3 + c) * 2] += g[k][r].re * h[k][c].re + g[k][r].im * h[k][c].im;
+                    m[(r * 3 + c) * 2 + 1] += g[k][r].im * h[k][c].re - g[k][r].re * h[k][c].im;
+                }
+        half_reg<MU, 1>(zo, g);    // g' = (1 + g_mu) Z(x)
+        half_reg<MU, 1>(xn, h);    // h' = (1 + g_mu) X(x + mu)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    m[(r * 3 + c) * 2] += h[k][r].re * g[k][c].re + h[k][r].im * g[k][c].im;
+                    m[(r * 3 + c) * 2 + 1] += h[k][r].im * g[k][c].re - h[k][r].re * g[k][c].im;
+                }
+    }
+    // reduce-scatter over the 16 lanes of the site: 18 -> 9 -> 5 -> 3 -> 2
+    int id18[18];
+#pragma unroll
+    for (int e = 0; e < 18; ++e) id18[e] = e;
+    rs_step<18>(m, id18, 8);
+    float v10[10];
+    int i10[10];
+    {
+        float t9[9];
+        int j9[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) { t9[e] = m[e]; j9[e] = id18[e]; }
+        rs_pad<9, 10>(t9, j9, v10, i10);
+    }
+    rs_step<10>(v10, i10, 4);
+    float v6[6];
+    int i6[6];
+    {
+        float t5[5];
+        int j5[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) { t5[e] = v10[e]; j5[e] = i10[e]; }
+        rs_pad<5, 6>(t5, j5, v6, i6);
+    }
+    rs_step<6>(v6, i6, 2);
+    float v4[4];
+    int i4[4];
+    {
+        float t3[3];
+        int j3[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) { t3[e] = v6[e]; j3[e] = i6[e]; }
+        rs_pad<3, 4>(t3, j3, v4, i4);
+    }
+    rs_step<4>(v4, i4, 1);
+    // park the two sums of this lane, then nine lanes form F = U M and TA(F)
+    float* Mg = sM + g16 * 18;
+    float* Fg = sF + g16 * 18;
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+        if (i4[e] >= 0) Mg[i4[e]] = v4[e];
+    __syncwarp();
+    const int lq = threadIdx.x & 15;
+    if (lq < 9) {
+        const int r = lq / 3, c = lq % 3;
+        const float* U = reinterpret_cast<const float*>(a.links[p]) + (i * 8 + MU) * 18;
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float ur = U[(r * 3 + k) * 2], ui = U[(r * 3 + k) * 2 + 1];
+            const float mr = Mg[(k * 3 + c) * 2], mi = Mg[(k * 3 + c) * 2 + 1];
+            re += ur * mr - ui * mi;
+            im += ur * mi + ui * mr;
+        }
+        Fg[lq * 2] = re;
+        Fg[lq * 2 + 1] = im;
+    }
+    __syncwarp();
+    if (lq < 9 && store) {   // a cut link (n < 0) has M = 0 and gets F = 0
+        const int r = lq / 3, c = lq % 3;
+        const int64_t gl = a.gidx[p][i * 8 + MU];
+        if (gl >= 0) {
+            bool act = true;
+            if (a.use_box) {
+                const int64_t lex = gl >> 2;
+                int x[4] = {(int)(lex % a.L[0]), (int)((lex / a.L[0]) % a.L[1]),
+                            (int)((lex / ((int64_t)a.L[0] * a.L[1])) % a.L[2]),
+                            (int)(lex / ((int64_t)a.L[0] * a.L[1] * a.L[2]))};
+                act = in_box(a, x);
+                x[MU] = (x[MU] + 1) % a.L[MU];
+                act = act && in_box(a, x);
+            }
+            const float tr = (Fg[1] + Fg[(1 * 3 + 1) * 2 + 1] + Fg[(2 * 3 + 2) * 2 + 1]) * (1.f / 3.f);
+            float re = -0.25f * (Fg[(r * 3 + c) * 2] - Fg[(c * 3 + r) * 2]);
+            float im = -0.25f * (Fg[(r * 3 + c) * 2 + 1] + Fg[(c * 3 + r) * 2 + 1]);
+            if (r == c) im += 0.5f * tr;
+            if (!act) re = im = 0.f;
+            double* o = a.out + gl * 18 + (r * 3 + c) * 2;
+            if (a.accumulate) {
+                o[0] += re;
+                o[1] += im;
+            } else {
+                o[0] = re;
+                o[1] = im;
+            }
+        }
+    }
+    __syncwarp();   // Mg, Fg are reused by the next direction
+}
+
+__global__ void __launch_bounds__(FW_THREADS, 2) k_force_w16(const ForceArgs a) {
+    __shared__ float sM[FW_THREADS / 16 * 18];
+    __shared__ float sF[FW_THREADS / 16 * 18];
+    const int g16 = threadIdx.x >> 4;          // site group in the block
+    const int l = threadIdx.x & 15;            // lane of the site
+    const bool on = l < a.N5;
+    const int64_t ngroups = (int64_t)gridDim.x * (FW_THREADS / 16);
+    // the two groups of a warp run the same number of iterations (shuffles)
+    const int64_t span = (a.ns + ngroups - 1) / ngroups * ngroups;
+    for (int64_t site0 = blockIdx.x * (int64_t)(FW_THREADS / 16) + g16; site0 < span; site0 += ngroups) {
+        const int64_t site = site0 < a.ns ? site0 : a.ns - 1;
+        const int p = site >= a.ns0 ? 1 : 0;
+        const int64_t i = site - (p ? a.ns0 : 0);
+        float2 xo[12], zo[12];
+        if (on) {
+            const float2* Xs = reinterpret_cast<const float2*>(a.X[p]) + i * 12 * a.N5 + l;
+            const float2* Zs = reinterpret_cast<const float2*>(a.Z[p]) + i * 12 * a.N5 + l;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                xo[c] = __ldg(Xs + c * a.N5);
+                zo[c] = __ldg(Zs + c * a.N5);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) xo[c] = zo[c] = make_float2(0.f, 0.f);
+        }
+        // a clamped site past the end only joins the shuffles and stores nothing
+        const bool store = site0 < a.ns;
+        dir_lane<0>(a, p, i, l, on, store, xo, zo, sM, sF, g16);
+        dir_lane<1>(a, p, i, l, on, store, xo, zo, sM, sF, g16);
+        dir_lane<2>(a, p, i, l, on, store, xo, zo, sM, sF, g16);
+        dir_lane<3>(a, p, i, l, on, store, xo, zo, sM, sF, g16);
+    }
+}
+
 }  // namespace
 
 dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
@@ -301,10 +517,15 @@ dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void*
     const int64_t nthreads = a.ns * 4;
     const int64_t want = (nthreads + 255) / 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
-    if (prec == DWF_FP64)
+    if (prec == DWF_FP64) {
         k_force<double, double, double><<<grid, 256, 0, s>>>(a);
-    else
+    } else if (a.N5 <= 16) {
+        const int64_t wgroups = (a.ns + FW_THREADS / 16 - 1) / (FW_THREADS / 16);
+        const int wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgroups, 152 * 8));
+        k_force_w16<<<wgrid, FW_THREADS, 0, s>>>(a);
+    } else {
         k_force<float, float, float><<<grid, 256, 0, s>>>(a);
+    }
     note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;

@@ -133,3 +133,23 @@ def test_bad_arguments():
     hb.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     with pytest.raises(G.DWFError):
         hb.force(out, X, X)
+
+
+def test_fp32_ls12_active_box_and_accumulate():
+    """The FP32 path at N5 = 12 (one lane per thread, sixteen threads per
+    site): against the oracle with an active box, then accumulating the
+    adjoint bilinear's force."""
+    dims, Ls = (4, 4, 4, 8), 12
+    rng, U, Xs, Ys, h = _setup(dims, Ls, MOBIUS, 1, "exp", seed=24)
+    box = ((3, 0, 1, 2), (3, 4, 2, 5))
+    act = box_links(dims, box)
+    want = force_bilinear(U, Xs, Ys, MOBIUS, active=act)
+    X, Y = _dev(Xs, dims, G.FP32), _dev(Ys, dims, G.FP32)
+    out = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
+    h.force(out, X, Y, prec=G.FP32, active=box)
+    got = _force_host(out.view(-1, 2), U)
+    assert LY.rel_l2(got, want) <= 2e-5
+    assert np.abs(got[~act]).max() == 0.0
+    h.force(out, Y, X, prec=G.FP32, active=box, accumulate=True)
+    got = _force_host(out.view(-1, 2), U)
+    assert LY.rel_l2(got, want + force_bilinear(U, Ys, Xs, MOBIUS, active=act)) <= 2e-5
