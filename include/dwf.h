@@ -398,6 +398,18 @@ dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const
                                     const double* phi, int nrhs, const dwf_box* active, int accumulate,
                                     const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
 
+/* Zolotarev's optimal relative rational approximation of 1/sqrt(x) on
+ * [lo, hi], type (n - 1, n), in partial fractions (host only, no GPU):
+ *   1/sqrt(x) ~ sum_{j<n} residues[j] / (x + shifts[j]),
+ * with relative error |1 - sqrt(x) r(x)| <= *delta, equioscillating.  The
+ * (D^+ D)^(-1/2) factor of the one-flavour DD-RHMC term of Sec. 2.3.1 is
+ * dwf_rational_apply with these coefficients (lo, hi bracketing the spectrum
+ * of M_pc^+ M_pc).  On y = x/lo, c_l = sn^2/cn^2(l K'/(2n) | 1 - lo/hi),
+ * poles the odd c_l, zeros the even ones, the scale centring the error.
+ * shifts, residues: caller arrays of n doubles; delta may be NULL.
+ * DWF_ERR_ARG unless 1 <= n <= 64 and 0 < lo < hi. */
+dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta);
+
 /* Rational function of the normal Schur operator in partial fractions,
  *   out = a0 in + sum_i residues[i] (M_pc^+ M_pc + shifts[i])^-1 in,
  * the form the DD-RHMC action of Sec. 2.3.1 takes for the powers of the

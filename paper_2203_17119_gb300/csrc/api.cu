@@ -314,6 +314,10 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
     return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
 
+dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta) {
+    return zolotarev_inv_sqrt(n, lo, hi, shifts, residues, delta);
+}
+
 dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
                               const double* residues, int n, int nrhs, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream) {

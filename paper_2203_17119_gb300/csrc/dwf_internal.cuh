@@ -202,6 +202,7 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
                          const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
 dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                           const dwf_box* active, int accumulate, cudaStream_t s);
+dwf_status zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta);
 dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
                           const double* residues, int n, int nrhs, const dwf_solver_params* sp,
                           dwf_solver_stats* stats, cudaStream_t s);

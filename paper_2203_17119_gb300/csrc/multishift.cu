@@ -398,4 +398,72 @@ dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a
     return st;
 }
 
+// ------------------------------------------------------------------------
+// Zolotarev's optimal relative approximation of 1/sqrt(x) on [lo, hi] in
+// partial fractions (host only).  On y = x / lo in [1, b] with m' = 1 - 1/b,
+// K' = K(m'), c_l = sn^2 / cn^2 (l K' / (2n) | m') for l = 1 .. 2n-1,
+//     r(y) = d0 prod_{i<n} (y + c_{2i}) / prod_{j<=n} (y + c_{2j-1}),
+// d0 centring the relative error so that it equioscillates (found on a dense
+// geometric grid).  Jacobi sn, cn and K by the arithmetic-geometric-mean
+// (descending Landen) sequence, with the complementary parameter passed
+// exactly (m1 = 1/b) so nothing cancels as m' -> 1.
+static void jacobi_agm(double u, double m, double m1, double* sn, double* cn, double* K) {
+    double a[64], c[64];
+    a[0] = 1.0;
+    c[0] = std::sqrt(m);
+    double b = std::sqrt(m1);
+    int N = 0;
+    while (std::fabs(c[N]) > 1e-17 * a[N] && N < 60) {
+        const double an = 0.5 * (a[N] + b), bn = std::sqrt(a[N] * b);
+        c[N + 1] = 0.5 * (a[N] - b);
+        a[N + 1] = an;
+        b = bn;
+        ++N;
+    }
+    double phi = std::ldexp(1.0, N) * a[N] * u;
+    for (int k = N; k >= 1; --k) phi = 0.5 * (phi + std::asin(c[k] / a[k] * std::sin(phi)));
+    if (sn) *sn = std::sin(phi);
+    if (cn) *cn = std::cos(phi);
+    if (K) *K = 3.14159265358979323846 / (2.0 * a[N]);
+}
+
+dwf_status zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta) {
+    if (n < 1 || n > 64 || !(lo > 0.0) || !(hi > lo) || shifts == nullptr || residues == nullptr) {
+        set_error("zolotarev: need 1 <= n <= 64, 0 < lo < hi and output arrays");
+        return DWF_ERR_ARG;
+    }
+    const double b = hi / lo, m1 = 1.0 / b, m = 1.0 - m1;
+    double Kp = 0.0;
+    jacobi_agm(0.0, m, m1, nullptr, nullptr, &Kp);
+    std::vector<double> c(2 * n);   // c[l], l = 1 .. 2n - 1
+    for (int l = 1; l < 2 * n; ++l) {
+        double sn = 0.0, cn = 1.0;
+        jacobi_agm(l * Kp / (2.0 * n), m, m1, &sn, &cn, nullptr);
+        c[l] = sn * sn / (cn * cn);
+    }
+    // d0: centre sqrt(y) r(y) between its extremes on [1, b]
+    const int G = 200001;
+    double emax = -1e300, emin = 1e300;
+    for (int g = 0; g < G; ++g) {
+        const double y = std::exp(std::log(b) * g / (G - 1));
+        double v = std::sqrt(y);
+        for (int i = 1; i < n; ++i) v *= y + c[2 * i];
+        for (int j = 1; j <= n; ++j) v /= y + c[2 * j - 1];
+        emax = std::max(emax, v);
+        emin = std::min(emin, v);
+    }
+    const double d0 = 2.0 / (emax + emin);
+    if (delta) *delta = (emax - emin) / (emax + emin);
+    for (int j = 1; j <= n; ++j) {
+        const double p = c[2 * j - 1];
+        double R = 1.0;
+        for (int i = 1; i < n; ++i) R *= c[2 * i] - p;
+        for (int k = 1; k <= n; ++k)
+            if (k != j) R /= c[2 * k - 1] - p;
+        shifts[j - 1] = lo * p;
+        residues[j - 1] = d0 * std::sqrt(lo) * R;
+    }
+    return DWF_OK;
+}
+
 }  // namespace dwf

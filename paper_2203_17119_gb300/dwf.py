@@ -99,6 +99,8 @@ def lib():
                                      C.POINTER(SolverStats), vp],
             "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
             "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
+            "dwf_zolotarev_inv_sqrt": [i, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)],
             "dwf_rational_apply": [vp, vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), i, i,
                                    C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
             "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
@@ -160,6 +162,15 @@ class Action:
     mf: float = 0.01
     b5: float = 1.0
     c5: float = 0.0
+
+
+def zolotarev_inv_sqrt(n, lo, hi):
+    """Zolotarev's 1/sqrt(x) on [lo, hi] in partial fractions: (shifts, residues, delta)."""
+    sh = (C.c_double * n)()
+    rs = (C.c_double * n)()
+    dl = C.c_double()
+    _check(lib().dwf_zolotarev_inv_sqrt(int(n), float(lo), float(hi), sh, rs, C.byref(dl)))
+    return list(sh), list(rs), dl.value
 
 
 class Handle:

@@ -119,3 +119,35 @@ def test_rational_apply_matches_oracle(boxes, nrhs, inner):
         for r in range(nrhs):
             want = rational_apply(_A(U, mask), bs[bi][r], a0, shifts, res, tol=1e-12)
             assert LY.rel_l2(got[bi][r], want) <= 1e-9, (bi, r)
+
+
+def test_zolotarev_inverse_square_root():
+    """(M_pc^+ M_pc)^(-1/2) b by dwf_rational_apply with the library's
+    Zolotarev coefficients, against the dense eigendecomposition, to within
+    the approximation's delta."""
+    from oracle import dense as Dn
+    dims, Ls = (2, 2, 2, 4), 4
+    rng = np.random.default_rng(57)
+    U = inputs.gauge_field(dims, "haar", rng=rng)
+    odd = O.parity_field(dims) == 1
+    shape = (dims[3], dims[2], dims[1], dims[0], Ls, 4, 3)
+
+    def A(f):
+        f = O.restrict(f, odd)
+        return O.mpc(U, O.mpc(U, f, MOBIUS), MOBIUS, True)
+
+    dofs = Dn.site_mask_to_dofs(odd, Ls * 12)
+    Ad = Dn.dense_matrix(A, shape)[np.ix_(dofs, dofs)]
+    w, V = np.linalg.eigh(Ad)
+    shifts, res, delta = G.zolotarev_inv_sqrt(16, 0.9 * w[0], 1.1 * w[-1])
+    assert delta < 1e-6
+    b = O.restrict(inputs.gaussian_source(dims, Ls, rng=rng), odd)
+    h = G.Handle(dims, Ls, G.Action(MOBIUS.M5, MOBIUS.mf, MOBIUS.b5, MOBIUS.c5))
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    bcb = torch.view_as_real(torch.from_numpy(LY.to_cb([[b]], dims, None, 1))).cuda().contiguous()
+    out = torch.zeros_like(bcb)
+    stats, rc = h.rational_apply(out, bcb, 0.0, shifts, res, tol=1e-12)
+    assert rc == 0
+    got = LY.from_cb(torch.view_as_complex(out.cpu()).numpy(), dims, None, 1, Ls)[0][0]
+    want = V @ ((w ** -0.5) * (V.conj().T @ b.reshape(-1)[dofs]))
+    assert np.linalg.norm(got.reshape(-1)[dofs] - want) <= (2 * delta + 1e-9) * np.linalg.norm(want)
