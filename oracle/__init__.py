@@ -17,7 +17,11 @@ Modules:
 * ``oracle.multishift`` -- multi-shift CG for the rational functions of the
   normal operators (Sec. 2.3.1).
 * ``oracle.force``    -- the link derivative of Re <X, D Y>, the insertion
-  of delta D that the DD-HMC forces of Sec. 2.3 are built from.
+  of delta D that the DD-HMC forces of Sec. 2.3 are built from, and the
+  dense boundary-action and Hasenbusch-ratio forces.
+* ``oracle.chebyshev`` -- the Chebyshev filter T_n(z(A)) v of Sec. 4.
+* ``oracle.rational`` -- Zolotarev's optimal rational approximation of
+  1/sqrt(x) in partial fractions.
 * ``oracle.nn``       -- the parallel-transport convolutional preconditioner
   (forward, analytic backward, Adam).
 
