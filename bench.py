@@ -669,6 +669,49 @@ def run_chebyshev(args):
                       "rayleigh_before": float(np.mean(rq0)), "rayleigh_after": float(np.mean(rq1))}))
 
 
+def run_large(args):
+    """The paper's per-GPU volume (--large): Moebius 32^4 x Ls=16, m_f = 0.005,
+    exp(i 0.3 H) links; mixed FP32/FP64 CGNE to 1e-10 of D and of D_Omega for
+    Dirichlet bands of width 1, 2 and 4 (the interior boxes), one solve each
+    (graph capture included), default kernel configuration.  One JSON line per
+    solve, flushed as it completes."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    dims, Ls, mf = (32, 32, 32, 32), 16, 0.005
+    rng = np.random.default_rng(SEED + 3)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
+    src = inputs.gaussian_source(dims, Ls, rng=rng)
+    Ut = torch.from_numpy(U.reshape(-1)).cuda()
+    del U
+    act = G.Action(M5, mf, B5, C5)
+    for name, w in (("D", 0), ("D_Omega_w1", 1), ("D_Omega_w2", 2), ("D_Omega_w4", 4)):
+        box = ((w // 2,) * 4, (32 - w,) * 4) if w else None
+        h = G.Handle(dims, Ls, act, boxes=[box] if box else None)
+        h.set_gauge(Ut)
+        if box:
+            o, e = box
+            canon = np.ascontiguousarray(src[o[3]:o[3] + e[3], o[2]:o[2] + e[2], o[1]:o[1] + e[1],
+                                             o[0]:o[0] + e[0]])
+        else:
+            canon = src
+        b = h.pack(torch.from_numpy(canon.reshape(-1)).cuda())
+        del canon
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.time()
+        st, rc = h.cgne_solve(x, b, tol=1e-10, inner=G.FP32, allow_fail=True)
+        torch.cuda.synchronize()
+        sec = time.time() - t
+        print(json.dumps({"workload": "Moebius DWF 32^4 x Ls=16, m_f=0.005, exp(i 0.3 H) links, mixed "
+                          "FP32/FP64 CGNE to 1e-10", "operator": name, "box": box, "ms": sec * 1e3,
+                          "iters": st[0]["iters"], "reliable_updates": st[0]["reliable_updates"],
+                          "true_resid": st[0]["true_resid"], "status": rc}), flush=True)
+        del h, b, x
+        torch.cuda.empty_cache()
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -739,6 +782,8 @@ def main():
                     help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--multishift", nargs="+", metavar="ARG",
                     help="NSHIFT [f64|f32]: multi-shift CG against single-shift solves")
+    ap.add_argument("--large", action="store_true",
+                    help="32^4 x 16 m_f = 0.005 solves of D and of D_Omega, bands 1, 2, 4")
     ap.add_argument("--chebyshev", nargs="*", metavar="ARG",
                     help="Chebyshev filter of the local normal operator: [ORDER] [f32|f64]")
     ap.add_argument("--boundary", nargs="*", metavar="ARG",
@@ -776,6 +821,9 @@ def main():
         return
     if args.chebyshev is not None:
         run_chebyshev(args)
+        return
+    if args.large:
+        run_large(args)
         return
     if args.hop:
         run_hop(args)
