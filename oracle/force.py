@@ -225,3 +225,98 @@ def ratio_action_force_dense(U, phi, p_light, p_pv, box, active=None) -> np.ndar
             - 2.0 * force_bilinear(U, zeta_b, pc["u_l"], p_light, active)
             + 2.0 * force_bilinear(U, pc["eta"], pc["d"] - pc["b"], p_pv, active)
             + 2.0 * force_bilinear(U, pc["kappa"], pc["b"] - pc["u_pv"], p_pv, active))
+
+
+# ------------------------------------------------------------------
+# One-flavour DD-RHMC boundary term (Sec. 2.3.1): det chi = det D / det D_dir,
+# D_dir = D with the links between Omega and Omega-bar cut (eq. ddrhmc).  With
+# A = M_pc^+ M_pc of D and A_d that of D_dir on the odd checkerboard and two
+# rational functions r1 ~ x^(1/4), r2 ~ x^(-1/2) in partial fractions
+# (a0, shifts, residues),
+#
+#   S = <w, r2(A) w>,  w = r1(A_d) phi.
+#
+# With z_j = (A_d + s'_j)^-1 phi, x_i = (A + s_i)^-1 w, v = r2(A) w and
+# y_j = (A_d + s'_j)^-1 v, the force is
+#
+#   F = -sum_i rho_i 2 F_M(M x_i, x_i) - 2 sum_j rho'_j [F_Md(M_d z_j, y_j) + F_Md(M_d y_j, z_j)],
+#
+# F_M(X, Y) the link derivative of Re <X, M_pc Y>: M_pc = D_oo - D_oe D_ee^-1 D_eo
+# and D_ee, D_oo do not depend on the links, so
+# F_M(X, Y) = -F(X_o, (D_ee^-1 D_eo Y)_e) - F((D_ee^-+ D_oe^+ X)_e, Y_o).
+# The formula holds for any rational functions; dense linear algebra.
+def _rational_dense(Amat, v, r):
+    a0, shifts, residues = r
+    n = Amat.shape[0]
+    out = a0 * v
+    sols = []
+    for s, rho in zip(shifts, residues):
+        x = np.linalg.solve(Amat + s * np.eye(n), v)
+        sols.append(x)
+        out = out + rho * x
+    return out, sols
+
+
+class _SchurDense:
+    """Dense D of a gauge field, its odd/even blocks and M_pc on odd dofs."""
+
+    def __init__(self, U, p, shape, D=None):
+        from oracle import dense as Dn
+        dims = O.lattice_dims(U)
+        self.U, self.p, self.shape = U, p, shape
+        self.D = _dense_D(U, shape, p) if D is None else D
+        par = O.parity_field(dims)
+        per = shape[4] * 12
+        self.od = Dn.site_mask_to_dofs(par == 1, per)
+        self.ev = Dn.site_mask_to_dofs(par == 0, per)
+        D = self.D
+        self.Dee = D[np.ix_(self.ev, self.ev)]
+        self.Deo = D[np.ix_(self.ev, self.od)]
+        self.Doe = D[np.ix_(self.od, self.ev)]
+        self.M = D[np.ix_(self.od, self.od)] - self.Doe @ np.linalg.solve(self.Dee, self.Deo)
+        self.A = np.conj(self.M.T) @ self.M
+
+    def full(self, v_o=None, v_e=None):
+        f = np.zeros(self.D.shape[0], dtype=np.complex128)
+        if v_o is not None:
+            f[self.od] = v_o
+        if v_e is not None:
+            f[self.ev] = v_e
+        return f.reshape(self.shape)
+
+    def force_M(self, X_o, Y_o):
+        """Link derivative of Re <X_o, M_pc Y_o>."""
+        W_e = np.linalg.solve(self.Dee, self.Deo @ Y_o)
+        V_e = np.linalg.solve(np.conj(self.Dee.T), np.conj(self.Doe.T) @ X_o)
+        return (-force_bilinear(self.U, self.full(v_o=X_o), self.full(v_e=W_e), self.p)
+                - force_bilinear(self.U, self.full(v_e=V_e), self.full(v_o=Y_o), self.p))
+
+
+def _one_flavour_pieces(U, phi, p, box, r1, r2, D=None, Dd=None):
+    shape = phi.shape
+    L = _SchurDense(U, p, shape, D)
+    Ld = _SchurDense(O.cut_gauge(U, [box]), p, shape, Dd)
+    ph = phi.reshape(-1)[L.od]
+    w, zs = _rational_dense(Ld.A, ph, r1)
+    v, xs = _rational_dense(L.A, w, r2)
+    return L, Ld, w, v, zs, xs
+
+
+def one_flavour_action_dense(U, phi, p, box, r1, r2, D=None, Dd=None) -> float:
+    """S = <w, r2(A) w>, w = r1(A_d) phi (the odd sites of the full field phi);
+    D, Dd: the dense D of U and of the cut field, if already built."""
+    _, _, w, v, _, _ = _one_flavour_pieces(U, phi, p, box, r1, r2, D, Dd)
+    return float(np.vdot(w, v).real)
+
+
+def one_flavour_force_dense(U, phi, p, box, r1, r2) -> np.ndarray:
+    """Link force of the one-flavour DD-RHMC term S (d/d eps S(exp(i eps H) U) = Re tr[i H F])."""
+    L, Ld, w, v, zs, xs = _one_flavour_pieces(U, phi, p, box, r1, r2)
+    F = np.zeros(U.shape, dtype=np.complex128)
+    for rho, x in zip(r2[2], xs):
+        F -= 2.0 * rho * L.force_M(L.M @ x, x)
+    n = Ld.A.shape[0]
+    for s, rho, z in zip(r1[1], r1[2], zs):
+        y = np.linalg.solve(Ld.A + s * np.eye(n), v)
+        F -= 2.0 * rho * (Ld.force_M(Ld.M @ z, y) + Ld.force_M(Ld.M @ y, z))
+    return F

@@ -224,3 +224,40 @@ def test_ratio_action_force_matches_finite_differences(light, pv):
         fd = (sp - sm) / (2 * eps)
         got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
         assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
+
+
+from oracle.force import one_flavour_action_dense, one_flavour_force_dense  # noqa: E402
+
+
+@pytest.mark.parametrize("prm", [SHAMIR, MOBIUS], ids=["shamir", "mobius"])
+def test_one_flavour_force_matches_finite_differences(prm):
+    """Central differences of S = <w, r2(A) w>, w = r1(A_d) phi (A, A_d the
+    normal Schur operators of D and of D with the Omega / Omega-bar links cut)
+    against the force assembled from Schur-operator insertions, at a link
+    inside Omega, a cut link and a link in Omega-bar.  The rational functions
+    are arbitrary partial fractions: the formula holds for any."""
+    rng = np.random.default_rng(35)
+    U = inputs.gauge_field(SLAB, "haar", rng=rng)
+    odd = O.parity_field(SLAB) == 1
+    phi = O.restrict(inputs.gaussian_source(SLAB, 4, rng=rng), odd)
+    box = O.band_box(SLAB, 2, dirs=(0,))
+    r1 = (0.4, [0.3, 2.0], [0.25, 1.5])
+    r2 = (0.1, [0.05, 0.7, 4.0], [0.2, 0.6, 2.5])
+    F = one_flavour_force_dense(U, phi, prm, box, r1, r2)
+    from oracle import dense as Dn
+    D0 = Dn.dense_matrix(lambda f: O.apply_D(U, f, prm), phi.shape)
+    Dd0 = Dn.dense_matrix(lambda f: O.apply_D(O.cut_gauge(U, [box]), f, prm), phi.shape)
+    eps = 1e-5
+    # (t, z, y, x, mu): y-link inside Omega, the cut x-link from x = 0 to 1, y-link in Omega-bar
+    for (t, z, y, x, mu) in [(0, 1, 1, 2, 1), (1, 0, 1, 0, 0), (1, 1, 1, 3, 1)]:
+        H = _hermitian_traceless(rng)
+        vals = []
+        for sgn in (1, -1):
+            U2 = U.copy()
+            U2[t, z, y, x, mu] = _expm_i(H, sgn * eps) @ U[t, z, y, x, mu]
+            D2 = _dense_after_link_change(D0, U2, prm, phi.shape, (t, z, y, x), mu)
+            Dd2 = _dense_after_link_change(Dd0, O.cut_gauge(U2, [box]), prm, phi.shape, (t, z, y, x), mu)
+            vals.append(one_flavour_action_dense(U2, phi, prm, box, r1, r2, D2, Dd2))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        got = float(np.real(np.trace(1j * H @ F[t, z, y, x, mu])))
+        assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (t, z, y, x, mu, got, fd)
