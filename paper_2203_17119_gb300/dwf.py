@@ -60,6 +60,61 @@ class SolverStats(C.Structure):
 _lib = None
 
 
+def signatures():
+    """argtypes of every entry point of include/dwf.h (restype: dwf_status)."""
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    return {
+        "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
+        "dwf_destroy": [vp],
+        "dwf_domain_sites": [vp, i, C.POINTER(C.c_int64)],
+        "dwf_box_sites": [vp, i, i, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "dwf_set_gauge": [vp, vp, vp],
+        "dwf_pack": [vp, vp, vp, i, i, vp],
+        "dwf_unpack": [vp, vp, vp, i, i, vp],
+        "dwf_dslash_eo": [vp, vp, vp, i, i, i, i, vp],
+        "dwf_mooee": [vp, vp, vp, i, i, i, i, vp],
+        "dwf_mooee_inv": [vp, vp, vp, i, i, i, i, vp],
+        "dwf_mpc": [vp, vp, vp, i, i, i, vp],
+        "dwf_apply_d": [vp, vp, vp, i, i, i, vp],
+        "dwf_dirichlet_block": [vp, vp, vp, i, i, i, vp],
+        "dwf_cgne_solve": [vp, vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_check_device": [vp],
+        "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
+        "dwf_launch_count": [C.POINTER(C.c_uint64)],
+        "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
+        "dwf_set_tile": [vp, i, i, i],
+        "dwf_set_hop_kernel": [vp, i, i],
+        "dwf_set_hop_chunk": [vp, i, i],
+        "dwf_get_tuning": [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                           C.POINTER(C.c_int)],
+        "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
+        "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
+                                 C.POINTER(SolverStats), vp],
+        "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
+        "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
+        "dwf_zolotarev_inv_sqrt": [i, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)],
+        "dwf_rational_apply": [vp, vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), i, i,
+                               C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
+        "dwf_boundary_r": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_boundary_ratio_force": [vp, vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i,
+                                     C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
+                               C.POINTER(SolverStats), vp],
+        "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
+                              C.POINTER(SolverStats), vp],
+        "dwf_nn_create": [C.POINTER(vp), i],
+        "dwf_nn_destroy": [vp],
+        "dwf_nn_set_weights": [vp, vp, C.c_size_t],
+        "dwf_nn_get_weights": [vp, vp, C.c_size_t],
+        "dwf_nn_apply": [vp, vp, vp, vp, i, vp],
+        "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
+        "dwf_nn_last_grad": [vp, vp, C.c_size_t],
+    }
+
+
 def lib():
     """The loaded ``libdwf.so`` (raises if it has not been built)."""
     global _lib
@@ -68,57 +123,7 @@ def lib():
             raise DWFError(2, f"{LIB_PATH} is missing: run __graft_entry__.build() or "
                               "python -m paper_2203_17119_gb300.build")
         L = C.CDLL(LIB_PATH)
-        vp, i, d = C.c_void_p, C.c_int, C.c_double
-        sig = {
-            "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
-            "dwf_destroy": [vp],
-            "dwf_domain_sites": [vp, i, C.POINTER(C.c_int64)],
-            "dwf_box_sites": [vp, i, i, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
-            "dwf_set_gauge": [vp, vp, vp],
-            "dwf_pack": [vp, vp, vp, i, i, vp],
-            "dwf_unpack": [vp, vp, vp, i, i, vp],
-            "dwf_dslash_eo": [vp, vp, vp, i, i, i, i, vp],
-            "dwf_mooee": [vp, vp, vp, i, i, i, i, vp],
-            "dwf_mooee_inv": [vp, vp, vp, i, i, i, i, vp],
-            "dwf_mpc": [vp, vp, vp, i, i, i, vp],
-            "dwf_apply_d": [vp, vp, vp, i, i, i, vp],
-            "dwf_dirichlet_block": [vp, vp, vp, i, i, i, vp],
-            "dwf_cgne_solve": [vp, vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
-            "dwf_check_device": [vp],
-            "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
-            "dwf_launch_count": [C.POINTER(C.c_uint64)],
-            "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
-            "dwf_set_tile": [vp, i, i, i],
-            "dwf_set_hop_kernel": [vp, i, i],
-            "dwf_set_hop_chunk": [vp, i, i],
-            "dwf_get_tuning": [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                               C.POINTER(C.c_int)],
-            "dwf_mpc_noalloc": [vp, vp, vp, i, i, i, vp],
-            "dwf_gcr_solve": [vp, vp, vp, i, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
-            "dwf_multishift_solve": [vp, vp, vp, C.POINTER(C.c_double), i, i, C.POINTER(SolverParams),
-                                     C.POINTER(SolverStats), vp],
-            "dwf_boundary_project": [vp, C.POINTER(Box), vp, vp, i, vp],
-            "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
-            "dwf_zolotarev_inv_sqrt": [i, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
-                                       C.POINTER(C.c_double)],
-            "dwf_rational_apply": [vp, vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), i, i,
-                                   C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
-            "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
-            "dwf_boundary_r": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
-            "dwf_boundary_ratio_force": [vp, vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i,
-                                         C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
-            "dwf_boundary_force": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(Box), i, C.POINTER(SolverParams),
-                                   C.POINTER(SolverStats), vp],
-            "dwf_boundary_rinv": [vp, C.POINTER(Box), vp, vp, i, C.POINTER(SolverParams),
-                                  C.POINTER(SolverStats), vp],
-            "dwf_nn_create": [C.POINTER(vp), i],
-            "dwf_nn_destroy": [vp],
-            "dwf_nn_set_weights": [vp, vp, C.c_size_t],
-            "dwf_nn_get_weights": [vp, vp, C.c_size_t],
-            "dwf_nn_apply": [vp, vp, vp, vp, i, vp],
-            "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
-            "dwf_nn_last_grad": [vp, vp, C.c_size_t],
-        }
+        sig = signatures()
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args

@@ -58,3 +58,27 @@ def test_argument_errors_without_gpu(libpath):
     p = dwf.Params((ctypes.c_int * 4)(4, 4, 4, 4), 7, 1.8, 0.01, 1.0, 0.0)   # Ls odd
     assert L.dwf_create(ctypes.byref(h), ctypes.byref(p), None, 0, 1) == 1
     assert L.dwf_mpc(None, None, None, 0, 0, 1, None) == 1
+
+
+def declared_arity():
+    """dwf_* prototype -> number of parameters, parsed from include/dwf.h."""
+    text = open(os.path.join(ROOT, "include", "dwf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(dwf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_matches_every_prototype():
+    """The ctypes binding declares every entry point of the header with the
+    header's number of arguments (a mismatch would corrupt a call silently)."""
+    pytest.importorskip("torch")
+    from paper_2203_17119_gb300 import dwf as G
+    arity = declared_arity()
+    sig = G.signatures()
+    missing = sorted(set(arity) - set(sig) - {"dwf_last_error"})
+    assert not missing, missing
+    wrong = {n: (len(a), arity[n]) for n, a in sig.items() if len(a) != arity.get(n, -1)}
+    assert not wrong, wrong
