@@ -19,6 +19,8 @@ Modules:
 * ``oracle.force``    -- the link derivative of Re <X, D Y>, the insertion
   of delta D that the DD-HMC forces of Sec. 2.3 are built from, and the
   dense boundary-action and Hasenbusch-ratio forces.
+* ``oracle.boundary`` -- matrix-free P, R^-1 and the boundary-action force
+  for lattices too large for dense matrices.
 * ``oracle.chebyshev`` -- the Chebyshev filter T_n(z(A)) v of Sec. 4.
 * ``oracle.rational`` -- Zolotarev's optimal rational approximation of
   1/sqrt(x) in partial fractions.
