@@ -23,6 +23,16 @@
  * directions x, y, z), g_4 = [[0, 1], [1, 0]] (t), g_5 = diag(1, 1, -1, -1),
  * P_+ = spins {0, 1}, P_- = spins {2, 3}.  4D parity is (x + y + z + t) mod 2.
  *
+ * Entry points, by group: handles and layouts (dwf_create ... dwf_unpack);
+ * operators (dwf_dslash_eo, dwf_hop, dwf_mooee, dwf_mooee_inv, dwf_mpc,
+ * dwf_apply_d, dwf_dirichlet_block); solvers (dwf_cgne_solve,
+ * dwf_multishift_solve, dwf_rational_apply, dwf_gcr_solve with the learned
+ * preconditioner dwf_nn_*); the DD-HMC boundary operator and forces of
+ * Sec. 2.1 and 2.3 (dwf_boundary_project, dwf_boundary_r, dwf_boundary_rinv,
+ * dwf_force, dwf_boundary_force, dwf_boundary_ratio_force); rational
+ * approximation and multigrid set-up (dwf_zolotarev_inv_sqrt,
+ * dwf_chebyshev_filter); kernel tuning (dwf_autotune, dwf_set_tile, ...).
+ *
  * ------------------------------------------------------------------------
  * DOMAINS.  A handle is bound to a domain: either the whole periodic
  * lattice (nbox = 0) or a list of boxes, each box an independent Dirichlet
