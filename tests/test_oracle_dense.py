@@ -177,3 +177,81 @@ def test_eq_ddrhmc(slab):
     lhs = Dn.logdet(chi)
     rhs = Dn.logdet(D) - Dn.logdet(Dc)
     assert abs(np.exp(lhs - rhs) - 1) < 1e-9
+
+
+@pytest.fixture(scope="module")
+def wrapped_box():
+    """4 x 4 x 4 x 2, Ls = 4, Moebius; Omega one box with odd extents that
+    wraps in x and z and is one layer thick in t: origin (3, 1, 2, 1),
+    extent (3, 3, 3, 1) (27 sites; hops leave it in every direction).  Only
+    the columns of D on Omega are built (1296 of them)."""
+    dims, Ls = (4, 4, 4, 2), 4
+    rng = np.random.default_rng(2718)
+    U = inputs.gauge_field(dims, "haar", rng=rng)
+    box = ((3, 1, 2, 1), (3, 3, 3, 1))
+    shape = (dims[3], dims[2], dims[1], dims[0], Ls, 4, 3)
+    mask = O.box_mask(dims, box)
+    par = O.parity_field(dims)
+    inner = Ls * 12
+    om_e = Dn.site_mask_to_dofs(mask & (par == 0), inner)
+    om_o = Dn.site_mask_to_dofs(mask & (par == 1), inner)
+    cols = np.concatenate([om_e, om_o])
+    n = int(np.prod(shape))
+    DO = np.empty((cols.size, cols.size), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j, c in enumerate(cols):
+        e[c] = 1.0
+        DO[:, j] = O.apply_D(U, e.reshape(shape), MOBIUS).reshape(-1)[cols]
+        e[c] = 0.0
+    ne = om_e.size
+    blocks = {"ee": DO[:ne, :ne], "eo": DO[:ne, ne:], "oe": DO[ne:, :ne], "oo": DO[ne:, ne:]}
+    return dims, Ls, U, shape, mask, om_e, om_o, blocks, rng
+
+
+def _check_on_random_vectors(apply, shape, src, dst, want, rng, tol):
+    """apply(v) = want @ v on the dofs ``dst`` and 0 on every other dof, for
+    three random complex v supported on the dofs ``src`` (a linear identity
+    checked on random vectors: a wrong block fails it with probability 1)."""
+    n = int(np.prod(shape))
+    off = np.ones(n, dtype=bool)
+    off[dst] = False
+    for _ in range(3):
+        v = rng.standard_normal(src.size) + 1j * rng.standard_normal(src.size)
+        f = np.zeros(n, dtype=np.complex128)
+        f[src] = v
+        got = apply(f.reshape(shape)).reshape(-1)
+        assert np.max(np.abs(got[off])) == 0.0
+        w = want @ v
+        assert np.linalg.norm(got[dst] - w) <= tol * np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_mpc_in_is_schur_complement_of_D_Omega(wrapped_box, dagger):
+    """The Dirichlet-block Schur operator of the oracle (every hop restricted
+    to the box) equals the Schur complement of the dense D_Omega = D[Omega,
+    Omega] (Sec. 2.1) over its 4D parity split:
+    S = D_oo - D_oe D_ee^-1 D_eo on the odd sites of Omega (its adjoint for
+    dagger), and it puts nothing anywhere else."""
+    dims, Ls, U, shape, mask, om_e, om_o, B, rng = wrapped_box
+    S = B["oo"] - B["oe"] @ np.linalg.solve(B["ee"], B["eo"])
+    want = S.conj().T if dagger else S
+    _check_on_random_vectors(lambda f: O.mpc_in(U, f, MOBIUS, mask, dagger), shape,
+                             om_o, om_o, want, rng, 1e-12)
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_eo_block_in_is_block_of_D_Omega(wrapped_box, out_parity, dagger):
+    """eo_block_in(out_parity) is the off-diagonal parity block of the dense
+    D_Omega (D_eo into even, D_oe into odd); dagger gives the adjoint of the
+    opposite block ((D_oe)^+ into even, (D_eo)^+ into odd).  Nothing lands
+    outside Omega's sites of the output parity."""
+    dims, Ls, U, shape, mask, om_e, om_o, B, rng = wrapped_box
+    src = om_o if out_parity == 0 else om_e
+    dst = om_e if out_parity == 0 else om_o
+    if not dagger:
+        want = B["eo"] if out_parity == 0 else B["oe"]
+    else:
+        want = (B["oe"] if out_parity == 0 else B["eo"]).conj().T
+    _check_on_random_vectors(lambda f: O.eo_block_in(U, f, MOBIUS, mask, out_parity, dagger),
+                             shape, src, dst, want, rng, 1e-13)

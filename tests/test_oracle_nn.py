@@ -88,6 +88,9 @@ def test_gradient_central_differences(energy):
             fd = (Lp - Lm) / (2 * h)
             an = (g1 if which == 0 else g2)[idx]
             an = an.real if part == 1.0 else an.imag
+            # the central difference (L+ - L-) / 2h carries a rounding error of
+            # about eps |L| / h = 2.2e-16 |L| / 1e-6 = 2.2e-10 |L| besides its
+            # O(h^2) truncation error: the absolute slack is five times that bound
             assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3) + 1e-9 * abs(L), (which, idx, part, fd, an)
 
 
