@@ -1,20 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the domain wall fermion hot path on one GB300 (per rank).
 
-Workload (default): Moebius DWF on 16^4 x Ls=12 (b5=1.5, c5=0.5, M5=1.8,
-m_f=0.01), links U = exp(i 0.3 H) from seed 1001, one Gaussian source.
-One step = the whole hot path on that source:
+Workload (default): the paper's per-GPU volume, Moebius DWF on 32^4 x Ls=16
+(b5=1.5, c5=0.5, M5=1.8, m_f=0.005), links U = exp(i 0.3 H) from seed 1003,
+one Gaussian source.  One step = the whole hot path on that source:
 
   * mixed-precision CGNE of D x = b to |b - D x|/|b| <= 1e-10 (FP32 operator,
     FP32 vectors, FP64 reliable updates, FP64 reductions and solution);
-  * the same solve with the Dirichlet block operator D_Omega of the 14^4
+  * the same solve with the Dirichlet block operator D_Omega of the 30^4
     interior box left by a band of width 2 in all four directions.
 
 The printed value is the Dslash-model throughput of the step: every Wilson
 hop the step applies counts 1320 flops per 5D site of its checkerboard,
-divided by the step time (CUDA events).  Beside it: time to solution of
-each solve, the plain FP64 CG time for the same system, the bare-hop
-roofline (FP32, L2 flushed between launches) and the CPU oracle baseline.
+divided by the step time (CUDA events).  Beside it, measured once: the same
+solves with plain FP64 CG, D_Omega for bands of width 1 and 4, the bare-hop
+roofline (FP32 at 32^4 x 16, L2 flushed between launches), the earlier
+16^4 x Ls=12 workload, and the CPU oracle on the host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -24,7 +25,9 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -34,13 +37,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DWF Dslash TFLOP/s & HBM GB/s; time-to-1e-10 residual vs plain FP64 CG"
-DIMS, LS = (16, 16, 16, 16), 12
-M5, MF, B5, C5 = 1.8, 0.01, 1.5, 0.5
-EPS, SEED = 0.3, 1001
-BAND_BOX = ((1, 1, 1, 1), (14, 14, 14, 14))
+DIMS, LS = (32, 32, 32, 32), 16
+M5, MF, B5, C5 = 1.8, 0.005, 1.5, 0.5
+EPS, SEED = 0.3, 1003
+BANDS = {1: ((0, 0, 0, 0), (31, 31, 31, 31)), 2: ((1, 1, 1, 1), (30, 30, 30, 30)),
+         4: ((2, 2, 2, 2), (28, 28, 28, 28))}
+STEP_BAND = 2
 FLOPS_PER_SITE = 1320
-WORKLOAD = ("Moebius DWF 16^4 x Ls=12 (b5=1.5, c5=0.5, M5=1.8, m_f=0.01, exp(i 0.3 H) links); "
-            "mixed FP32/FP64 CGNE to 1e-10 of D and of D_Omega (w=2 band, 14^4 interior box)")
+WORKLOAD = ("Moebius DWF 32^4 x Ls=16 (b5=1.5, c5=0.5, M5=1.8, m_f=0.005, exp(i 0.3 H) links); "
+            "mixed FP32/FP64 CGNE to 1e-10 of D and of D_Omega (w=2 band, 30^4 interior box)")
+# the earlier, smaller workload (Moebius 16^4 x Ls=12, m_f = 0.01), reported as extra keys
+SMALL_DIMS, SMALL_LS, SMALL_MF, SMALL_SEED = (16, 16, 16, 16), 12, 0.01, 1001
+SMALL_BAND = ((1, 1, 1, 1), (14, 14, 14, 14))
+SMALL_WORKLOAD = "Moebius DWF 16^4 x Ls=12 (b5=1.5, c5=0.5, M5=1.8, m_f=0.01, exp(i 0.3 H) links)"
+# CPU oracle sample: one M_pc^+ M_pc application (the operator work of one CG
+# iteration) on an 8^4 x Ls=16 lattice per worker
+ORACLE_SAMPLE_DIMS = (8, 8, 8, 8)
 
 
 def hop_bytes_per_site(Ls, word):
@@ -122,6 +134,96 @@ def job_value(world, flops_per_rank, job_ms):
     return world * flops_per_rank / (job_ms * 1e-3) / 1e12
 
 
+def _event_ms(fn, stream):
+    """Run fn() between two CUDA events on `stream`; returns (result, ms)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return r, a.elapsed_time(b)
+
+
+def _bare_hop(G, h, prec, configs, flush, stream, reps, tc=False):
+    """Mean time (ms) of the bare hop Dh into the even checkerboard (CUDA
+    events on the launching stream, L2 flushed before every launch) for each
+    kernel configuration (tile, lanes, chunk) or None (the handle's current
+    one); returns the best as (ms, config)."""
+    import torch
+    h.set_hop_kernel(1, 1 if tc else 0)
+    inp = torch.randn(h.cb_shape(1), device=stream.device).to(G._DTYPE[prec])
+    out = h.empty_cb(0, 1, prec)
+    saved = h.tuning(1)
+    best = None
+    for cfg in configs:
+        if cfg is not None:
+            h.set_tile(1, cfg[0], cfg[1])
+            h.set_hop_chunk(1, cfg[2])
+        for _ in range(3):
+            h.hop(out, inp, 0, prec=prec)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            ts.append(_event_ms(lambda: h.hop(out, inp, 0, prec=prec), stream)[1])
+        m = statistics.mean(ts)
+        if best is None or m < best[0]:
+            best = (m, list(cfg) if cfg is not None else list(h.tuning(1)[:3]))
+    h.set_tile(1, saved[0], saved[1])
+    h.set_hop_chunk(1, saved[2])
+    h.set_hop_kernel(1, 0)
+    del inp, out
+    return best
+
+
+def _box_source(src, box):
+    o, e = box
+    sub = src[o[3]:o[3] + e[3], o[2]:o[2] + e[2], o[1]:o[1] + e[1], o[0]:o[0] + e[0]]
+    return sub.reshape(-1)
+
+
+def _solve_flops(st, sites):
+    """Dslash-model flops of one CGNE solve: 2 hops per M_pc application, plus
+    b' (1 hop), x_e (1 hop) and the final D x (2 hops)."""
+    return (2 * st["op_applies"] + 4) * FLOPS_PER_SITE * sites
+
+
+def _small_workload(G, inputs, dev, stream, flush):
+    """The earlier workload, Moebius 16^4 x Ls=12, m_f = 0.01: one mixed solve
+    of D and of D_Omega (w = 2, 14^4 box) after a warm-up solve, and the bare
+    FP32 hop (autotuned configuration)."""
+    import numpy as np
+    import torch
+    act = G.Action(M5, SMALL_MF, B5, C5)
+    rng = np.random.default_rng(SMALL_SEED)
+    U = inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, rng=rng)
+    src = inputs.gaussian_source(SMALL_DIMS, SMALL_LS, rng=rng)
+    Ut = torch.from_numpy(U.reshape(-1)).to(dev)
+    res = {"workload": "Moebius DWF 16^4 x Ls=12 (m_f=0.01, exp(i 0.3 H) links, seed 1001): "
+                       "mixed CGNE to 1e-10 of D and of D_Omega (w=2, 14^4 box)"}
+    for name, box in (("D", None), ("D_Omega", SMALL_BAND)):
+        h = G.Handle(SMALL_DIMS, SMALL_LS, act, boxes=[box] if box else None)
+        h.set_gauge(Ut)
+        h.autotune(1, G.FP32)
+        canon = src.reshape(-1) if box is None else _box_source(src, box)
+        b = h.pack(torch.from_numpy(np.ascontiguousarray(canon)).to(dev))
+        x = torch.zeros_like(b)
+        for _ in range(2):
+            x.zero_()
+            (st, _), ms = _event_ms(lambda: h.cgne_solve(x, b, tol=1e-10, inner=G.FP32), stream)
+        res[name] = {"ms": round(ms, 3), "iters": st[0]["iters"], "true_resid": st[0]["true_resid"]}
+        if box is None:
+            sites = SMALL_DIMS[0] ** 4 // 2 * SMALL_LS
+            ms_hop, cfg = _bare_hop(G, h, G.FP32, [None], flush, stream, 10)
+            nbytes = hop_bytes_per_site(SMALL_LS, 4) * sites
+            res["dslash_f32"] = {"ms": round(ms_hop, 4), "config": cfg,
+                                 "tflops": round(FLOPS_PER_SITE * sites / (ms_hop * 1e-3) / 1e12, 3),
+                                 "gbs": round(nbytes / (ms_hop * 1e-3) / 1e9, 1)}
+        del h, b, x
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -131,20 +233,21 @@ def run_ours(args, rank, world):
     local = env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
     act = G.Action(M5, MF, B5, C5)
+    t_setup = time.time()
     rng = np.random.default_rng(SEED)
     U = inputs.gauge_field(DIMS, "exp", eps=EPS, rng=rng)
     src = inputs.gaussian_source(DIMS, LS, rng=rng)
     Ut = torch.from_numpy(U.reshape(-1)).to(dev)
+    del U
+    box = BANDS[STEP_BAND]
     hD = G.Handle(DIMS, LS, act)
     hD.set_gauge(Ut)
-    hO = G.Handle(DIMS, LS, act, boxes=[BAND_BOX])
+    hO = G.Handle(DIMS, LS, act, boxes=[box])
     hO.set_gauge(Ut)
-    # sources in the canonical layout -> device fields
     canonD = torch.from_numpy(src.reshape(-1)).to(dev)
-    o, e = BAND_BOX
-    sub = src[o[3]:o[3] + e[3], o[2]:o[2] + e[2], o[1]:o[1] + e[1], o[0]:o[0] + e[0]]
-    canonO = torch.from_numpy(np.ascontiguousarray(sub).reshape(-1)).to(dev)
+    canonO = torch.from_numpy(np.ascontiguousarray(_box_source(src, box))).to(dev)
     if args.config:   # a fixed kernel configuration (e.g. to replay a tuned run under a profiler)
         for hh in (hD, hO):
             hh.set_tile(1, args.config[0], args.config[1])
@@ -156,8 +259,10 @@ def run_ours(args, rank, world):
     bD, bO = hD.pack(canonD), hO.pack(canonO)
     xD, xO = torch.zeros_like(bD), torch.zeros_like(bO)
     sitesD = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
+    e = box[1]
     sitesO = (e[0] * e[1] * e[2] * e[3]) // 2 * LS
     del canonD, canonO
+    print(f"[bench] set-up {time.time() - t_setup:.1f} s", file=sys.stderr)
 
     def step(host=None):
         stats = []
@@ -173,11 +278,8 @@ def run_ours(args, rank, world):
         return stats
 
     def flops(stats):
-        # each M_pc application = 2 hops; + b' (1 hop), x_e (1 hop), final D (2 hops)
-        return sum((2 * s["op_applies"] + 4) * FLOPS_PER_SITE * n
-                   for s, n in zip(stats, (sitesD, sitesO)))
+        return sum(_solve_flops(s, n) for s, n in zip(stats, (sitesD, sitesO)))
 
-    stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -206,119 +308,90 @@ def run_ours(args, rank, world):
     tot_ms = job_time_ms(tot_ms, world, dev)
     value = job_value(world, tot_flops, tot_ms)
     last = all_stats[-1]
+    mixed_ms = {"D": last[0]["seconds"] * 1e3, "D_Omega": last[1]["seconds"] * 1e3}
 
     # ---- end to end: host (pinned) source in, solution out, per step
+    n_e2e = max(1, min(args.steps, 3))
     hb = [bD.cpu().pin_memory(), None, bO.cpu().pin_memory(), None]
     hb[1] = torch.empty_like(hb[0]).pin_memory()
     hb[3] = torch.empty_like(hb[2]).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-    e2e_flops = 0
-    for k in range(args.steps):
-        e2e_ev[k][0].record(stream)
-        st = step(hb)
-        e2e_ev[k][1].record(stream)
+    e2e_ms, e2e_flops = 0.0, 0
+    for _ in range(n_e2e):
+        st, ms = _event_ms(lambda: step(hb), stream)
+        e2e_ms += ms
         e2e_flops += flops(st)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
     h2d = (bD.numel() + bO.numel()) * bD.element_size()
     d2h = (xD.numel() + xO.numel()) * xD.element_size()
+    del hb
 
-    # ---- plain FP64 CG on the same two systems (time to 1e-10)
+    # ---- plain FP64 CG on the same two systems (time to 1e-10), once
     fp64 = {}
-    for name, h, x, b in (("D", hD, xD, bD), ("D_Omega", hO, xO, bO)):
-        x.zero_()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        st, _ = h.cgne_solve(x, b, tol=1e-10, inner=G.FP64)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        fp64[name] = {"ms": s0.elapsed_time(s1), "iters": st[0]["iters"],
-                      "true_resid": st[0]["true_resid"]}
-    mixed_ms = {"D": last[0]["seconds"] * 1e3, "D_Omega": last[1]["seconds"] * 1e3}
+    if not args.no_fp64_cg:
+        for name, h, x, b in (("D", hD, xD, bD), ("D_Omega", hO, xO, bO)):
+            x.zero_()
+            (st, _), ms = _event_ms(lambda: h.cgne_solve(x, b, tol=1e-10, inner=G.FP64), stream)
+            fp64[name] = {"ms": round(ms, 1), "iters": st[0]["iters"], "true_resid": st[0]["true_resid"]}
 
-    # ---- bare hop (dominant kernel): CUDA events per launch, L2 flushed
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # ---- D_Omega for the other band widths, once each (one warm-up solve)
+    bands = {}
+    for w in sorted(BANDS):
+        if w == STEP_BAND:
+            continue
+        h = G.Handle(DIMS, LS, act, boxes=[BANDS[w]])
+        h.set_gauge(Ut)
+        h.set_tile(1, tiles["D_Omega"][0], tiles["D_Omega"][1])
+        h.set_hop_chunk(1, tiles["D_Omega"][2])
+        b = h.pack(torch.from_numpy(np.ascontiguousarray(_box_source(src, BANDS[w]))).to(dev))
+        x = torch.zeros_like(b)
+        for _ in range(2):
+            x.zero_()
+            (st, _), ms = _event_ms(lambda: h.cgne_solve(x, b, tol=1e-10, inner=G.FP32), stream)
+        bands[f"w{w}"] = {"box": [list(BANDS[w][0]), list(BANDS[w][1])], "ms": round(ms, 3),
+                          "iters": st[0]["iters"], "true_resid": st[0]["true_resid"]}
+        del h, b, x
+    torch.cuda.empty_cache()
+    del src
+
+    # ---- bare hop (dominant kernel) at 32^4 x 16: CUDA events per launch, L2 flushed
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    reps = max(args.steps, 10)
     hop = {}
-    for name, prec, word in (("f32", G.FP32, 4), ("bf16", G.BF16, 2), ("bf16_tc", G.BF16, 2),
-                             ("f64", G.FP64, 8)):
-        hD.set_hop_kernel(1, 1 if name == "bf16_tc" else 0)
-        inp = torch.randn(hD.cb_shape(1), device=dev).to(G._DTYPE[prec])
-        out = hD.empty_cb(0, 1, prec)
-        for _ in range(3):
-            hD.hop(out, inp, 0, prec=prec)
-        ts = []
-        for _ in range(max(args.steps, 10)):
-            flush.fill_(1.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            hD.hop(out, inp, 0, prec=prec)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        ms = statistics.mean(ts)
+    for name, prec, word, tc in (("f32", G.FP32, 4, False), ("bf16", G.BF16, 2, False),
+                                 ("bf16_tc", G.BF16, 2, True), ("f64", G.FP64, 8, False)):
+        cfgs = [None]
+        if prec == G.FP32:
+            cfgs += [(64, 2, 8), (64, 2, 1), (32, 2, 8)]
+        ms, cfg = _bare_hop(G, hD, prec, cfgs, flush, stream, reps if prec != G.FP64 else 3, tc)
         nbytes = hop_bytes_per_site(LS, word) * sitesD
-        hop[name] = {"ms": ms, "tflops": FLOPS_PER_SITE * sitesD / (ms * 1e-3) / 1e12,
-                     "gbs": nbytes / (ms * 1e-3) / 1e9, "bytes": nbytes}
-        del inp, out
-    hD.set_hop_kernel(1, 0)
-
-    # ---- the bare FP32 hop at 32^4 x 16 (the volume its HBM-roofline target is quoted
-    # at), autotuned; unit links (the kernel's work does not depend on the values)
-    big = None
-    if not args.no_big_hop:
-        dims_b, ls_b = (32, 32, 32, 32), 16
-        hb = G.Handle(dims_b, ls_b, act)
-        hb.set_gauge(torch.from_numpy(inputs.gauge_field(dims_b, "unit").reshape(-1)).to(dev))
-        inp = torch.randn(hb.cb_shape(1), device=dev)
-        out = hb.empty_cb(0, 1, G.FP32)
-        best = None
-        for tile, chunk in ((32, 1), (64, 1), (32, 8), (64, 8)):   # the bare hop's own tuning
-            hb.set_tile(1, tile, 2)
-            hb.set_hop_chunk(1, chunk)
-            for _ in range(3):
-                hb.hop(out, inp, 0, prec=G.FP32)
-            ts = []
-            for _ in range(10):
-                flush.fill_(1.0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                hb.hop(out, inp, 0, prec=G.FP32)
-                b.record(stream)
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b))
-            m = statistics.mean(ts)
-            if best is None or m < best[0]:
-                best = (m, tile, chunk)
-        ms = best[0]
-        sites_b = 32 ** 4 // 2 * ls_b
-        nb = hop_bytes_per_site(ls_b, 4) * sites_b
-        big = {"lattice": list(dims_b), "Ls": ls_b, "tile_sites": best[1], "chunk": best[2],
-               "ms": round(ms, 4),
-               "tflops": round(FLOPS_PER_SITE * sites_b / (ms * 1e-3) / 1e12, 3),
-               "gbs": round(nb / (ms * 1e-3) / 1e9, 1), "bytes": nb}
-        del hb, inp, out
+        hop[name] = {"ms": round(ms, 4), "config": cfg,
+                     "tflops": round(FLOPS_PER_SITE * sitesD / (ms * 1e-3) / 1e12, 3),
+                     "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes}
+    small = None if args.no_small else _small_workload(G, inputs, dev, stream, flush)
     del flush
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    if big is not None:
-        big["frac_hbm"] = round(big["gbs"] / peaks.get("hbm_gbs", 6800.0), 3)
     peak = peaks.get("hbm_gbs", 6800.0)
+    for v in hop.values():
+        v["frac_hbm"] = round(v["gbs"] / peak, 3)
     traffic = None
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "hop_f32_traffic.json")))
         src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2203_17119_gb300", "csrc", "hop.cu"),
                                        "rb").read()).hexdigest()[:16]
-        if prof.get("hop_cu_sha256_16") == src_hash:
+        if prof.get("hop_cu_sha256_16") == src_hash and prof.get("lattice") == list(DIMS) \
+                and prof.get("Ls") == LS:
             traffic = prof["dram_bytes_per_launch_scaled"]
     except (OSError, ValueError, KeyError):
         pass
-    roof = {"bound": "hbm", "kernel": "k_hop<float> (bare Wilson hop, FP32, Ls=12)",
-            "achieved": round(hop["f32"]["gbs"], 1), "peak": peak, "unit": "GB/s",
+    roof = {"bound": "hbm", "kernel": "k_hop<float> (bare Wilson hop, FP32, 32^4 x Ls=16)",
+            "config_tile_lanes_chunk": hop["f32"]["config"],
+            "achieved": hop["f32"]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": round(hop["f32"]["gbs"] / peak, 3), "traffic": traffic,
+            "algorithmic_bytes_per_launch": hop["f32"]["bytes"],
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
             else "fallback 6800 GB/s"}
 
@@ -327,22 +400,23 @@ def run_ours(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded exp(i 0.3 H) SU(3) links, Gaussian source)",
-        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS,
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS, "mf": MF,
                    "inner": "FP32 operator + FP32 vectors; FP64 reliable updates/reductions/x",
-                   "l2": "working set > L2 (FP64 + FP32 solver state ~0.6 GB per solve)",
+                   "l2": "inputs larger than L2 (one FP32 checkerboard field is 0.8 GB; solver "
+                         "state ~20 GB per solve)",
                    "parallelism": f"replicas x{world}", "tile_sites_lanes_chunk": tiles},
         "time_to_solution_ms": {k: round(v, 3) for k, v in mixed_ms.items()},
         "iters": {"D": last[0]["iters"], "D_Omega": last[1]["iters"]},
         "reliable_updates": {"D": last[0]["reliable_updates"], "D_Omega": last[1]["reliable_updates"]},
         "true_resid": {"D": last[0]["true_resid"], "D_Omega": last[1]["true_resid"]},
         "fp64_cg": fp64,
-        "speedup_vs_fp64_cg": {k: round(fp64[k]["ms"] / mixed_ms[k], 2) for k in mixed_ms},
-        "dslash": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
-                   for k, v in hop.items()},
+        "speedup_vs_fp64_cg": {k: round(fp64[k]["ms"] / mixed_ms[k], 2) for k in fp64},
+        "d_omega_other_bands": bands,
+        "dslash": hop,
         "roofline": roof,
-        "dslash_32x16": big,
+        "small_16x12": small,
         "e2e": {"value": round(world * e2e_flops / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "steps": n_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -350,44 +424,132 @@ def run_ours(args, rank, world):
 
 
 # --------------------------------------------------------- CPU oracle leg
-def oracle_sample(seconds_hint=None):
-    """Time the oracle's Wilson hop (whole lattice, both parities) on the
-    workload's lattice once in a single-threaded subprocess; returns
-    (TFLOP/s, seconds, cores)."""
-    code = (
-        "import time, numpy as np, sys\n"
-        f"sys.path.insert(0, {ROOT!r})\n"
-        "from oracle import dwf as O\n"
-        "from paper_2203_17119_gb300 import inputs\n"
-        f"rng = np.random.default_rng({SEED})\n"
-        f"U = inputs.gauge_field({DIMS}, 'exp', eps={EPS}, rng=rng)\n"
-        f"psi = inputs.gaussian_source({DIMS}, {LS}, rng=rng)\n"
-        "t = time.perf_counter(); O.hop(U, psi); dt = time.perf_counter() - t\n"
-        "print(dt)\n")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    dt = float(out.stdout.strip().splitlines()[-1])
-    sites = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * LS   # both parities
-    return FLOPS_PER_SITE * sites / dt / 1e12, dt, 1
+def _oracle_mpc_normal(seed):
+    """One M_pc^+ M_pc application of the oracle (the operator work of one CG
+    iteration) on the sample lattice; returns its wall time in seconds.  Runs
+    in a spawned worker with one thread."""
+    import numpy as np
+    from oracle import dwf as O
+    from paper_2203_17119_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    # Haar links: the oracle's work does not depend on the link values
+    U = inputs.gauge_field(ORACLE_SAMPLE_DIMS, "haar", rng=rng)
+    psi = O.parity_part(inputs.gaussian_source(ORACLE_SAMPLE_DIMS, LS, rng=rng), 1)
+    prm = O.DWFParams(M5=M5, mf=MF, b5=B5, c5=C5)
+    t = time.perf_counter()
+    O.mpc(U, O.mpc(U, psi, prm), prm, True)
+    return time.perf_counter() - t
+
+
+def _sample_flops():
+    """Dslash-model flops of one M_pc^+ M_pc (4 hops) on the sample lattice."""
+    V = 1
+    for d in ORACLE_SAMPLE_DIMS:
+        V *= d
+    return 4 * FLOPS_PER_SITE * (V // 2) * LS
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """Spawned single-threaded worker processes that run the oracle sample
+    (spawn: no fork after CUDA initialisation)."""
+
+    def __init__(self, n):
+        self.n = n
+        keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                "MKL_NUM_THREADS")}
+        for k in keep:
+            os.environ[k] = "1"
+        self.pool = multiprocessing.get_context("spawn").Pool(n)
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+    def run(self, workers, seed):
+        """`workers` samples at once; returns the time of the slowest sample's
+        operator application (the samples run concurrently; their set-up is
+        not timed)."""
+        return max(self.pool.map(_oracle_mpc_normal, [seed + i for i in range(workers)]))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(iters_D):
+    """The oracle timed on the host cores: one M_pc^+ M_pc application of the
+    8^4 x 16 sample per worker, on all cores at once and on one core, in the
+    Dslash-model TFLOP/s of `value`; plus the oracle's time to 1e-10 for the D
+    solve extrapolated from it (per-iteration time scaled by volume, times the
+    GPU's iteration count)."""
+    cores = _host_cores()
+    pool = OraclePool(cores)
+    pool.run(cores, 7)                                  # warm-up: imports, first touch
+    wall_all = pool.run(cores, 11)
+    wall_1 = pool.run(1, 13)
+    pool.close()
+    f = _sample_flops()
+    scale = 1.0
+    for a, b in zip(DIMS, ORACLE_SAMPLE_DIMS):
+        scale *= a / b
+    per_iter_1 = wall_1 * scale
+    return {
+        "value": cores * f / wall_all / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+        "sample": (f"one oracle M_pc^+ M_pc (4 Wilson hops, the operator of one CG iteration) on a "
+                   f"{'x'.join(map(str, ORACLE_SAMPLE_DIMS))} x Ls={LS} Moebius lattice per worker, "
+                   f"{cores} single-threaded workers at once ({wall_all:.1f} s), numpy FP64; "
+                   "same flop model as value"),
+        "cpu_model": _cpu_model(),
+        "one_core": {"value": f / wall_1 / 1e12, "unit": "TFLOP/s", "seconds": round(wall_1, 2)},
+        "extrapolated_time_to_solution_s": {
+            "D": round(per_iter_1 * iters_D / cores, 1) if iters_D else None,
+            "how": "one-core sample time x (32^4 / sample volume) x GPU iteration count / cores "
+                   "(extrapolated, not run)"},
+    }
 
 
 def run_reference(args):
-    vals, secs = [], []
+    """The reference arm: the CPU oracle as it stands on the host cores.  Each
+    step is one M_pc^+ M_pc application of the 8^4 x 16 sample per core, all
+    cores at once; value = Dslash-model TFLOP/s over the timed steps."""
+    cores = _host_cores()
+    pool = OraclePool(cores)
+    walls = []
     for k in range(args.warmup + args.steps):
-        v, dt, cores = oracle_sample()
+        wall = pool.run(cores, 100 + k * cores)
         if k >= args.warmup:
-            vals.append(v)
-            secs.append(dt)
-    value = statistics.mean(vals)
-    sample = (f"oracle Wilson hop Dh on the whole 16^4 x Ls=12 lattice (both parities, "
-              f"{DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * LS} 5D sites) per step, numpy FP64, 1 thread")
+            walls.append(wall)
+    pool.close()
+    f = _sample_flops() * cores
+    value = f * len(walls) / sum(walls) / 1e12
+    sample = (f"per step one oracle M_pc^+ M_pc (4 Wilson hops) on a "
+              f"{'x'.join(map(str, ORACLE_SAMPLE_DIMS))} x Ls={LS} Moebius lattice on each of "
+              f"{cores} single-threaded workers at once, numpy FP64")
     return {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "Ls": LS}, "impl": "reference",
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -404,8 +566,8 @@ def run_hop(args):
     prec = G.PREC[prec_name]
     word = {G.FP64: 8, G.FP32: 4, G.BF16: 2}[prec]
     dims = (L, L, L, L)
-    U = inputs.gauge_field(dims, "exp", eps=EPS, seed=SEED)
-    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), nrhs_max=nrhs)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, seed=SMALL_SEED)
+    h = G.Handle(dims, Ls, G.Action(M5, SMALL_MF, B5, C5), nrhs_max=nrhs)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     del U
     if args.hop_config:
@@ -458,12 +620,12 @@ def run_multishift(args):
     ns = int(args.multishift[0])
     prec = G.PREC[args.multishift[1]] if len(args.multishift) > 1 else G.FP64
     tol = 1e-10
-    rng = np.random.default_rng(SEED)
-    U = inputs.gauge_field(DIMS, "exp", eps=EPS, rng=rng)
-    h = G.Handle(DIMS, LS, G.Action(M5, MF, B5, C5))
+    rng = np.random.default_rng(SMALL_SEED)
+    U = inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, rng=rng)
+    h = G.Handle(SMALL_DIMS, SMALL_LS, G.Action(M5, SMALL_MF, B5, C5))
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     h.autotune(1, G.FP32)
-    full = h.pack(torch.from_numpy(inputs.gaussian_source(DIMS, LS, rng=rng).reshape(-1)).cuda())
+    full = h.pack(torch.from_numpy(inputs.gaussian_source(SMALL_DIMS, SMALL_LS, rng=rng).reshape(-1)).cuda())
     b = full[h.nsite[0]:].contiguous()
     shifts = list(np.logspace(-4, 0, ns))
     x = torch.zeros((ns,) + tuple(b.shape), dtype=torch.float64, device="cuda")
@@ -480,7 +642,7 @@ def run_multishift(args):
         singles.append(st1[0][0]["iters"])
     torch.cuda.synchronize()
     t_single = time.time() - t
-    print(json.dumps({"workload": f"multi-shift CG on M_pc^+ M_pc, {WORKLOAD.split(';')[0]}",
+    print(json.dumps({"workload": f"multi-shift CG on M_pc^+ M_pc, {SMALL_WORKLOAD}",
                       "nshift": ns, "prec": args.multishift[1] if len(args.multishift) > 1 else "f64",
                       "tol": tol, "seconds": t_ms, "seconds_single_shift_solves": t_single,
                       "speedup": t_single / t_ms,
@@ -499,14 +661,14 @@ def run_force(args):
     from paper_2203_17119_gb300 import dwf as G
     from paper_2203_17119_gb300 import inputs
     prec_name = args.force[0] if args.force else "f64"
-    L = int(args.force[1]) if len(args.force) > 1 else DIMS[0]
-    Ls = int(args.force[2]) if len(args.force) > 2 else LS
+    L = int(args.force[1]) if len(args.force) > 1 else SMALL_DIMS[0]
+    Ls = int(args.force[2]) if len(args.force) > 2 else SMALL_LS
     prec = G.PREC[prec_name]
     word = {G.FP64: 8, G.FP32: 4}[prec]
     dims = (L, L, L, L)
-    rng = np.random.default_rng(SEED)
+    rng = np.random.default_rng(SMALL_SEED)
     U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
-    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5))
+    h = G.Handle(dims, Ls, G.Action(M5, SMALL_MF, B5, C5))
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     n = 2 * 12 * Ls * L ** 4
     X = torch.randn(n, dtype=torch.float64, device="cuda").to(G._DTYPE[prec])
@@ -543,7 +705,7 @@ def run_force(args):
     sd = (8, 8, 8, 8)
     Us = inputs.gauge_field(sd, "exp", eps=EPS, rng=rng)
     Xs, Ys = (inputs.gaussian_source(sd, Ls, rng=rng) for _ in range(2))
-    prm = O.DWFParams(M5=M5, mf=MF, b5=B5, c5=C5)
+    prm = O.DWFParams(M5=M5, mf=SMALL_MF, b5=B5, c5=C5)
     t = time.time()
     force_bilinear(Us, Xs, Ys, prm)
     oracle_s_per_site = (time.time() - t) / 8 ** 4
@@ -567,12 +729,12 @@ def run_boundary(args):
     from paper_2203_17119_gb300 import inputs
     prec_name = args.boundary[0] if args.boundary else "f32"
     prec = G.PREC[prec_name]
-    rng = np.random.default_rng(SEED)
-    U = inputs.gauge_field(DIMS, "exp", eps=EPS, seed=SEED)
-    h = G.Handle(DIMS, LS, G.Action(M5, MF, B5, C5))
+    rng = np.random.default_rng(SMALL_SEED)
+    U = inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, seed=SMALL_SEED)
+    h = G.Handle(SMALL_DIMS, SMALL_LS, G.Action(M5, SMALL_MF, B5, C5))
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     h.autotune(1, G.FP32)
-    phi = h.pack(torch.from_numpy(inputs.gaussian_source(DIMS, LS, rng=rng).reshape(-1)).cuda())
+    phi = h.pack(torch.from_numpy(inputs.gaussian_source(SMALL_DIMS, SMALL_LS, rng=rng).reshape(-1)).cuda())
     out = torch.empty_like(phi)
     force = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
     del U
@@ -587,30 +749,30 @@ def run_boundary(args):
         res[name + "_ms"] = (time.time() - t) * 1e3
         return r
 
-    timed("project", lambda: h.boundary_project(out, phi, BAND_BOX))
-    st = timed("rinv", lambda: h.boundary_rinv(out, phi, BAND_BOX, tol=1e-10, inner=prec))
+    timed("project", lambda: h.boundary_project(out, phi, SMALL_BAND))
+    st = timed("rinv", lambda: h.boundary_rinv(out, phi, SMALL_BAND, tol=1e-10, inner=prec))
     res["rinv_iters"] = st[0]["iters"]
     res["rinv_true_resid"] = st[0]["true_resid"]
-    st = timed("force", lambda: h.boundary_force(force, phi, BAND_BOX, tol=1e-10, inner=prec))
+    st = timed("force", lambda: h.boundary_force(force, phi, SMALL_BAND, tol=1e-10, inner=prec))
     res["force_iters"] = [s["iters"] for s in st]
     res["force_true_resid"] = max(s["true_resid"] for s in st)
     # the Hasenbusch ratio force against the Pauli-Villars (m_f = 1) boundary operator
-    hp = G.Handle(DIMS, LS, G.Action(M5, 1.0, B5, C5))
-    hp.set_gauge(torch.from_numpy(inputs.gauge_field(DIMS, "exp", eps=EPS, seed=SEED).reshape(-1)).cuda())
-    st = timed("ratio_force", lambda: h.boundary_ratio_force(hp, force, phi, BAND_BOX, tol=1e-10, inner=prec))
+    hp = G.Handle(SMALL_DIMS, SMALL_LS, G.Action(M5, 1.0, B5, C5))
+    hp.set_gauge(torch.from_numpy(inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, seed=SMALL_SEED).reshape(-1)).cuda())
+    st = timed("ratio_force", lambda: h.boundary_ratio_force(hp, force, phi, SMALL_BAND, tol=1e-10, inner=prec))
     res["ratio_force_iters"] = [s["iters"] for s in st]
     res["ratio_force_true_resid"] = max(s["true_resid"] for s in st)
     del hp
     # R itself: two FP64 Dirichlet CGNR solves (Omega-bar, then Omega), timed once
     torch.cuda.synchronize()
     t = time.time()
-    st = h.boundary_r(out, phi, BAND_BOX, tol=1e-10)
+    st = h.boundary_r(out, phi, SMALL_BAND, tol=1e-10)
     torch.cuda.synchronize()
     res["r_ms"] = (time.time() - t) * 1e3
     res["r_iters"] = [s["iters"] for s in st]
     res["r_true_resid"] = max(s["true_resid"] for s in st)
-    print(json.dumps({"workload": "DD-HMC boundary operator, " + WORKLOAD.split(";")[0]
-                      + f", Omega = {BAND_BOX}", "inner": prec_name, **res}))
+    print(json.dumps({"workload": "DD-HMC boundary operator, " + SMALL_WORKLOAD
+                      + f", Omega = {SMALL_BAND}", "inner": prec_name, **res}))
 
 
 def run_chebyshev(args):
@@ -628,12 +790,12 @@ def run_chebyshev(args):
     prec = G.PREC[prec_name]
     nvec = 8
     from paper_2203_17119_gb300 import inputs
-    U = inputs.gauge_field(DIMS, "exp", eps=EPS, seed=SEED)
-    h = G.Handle(DIMS, LS, G.Action(M5, MF, 1.0, 0.0), boxes=[BAND_BOX], nrhs_max=nvec)
+    U = inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, seed=SMALL_SEED)
+    h = G.Handle(SMALL_DIMS, SMALL_LS, G.Action(M5, SMALL_MF, 1.0, 0.0), boxes=[SMALL_BAND], nrhs_max=nvec)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     del U
     h.autotune(nvec, G.FP32)
-    g = torch.Generator(device="cuda").manual_seed(SEED)
+    g = torch.Generator(device="cuda").manual_seed(SMALL_SEED)
     v = torch.randn(h.cb_shape(1, nvec), dtype=torch.float64, device="cuda", generator=g).to(G._DTYPE[prec])
     t1, t2 = torch.empty_like(v), torch.empty_like(v)
 
@@ -643,7 +805,7 @@ def run_chebyshev(args):
 
     def rq(x):
         A(t2, x)
-        xr, ar = x.double().view(-1, 12, nvec, LS, 2), t2.double().view(-1, 12, nvec, LS, 2)
+        xr, ar = x.double().view(-1, 12, nvec, SMALL_LS, 2), t2.double().view(-1, 12, nvec, SMALL_LS, 2)
         num = (xr * ar).sum(dim=(0, 1, 3, 4))
         den = (xr * xr).sum(dim=(0, 1, 3, 4))
         return (num / den).cpu().numpy()
@@ -663,7 +825,7 @@ def run_chebyshev(args):
     sec = time.time() - t
     rq0, rq1 = rq(v), rq(out)
     print(json.dumps({"workload": "Chebyshev filter of the Shamir D_Omega normal Schur operator, 16^4 x Ls=12, "
-                      f"Omega = {BAND_BOX}, {nvec} vectors", "prec": prec_name, "order": order,
+                      f"Omega = {SMALL_BAND}, {nvec} vectors", "prec": prec_name, "order": order,
                       "lo": lo, "hi": hi, "ms": sec * 1e3,
                       "ms_per_A_per_vector": sec * 1e3 / order / nvec,
                       "rayleigh_before": float(np.mean(rq0)), "rayleigh_after": float(np.mean(rq1))}))
@@ -680,7 +842,7 @@ def run_large(args):
     from paper_2203_17119_gb300 import dwf as G
     from paper_2203_17119_gb300 import inputs
     dims, Ls, mf = (32, 32, 32, 32), 16, 0.005
-    rng = np.random.default_rng(SEED + 3)
+    rng = np.random.default_rng(SEED)
     U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
     src = inputs.gaussian_source(dims, Ls, rng=rng)
     Ut = torch.from_numpy(U.reshape(-1)).cuda()
@@ -731,7 +893,7 @@ def run_batched(args):
     dims, Ls = (24, 24, 24, 24), 16
     rng = np.random.default_rng(1002)
     U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
-    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), boxes=BATCH_BOXES, nrhs_max=nrhs)
+    h = G.Handle(dims, Ls, G.Action(M5, SMALL_MF, B5, C5), boxes=BATCH_BOXES, nrhs_max=nrhs)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     del U
     T = h.autotune(nrhs, prec)
@@ -802,7 +964,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-big-hop", action="store_true", help="skip the 32^4 x 16 hop line")
+    ap.add_argument("--no-fp64-cg", action="store_true", help="skip the plain FP64 CG solves")
+    ap.add_argument("--no-small", action="store_true", help="skip the 16^4 x 12 extra keys")
     ap.add_argument("--config", nargs=3, type=int, metavar=("TILE", "VL", "CHUNK"),
                     help="default workload: fixed kernel configuration instead of autotuning")
     args = ap.parse_args()
@@ -841,12 +1004,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     res = run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline:
-            v, dt, cores = oracle_sample()
-            res["cpu_baseline"] = {
-                "value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                "sample": f"one oracle Wilson hop on the whole 16^4 x Ls=12 lattice ({dt:.1f} s, "
-                          "numpy FP64, 1 thread); same flop model as value"}
+        if not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = cpu_baseline(res["iters"]["D"])
         print(json.dumps(res))
     if world > 1:
         import torch

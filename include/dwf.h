@@ -68,7 +68,9 @@
  *
  * ERRORS.  Every call returns a dwf_status; dwf_last_error() returns a
  * thread-local message for the last failure on the calling thread.  A
- * failed argument check leaves the handle unchanged.  Device kernels never
+ * failed argument check leaves the handle unchanged.  A handle belongs to
+ * the device that was current when it was created: calls that take it
+ * return DWF_ERR_ARG while another device is current.  Device kernels never
  * trap: a bounded wait that runs out sets a device error word, reported as
  * DWF_ERR_DEVICE by dwf_check_device() and by the solves.
  */
@@ -174,7 +176,7 @@ dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger,
 
 /* Same result as dwf_mpc, for callers that may not allocate device memory
  * where they apply the operator (a framework whose pool owns all device
- * memory, a CUDA-graph capture in progress, a fixed-footprint embedding).
+ * memory, a fixed-footprint embedding).
  * The paper has no counterpart: it is a deployment convenience.  The two
  * checkerboard temporaries come from a static device array of 2 x 32 MiB
  * reserved on every GPU that loads the library (held until exit); requests
@@ -184,7 +186,8 @@ dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger,
  * contents; nothing in it needs to start at zero), so calls that overlap on
  * the GPU race: serialise them.  The first call on a device looks up the
  * array's address (cudaGetSymbolAddress) with that device current; make it
- * before any stream capture. */
+ * before any stream capture.  DWF_ERR_ARG if the current device is not the
+ * one the handle was created on (as for every call taking a handle). */
 dwf_status dwf_mpc_noalloc(dwf_handle* h, void* out, const void* in, int dagger,
                            dwf_prec prec, int nrhs, void* stream);
 
@@ -287,6 +290,12 @@ dwf_status dwf_get_tuning(const dwf_handle* h, int nrhs, int* tile_sites, int* l
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);
+
+/* Number of device memory allocations (cudaMalloc) the library has made in
+ * this process so far, over all handles and devices: a caller can check that
+ * a sequence of calls allocated nothing (the operator calls, once their tile
+ * table exists, and dwf_mpc_noalloc always). */
+dwf_status dwf_alloc_count(uint64_t* n);
 
 /* Multi-shift CG: for every shift sigma_s >= 0 solve
  * (M_pc^+ M_pc + sigma_s) x_s = b on the odd checkerboard of every box and

@@ -407,3 +407,56 @@ def mpc_in(U, psi_o, p: DWFParams, mask, dagger: bool = False):
 def box_mask(dims, box) -> np.ndarray:
     """Boolean 4D mask of one box (origin, extent), periodic wrap allowed."""
     return box_id_field(dims, [box]) == 0
+
+
+class _SiteField:
+    """A field given site by site: ``f[t, z, y, x]`` -> (Ls, 4, 3) array from
+    ``value(site)``, site = (x, y, z, t), computed once per site.  ``shape``
+    is that of the full-lattice array it stands for."""
+
+    def __init__(self, shape, value):
+        self.shape = tuple(shape)
+        self._value = value
+        self._memo = {}
+
+    def __getitem__(self, key):
+        t, z, y, x = (int(k) for k in key)
+        site = (x, y, z, t)
+        v = self._memo.get(site)
+        if v is None:
+            v = self._memo[site] = self._value(site)
+        return v
+
+
+def _one_site(op, v, *args):
+    """A whole-field operator of the fifth dimension applied to one site's
+    (Ls, 4, 3) values."""
+    return op(v[None, None, None, None], *args)[0, 0, 0, 0]
+
+
+def mpc_in_site(U, psi, p: DWFParams, site, inside, dagger: bool = False):
+    """(M_pc psi)(x) of the Dirichlet block on the sites where ``inside``
+    holds (the Schur operator of mpc_in: M_oo - M_oe M_ee^-1 M_eo, every hop
+    restricted to the block), at one odd site x = ``site`` of the block, from
+    the sites within two hops of x only.  ``psi`` is indexed psi[t, z, y, x]
+    -> (Ls, 4, 3) (a full array or any object with that indexing and a
+    ``shape``); it is restricted to the block's odd sites here.  ``inside``
+    maps a site (x, y, z, t) to True / False.  Returns (Ls, 4, 3)."""
+    L = lattice_dims(U)
+    shape = tuple(L[::-1]) + tuple(psi.shape[4:])
+    zero = np.zeros(psi.shape[4:], dtype=np.complex128)
+    odd = lambda s: (s[0] + s[1] + s[2] + s[3]) % 2 == 1
+
+    def src(s):
+        return np.asarray(psi[s[3], s[2], s[1], s[0]]) if inside(s) and odd(s) else zero
+
+    f = _SiteField(shape, src)
+
+    def mid(s):   # (M_ee^-1 M_eo psi)(s) on the block's even sites, zero elsewhere
+        if not inside(s) or odd(s):
+            return zero
+        return _one_site(mooee_inv, eo_block_site(U, f, p, s, dagger), p, dagger)
+
+    t = _SiteField(shape, mid)
+    return _one_site(mooee, f[site[3], site[2], site[1], site[0]], p, dagger) \
+        - eo_block_site(U, t, p, site, dagger)

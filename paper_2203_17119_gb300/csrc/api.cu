@@ -149,9 +149,10 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
         set_error("dwf_set_tile: %d sites per tile exceed the FP64 hop's shared memory", tile_sites);
         return DWF_ERR_ARG;
     }
+    const TileSet* ts = nullptr;
+    DWF_TRY(get_tiles(h, tile_sites, &ts));
     h->tuned_T[nrhs] = tile_sites;
     h->tuned_vl[nrhs] = lanes_per_thread;
-    get_tiles(h, tile_sites);
     return DWF_OK;
 }
 
@@ -199,6 +200,15 @@ dwf_status dwf_launch_count(uint64_t* n) {
         return DWF_ERR_ARG;
     }
     *n = launch_count();
+    return DWF_OK;
+}
+
+dwf_status dwf_alloc_count(uint64_t* n) {
+    if (n == nullptr) {
+        set_error("dwf_alloc_count: null pointer");
+        return DWF_ERR_ARG;
+    }
+    *n = alloc_count();
     return DWF_OK;
 }
 

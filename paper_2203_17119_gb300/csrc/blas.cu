@@ -124,7 +124,9 @@ static dwf_status axpby_y(const int4* tiles, int nt, int nrhs, int Ls, const dou
 dwf_status launch_axpby(dwf_handle* h, int parity, int nrhs, const double* a_sys, double a_imm,
                         const void* x, dwf_prec px, const double* b_sys, double b_imm, void* y,
                         dwf_prec py, const int* run, int T, cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, T > 0 ? T : 16);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, tile_or_default(T), &tsp));
+    const TileSet& ts = *tsp;
     const int nt = ts.ntiles[parity];
     const int4* tl = ts.d_tiles[parity];
     const int Ls = h->p.Ls;
@@ -196,7 +198,9 @@ static dwf_status dot_a(const int4* tl, int nt, int nrhs, int Ls, const void* a,
 dwf_status launch_dot_partial(dwf_handle* h, int parity, const void* a, const void* b,
                               dwf_prec pa, dwf_prec pb, int nrhs, double* partial, int T,
                               cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, T > 0 ? T : 16);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, tile_or_default(T), &tsp));
+    const TileSet& ts = *tsp;
     const int nt = ts.ntiles[parity];
     const int4* tl = ts.d_tiles[parity];
     const int Ls = h->p.Ls;
@@ -227,8 +231,9 @@ __global__ void k_reduce_sys(const double* __restrict__ partial, const int* __re
 
 dwf_status launch_reduce_sys(dwf_handle* h, int parity, const double* partial, int nrhs,
                              double* out, int T, cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, T > 0 ? T : 16);
-    k_reduce_sys<<<h->nbox * nrhs, 256, 0, s>>>(partial, ts.d_box_tile_begin[parity], nrhs, out);
+    const TileSet* ts = nullptr;
+    DWF_TRY(get_tiles(h, tile_or_default(T), &ts));
+    k_reduce_sys<<<h->nbox * nrhs, 256, 0, s>>>(partial, ts->d_box_tile_begin[parity], nrhs, out);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;

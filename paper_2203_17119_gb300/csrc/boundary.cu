@@ -276,9 +276,9 @@ struct DevTables {
 };
 
 dwf_status upload(const BoundaryTables& tb, DevTables& dt) {
-    DWF_CUDA(cudaMalloc(&dt.pat, tb.pat.size() * sizeof(int)));
-    DWF_CUDA(cudaMalloc(&dt.in_omega, tb.in_omega.size() * sizeof(int)));
-    DWF_CUDA(cudaMalloc(&dt.P, tb.P.size() * sizeof(double2)));
+    DWF_CUDA(dev_malloc(&dt.pat, tb.pat.size() * sizeof(int)));
+    DWF_CUDA(dev_malloc(&dt.in_omega, tb.in_omega.size() * sizeof(int)));
+    DWF_CUDA(dev_malloc(&dt.P, tb.P.size() * sizeof(double2)));
     DWF_CUDA(cudaMemcpy(dt.pat, tb.pat.data(), tb.pat.size() * sizeof(int), cudaMemcpyHostToDevice));
     DWF_CUDA(cudaMemcpy(dt.in_omega, tb.in_omega.data(), tb.in_omega.size() * sizeof(int),
                         cudaMemcpyHostToDevice));
@@ -408,7 +408,7 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
         return DWF_OK;
     }
     double* scratch = nullptr;   // u, v, y: three full FP64 fields
-    DWF_CUDA(cudaMalloc(&scratch, 3 * elems * 16));
+    DWF_CUDA(dev_malloc(&scratch, 3 * elems * 16));
     double* u = scratch;
     double* v = scratch + 2 * elems;
     double* y = scratch + 4 * elems;
@@ -476,7 +476,7 @@ dwf_status boundary_force(dwf_handle* h, const dwf_box* omega, double* out, cons
         return DWF_OK;
     }
     double* scratch = nullptr;   // u, v, y, w: four full FP64 fields
-    DWF_CUDA(cudaMalloc(&scratch, 4 * elems * 16));
+    DWF_CUDA(dev_malloc(&scratch, 4 * elems * 16));
     double* u = scratch;
     double* v = scratch + 2 * elems;
     double* y = scratch + 4 * elems;
@@ -810,7 +810,7 @@ dwf_status boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const do
     // u, a, b, four FP64 and six FP32 solver work fields, the reduction buffers
     double* scratch = nullptr;
     const size_t fb = (size_t)elems * 16;
-    DWF_CUDA(cudaMalloc(&scratch, 10 * fb + ((size_t)kDotBlocks + 2) * nrhs * sizeof(double)));
+    DWF_CUDA(dev_malloc(&scratch, 10 * fb + ((size_t)kDotBlocks + 2) * nrhs * sizeof(double)));
     double* u = scratch;
     double* a = scratch + 2 * elems;
     double* b = scratch + 4 * elems;
@@ -927,7 +927,7 @@ dwf_status boundary_ratio_force(dwf_handle* hl, dwf_handle* hp, const dwf_box* o
     constexpr int NF = 18;   // 15 FP64 fields, then six FP32 solver work fields
     double* scratch = nullptr;
     const size_t red = ((size_t)kDotBlocks + 2) * nrhs * sizeof(double);
-    DWF_CUDA(cudaMalloc(&scratch, NF * (size_t)elems * 16 + red));
+    DWF_CUDA(dev_malloc(&scratch, NF * (size_t)elems * 16 + red));
     double* F[NF];
     for (int k = 0; k < NF; ++k) F[k] = scratch + 2 * elems * k;
     double *u_pv = F[0], *t1 = F[1], *b = F[2], *d = F[3], *u_l = F[4], *chi = F[5], *y = F[6], *zeta = F[7],

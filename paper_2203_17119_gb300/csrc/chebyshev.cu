@@ -30,7 +30,7 @@ dwf_status chebyshev_filter(dwf_handle* h, void* out, const void* in, int order,
     const double c0 = (hi + lo) / (hi - lo), c1 = -2.0 / (hi - lo);
     const int T = tile_for(h, nrhs);
     char* scratch = nullptr;   // three fields: w_{k-1}, M_pc w_k, A w_k
-    DWF_CUDA(cudaMalloc(&scratch, 3 * bytes));
+    DWF_CUDA(dev_malloc(&scratch, 3 * bytes));
     void* a = scratch;
     void* u = scratch + bytes;
     void* t = scratch + 2 * bytes;

@@ -12,6 +12,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "dev_common.cuh"
 #include "dwf_internal.cuh"
@@ -30,6 +33,10 @@ void set_error(const char* fmt, ...) {
 const char* last_error() { return g_err; }
 
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_allocs{0};
+
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+uint64_t alloc_count() { return g_allocs.load(); }
 static thread_local int g_capturing = 0;
 static thread_local int g_captured = 0;
 
@@ -49,12 +56,60 @@ dwf_status check_handle(const dwf_handle* h) {
         set_error("null handle");
         return DWF_ERR_ARG;
     }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) {
+        set_error("handle created on device %d used with device %d current", h->device, dev);
+        return DWF_ERR_ARG;
+    }
     return DWF_OK;
 }
 
-const TileSet& get_tiles(dwf_handle* h, int T) {
+dwf_status persistent_grid(const void* kern, int threads, size_t smem, int ntiles, int* grid) {
+    static std::mutex mu;
+    static std::map<int, int> n_sm;                                    // device -> SMs
+    static std::map<std::tuple<int, const void*, int, size_t>, int> occ;   // -> blocks per SM
+    int dev = 0;
+    DWF_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto is = n_sm.find(dev);
+    if (is == n_sm.end()) {
+        int n = 0;
+        DWF_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        is = n_sm.emplace(dev, n > 0 ? n : 1).first;
+    }
+    const auto key = std::make_tuple(dev, kern, threads, smem);
+    auto io = occ.find(key);
+    if (io == occ.end()) {
+        int per_sm = 0;
+        DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        io = occ.emplace(key, per_sm > 0 ? per_sm : 1).first;
+    }
+    const long g = (long)io->second * is->second;
+    *grid = (int)(g < ntiles ? g : ntiles);
+    return DWF_OK;
+}
+
+const TileSet* find_tiles(const dwf_handle* h, int T) {
     auto it = h->tiles.find(T);
-    if (it != h->tiles.end()) return it->second;
+    return it == h->tiles.end() ? nullptr : &it->second;
+}
+
+static void free_tiles(TileSet& ts) {
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(ts.d_tiles[p]);
+        cudaFree(ts.d_box_tile_begin[p]);
+        ts.d_tiles[p] = nullptr;
+        ts.d_box_tile_begin[p] = nullptr;
+    }
+}
+
+dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
+    *out = find_tiles(h, T);
+    if (*out != nullptr) return DWF_OK;
+    if (T < 1) {
+        set_error("tile table: %d sites per tile", T);
+        return DWF_ERR_ARG;
+    }
     TileSet ts;
     ts.T = T;
     for (int p = 0; p < 2; ++p) {
@@ -68,15 +123,24 @@ const TileSet& get_tiles(dwf_handle* h, int T) {
         }
         ts.box_tile_begin[p][h->nbox] = (int)tl.size();
         ts.ntiles[p] = (int)tl.size();
+        cudaError_t e = cudaSuccess;
         if (!tl.empty()) {
-            cudaMalloc(&ts.d_tiles[p], tl.size() * sizeof(int4));
-            cudaMemcpy(ts.d_tiles[p], tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            e = dev_malloc(&ts.d_tiles[p], tl.size() * sizeof(int4));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(ts.d_tiles[p], tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
         }
-        cudaMalloc(&ts.d_box_tile_begin[p], (h->nbox + 1) * sizeof(int));
-        cudaMemcpy(ts.d_box_tile_begin[p], ts.box_tile_begin[p].data(), (h->nbox + 1) * sizeof(int),
-                   cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = dev_malloc(&ts.d_box_tile_begin[p], (h->nbox + 1) * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ts.d_box_tile_begin[p], ts.box_tile_begin[p].data(), (h->nbox + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_tiles(ts);
+            set_error("tile table of %d sites per tile: %s", T, cudaGetErrorString(e));
+            return DWF_ERR_CUDA;
+        }
     }
-    return h->tiles.emplace(T, ts).first->second;
+    *out = &h->tiles.emplace(T, ts).first->second;
+    return DWF_OK;
 }
 
 // ----------------------------------------------------------- link tables
@@ -224,11 +288,16 @@ static FiveD make_f5(const dwf_params& p) {
     return f;
 }
 
+static dwf_status h2d(void* dst, const void* src, size_t bytes) {
+    DWF_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+    return DWF_OK;
+}
+
 template <class T>
 static dwf_status dalloc(T** ptr, size_t n) {
     *ptr = nullptr;
     if (n == 0) n = 1;
-    DWF_CUDA(cudaMalloc((void**)ptr, n * sizeof(T)));
+    DWF_CUDA(dev_malloc(ptr, n * sizeof(T)));
     return DWF_OK;
 }
 
@@ -364,10 +433,10 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         if (st == DWF_OK) st = dalloc(&h->d_site_box[q], ns);
         if (st == DWF_OK) st = dalloc(&h->d_site_local[q], ns);
         if (st != DWF_OK) break;
-        cudaMemcpy(h->d_nbr[q], nbr.data(), ns * 8 * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(h->d_link_src[q], lsrc.data(), ns * 8 * sizeof(int64_t), cudaMemcpyHostToDevice);
-        cudaMemcpy(h->d_site_box[q], site_box[q].data(), ns * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(h->d_site_local[q], site_local[q].data(), ns * sizeof(int), cudaMemcpyHostToDevice);
+        st = h2d(h->d_nbr[q], nbr.data(), ns * 8 * sizeof(int));
+        if (st == DWF_OK) st = h2d(h->d_link_src[q], lsrc.data(), ns * 8 * sizeof(int64_t));
+        if (st == DWF_OK) st = h2d(h->d_site_box[q], site_box[q].data(), ns * sizeof(int));
+        if (st == DWF_OK) st = h2d(h->d_site_local[q], site_local[q].data(), ns * sizeof(int));
         for (int pr = 0; pr < 3 && st == DWF_OK; ++pr)
             st = dalloc((char**)&h->d_links[pr][q], ns * 144 * prec_size((dwf_prec)pr));
     }
@@ -376,7 +445,7 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         for (int b = 0; b < h->nbox; ++b) { bv[b] = h->box_vol[b]; bv[h->nbox + b] = prefix[b]; }
         st = dalloc(&h->d_box_canon_vol, 2 * h->nbox);
         if (st == DWF_OK)
-            cudaMemcpy(h->d_box_canon_vol, bv.data(), bv.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            st = h2d(h->d_box_canon_vol, bv.data(), bv.size() * sizeof(int64_t));
     }
     if (st == DWF_OK) st = init_hop_kernels();
     if (st == DWF_OK) st = init_local_kernels();
@@ -387,16 +456,22 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         build_fived_mats(f5, mats);
         st = dalloc(&h->d_mats, mats.size());
         if (st == DWF_OK)
-            cudaMemcpy(h->d_mats, mats.data(), mats.size() * sizeof(float), cudaMemcpyHostToDevice);
+            st = h2d(h->d_mats, mats.data(), mats.size() * sizeof(float));
     }
     if (st == DWF_OK) st = dalloc(&h->d_err, 1);
     if (st == DWF_OK) {
-        cudaMemset(h->d_err, 0, sizeof(int));
+        if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess) {
+            set_error("dwf_create: clearing the device error word failed");
+            st = DWF_ERR_CUDA;
+        }
         const size_t nmax = (size_t)std::max(h->nsite[0], h->nsite[1]) * 12 * p->Ls * nrhs_max * 2;
-        st = dalloc((double**)&h->d_tmp, nmax);
+        if (st == DWF_OK) st = dalloc((double**)&h->d_tmp, nmax);
         if (st == DWF_OK) st = dalloc((double**)&h->d_tmp2, nmax);
     }
-    if (st == DWF_OK) get_tiles(h, 32);   // default tile table, built up front
+    if (st == DWF_OK) {   // default tile table, built up front
+        const TileSet* ts = nullptr;
+        st = get_tiles(h, 32, &ts);
+    }
     if (st == DWF_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {

@@ -31,6 +31,15 @@ inline size_t hop_smem(int T, size_t link_word, int nwarps, int nrhs) {
 // ------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
 
+// device allocations made by the library (cudaMalloc through dev_malloc)
+void note_alloc();
+uint64_t alloc_count();
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+    note_alloc();
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 // kernel launch accounting (graph captures count into the graph instead)
 void note_launch();
 void capture_begin();
@@ -151,9 +160,18 @@ struct dwf_handle {
 namespace dwf {
 
 // ------------------------------------------------------ host helpers
-const TileSet& get_tiles(dwf_handle* h, int T);
+// Sites per tile of a launch: the call's own value, or 16 when it gives none.
+inline int tile_or_default(int T) { return T > 0 ? T : 16; }
+// The tile table of T sites per tile, built (and allocated) on first use.
+dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out);
+// The tile table if it exists already (never allocates), else nullptr.
+const TileSet* find_tiles(const dwf_handle* h, int T);
+// A handle is used on the device it was created on: DWF_ERR_ARG otherwise.
 dwf_status check_handle(const dwf_handle* h);
 size_t prec_size(dwf_prec p);   // bytes per real
+// Persistent grid of a kernel: the blocks resident at once on the current
+// device (occupancy and SM count cached per device), at most one per tile.
+dwf_status persistent_grid(const void* kern, int threads, size_t smem, int ntiles, int* grid);
 
 // ------------------------------------------------------ launchers
 // hop kinds

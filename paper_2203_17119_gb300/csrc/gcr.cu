@@ -108,23 +108,23 @@ static dwf_status gcr_ws(dwf_handle* h, int nrhs, int k, GcrWS** out) {
         GcrWS& v = g_gcr[h];
         const size_t no = cb_elems(h, 1, nrhs), ne = cb_elems(h, 0, nrhs);
         const size_t nm = no > ne ? no : ne;
-        DWF_CUDA(cudaMalloc(&v.q, (size_t)k * no * 8));
-        DWF_CUDA(cudaMalloc(&v.zz, (size_t)k * no * 8));
-        DWF_CUDA(cudaMalloc(&v.r, no * 8));
-        DWF_CUDA(cudaMalloc(&v.xlo, no * 8));
-        DWF_CUDA(cudaMalloc(&v.tA, nm * 16));
-        DWF_CUDA(cudaMalloc(&v.tB, nm * 16));
-        DWF_CUDA(cudaMalloc(&v.x64, no * 16));
-        DWF_CUDA(cudaMalloc(&v.bp64, no * 16));
-        DWF_CUDA(cudaMalloc(&v.t64a, nm * 16));
-        DWF_CUDA(cudaMalloc(&v.t64b, nm * 16));
-        DWF_CUDA(cudaMalloc(&v.t64c, nm * 16));
-        DWF_CUDA(cudaMalloc(&v.full64, (no + ne) * 16));
-        DWF_CUDA(cudaMalloc(&v.t64d, no * 16));
-        DWF_CUDA(cudaMalloc(&v.t32, no * 8));
+        DWF_CUDA(dev_malloc(&v.q, (size_t)k * no * 8));
+        DWF_CUDA(dev_malloc(&v.zz, (size_t)k * no * 8));
+        DWF_CUDA(dev_malloc(&v.r, no * 8));
+        DWF_CUDA(dev_malloc(&v.xlo, no * 8));
+        DWF_CUDA(dev_malloc(&v.tA, nm * 16));
+        DWF_CUDA(dev_malloc(&v.tB, nm * 16));
+        DWF_CUDA(dev_malloc(&v.x64, no * 16));
+        DWF_CUDA(dev_malloc(&v.bp64, no * 16));
+        DWF_CUDA(dev_malloc(&v.t64a, nm * 16));
+        DWF_CUDA(dev_malloc(&v.t64b, nm * 16));
+        DWF_CUDA(dev_malloc(&v.t64c, nm * 16));
+        DWF_CUDA(dev_malloc(&v.full64, (no + ne) * 16));
+        DWF_CUDA(dev_malloc(&v.t64d, no * 16));
+        DWF_CUDA(dev_malloc(&v.t32, no * 8));
         const int64_t nsmax = h->nsite[0] > h->nsite[1] ? h->nsite[0] : h->nsite[1];
-        DWF_CUDA(cudaMalloc(&v.part, (size_t)2 * (nsmax / kMinTile + h->nbox + 1) * nrhs * 8));
-        DWF_CUDA(cudaMalloc(&v.scal, (size_t)8 * h->nbox * nrhs * 8));
+        DWF_CUDA(dev_malloc(&v.part, (size_t)2 * (nsmax / kMinTile + h->nbox + 1) * nrhs * 8));
+        DWF_CUDA(dev_malloc(&v.scal, (size_t)8 * h->nbox * nrhs * 8));
         v.nrhs = nrhs;
         v.k = k;
         *out = &v;
@@ -151,7 +151,9 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
     cudaStream_t s = user;
     const int nsys = h->nbox * nrhs;
     const int T = tile_for(h, nrhs);
-    const TileSet& ts = get_tiles(h, T);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, T, &tsp));
+    const TileSet& ts = *tsp;
     const size_t ne = cb_elems(h, 0, nrhs), no = cb_elems(h, 1, nrhs);
     const double* be = b;
     const double* bo = b + 2 * ne;

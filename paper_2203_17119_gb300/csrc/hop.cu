@@ -536,24 +536,8 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
         return DWF_ERR_ARG;
     }
     // persistent grid: as many CTAs as are resident at once, at most one per tile
-    static std::map<std::pair<const void*, long>, int> occ_cache;
-    const auto key = std::make_pair((const void*)kern, (long)threads * 1000000L + (long)smem);
-    int per_sm = 0;
-    auto it = occ_cache.find(key);
-    if (it == occ_cache.end()) {
-        DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-        occ_cache[key] = per_sm;
-    } else {
-        per_sm = it->second;
-    }
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    int grid = (per_sm > 0 ? per_sm : 1) * n_sm;
-    if (grid > nt) grid = nt;
+    int grid = 0;
+    DWF_TRY(persistent_grid((const void*)kern, threads, smem, nt, &grid));
     kern<<<grid, threads, smem, s>>>(a);
     note_launch();
     DWF_CUDA(cudaGetLastError());
@@ -616,7 +600,9 @@ dwf_status init_hop_kernels() {
 }
 
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, c.T > 0 ? c.T : 16);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, tile_or_default(c.T), &tsp));
+    const TileSet& ts = *tsp;
     if (c.prec_link == DWF_FP64) {
         if (c.prec_in != DWF_FP64 || c.prec_out != DWF_FP64) return DWF_ERR_UNSUPPORTED;
         return launch_t<double, double, double, double, 1>(h, c, ts, s);

@@ -313,23 +313,8 @@ static dwf_status launch_tc_t(dwf_handle* h, const HopCall& c, const TileSet& ts
         kern = moo ? k_hop_tc<Sin, Sout, true, EPI_MOO> : k_hop_tc<Sin, Sout, true, EPI_PLAIN>;
     else
         kern = moo ? k_hop_tc<Sin, Sout, false, EPI_MOO> : k_hop_tc<Sin, Sout, false, EPI_PLAIN>;
-    static std::map<std::pair<const void*, long>, int> occ_cache;
-    const auto key = std::make_pair((const void*)kern, (long)smem);
-    int per_sm = 0;
-    auto it = occ_cache.find(key);
-    if (it == occ_cache.end()) {
-        DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-        occ_cache[key] = per_sm;
-    } else {
-        per_sm = it->second;
-    }
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const int grid = std::min(nt, std::max(per_sm, 1) * n_sm);
+    int grid = 0;
+    DWF_TRY(persistent_grid((const void*)kern, threads, smem, nt, &grid));
     kern<<<grid, threads, smem, s>>>(a);
     note_launch();
     DWF_CUDA(cudaGetLastError());

@@ -601,27 +601,6 @@ static LocalMatArgs mat_args(dwf_handle* h, const LocalCall& c, const TileSet& t
     return a;
 }
 
-// Persistent grid: the blocks resident at once, at most one per tile.
-static dwf_status persistent_grid(const void* kern, int threads, size_t smem, int nt, int* grid) {
-    static std::map<std::pair<const void*, long>, int> cache;
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const auto key = std::make_pair(kern, (long)threads * 1000000L + (long)smem);
-    auto it = cache.find(key);
-    int per_sm = 0;
-    if (it == cache.end()) {
-        DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-        cache[key] = per_sm;
-    } else {
-        per_sm = it->second;
-    }
-    *grid = std::min(nt, std::max(per_sm, 1) * std::max(n_sm, 1));
-    return DWF_OK;
-}
 
 template <class Sin, class Sin2, class Sout, class Svec>
 static dwf_status launch_mat(dwf_handle* h, const LocalCall& c, const TileSet& ts, cudaStream_t s) {
@@ -734,7 +713,9 @@ static dwf_status launch_lt(dwf_handle* h, const LocalCall& c, const TileSet& ts
 }
 
 dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, c.T > 0 ? c.T : 16);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, tile_or_default(c.T), &tsp));
+    const TileSet& ts = *tsp;
     const dwf_prec pi = c.prec_in, po = c.prec_out;
     const dwf_prec p2 = c.in2 ? c.prec_in2 : pi;
     if (c.f5 != nullptr && (pi != DWF_FP64 || po != DWF_FP64)) return DWF_ERR_UNSUPPORTED;

@@ -32,7 +32,7 @@ struct DevBuf {
 };
 
 dwf_status dev_alloc(DevBuf& b, size_t bytes) {
-    DWF_CUDA(cudaMalloc(&b.p, bytes ? bytes : 16));
+    DWF_CUDA(dev_malloc(&b.p, bytes ? bytes : 16));
     return DWF_OK;
 }
 
@@ -95,7 +95,9 @@ static dwf_status multishift_core(dwf_handle* h, double* x, const double* b, con
     DWF_TRY(dev_alloc(tA, f64));
     DWF_TRY(dev_alloc(tB, f64));
     DWF_TRY(dev_alloc(ps, f64 * (size_t)std::max(nshift - 1, 1)));
-    const TileSet& ts = get_tiles(h, T);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, T, &tsp));
+    const TileSet& ts = *tsp;
     DWF_TRY(dev_alloc(part, (size_t)ts.ntiles[1] * nrhs * sizeof(double)));
     // device scalars: [4][nshift][nsys] (x coefficient, zeta, beta_s, unused) + [3][nsys]
     DWF_TRY(dev_alloc(dsc, ((size_t)4 * nshift + 3) * nsys * sizeof(double)));
@@ -337,7 +339,9 @@ dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const dou
                                  nullptr, T, s));
             std::vector<double> rn(nsys), bn(nsys);
             DevBuf part, d2;
-            DWF_TRY(dev_alloc(part, (size_t)get_tiles(h, T).ntiles[1] * nrhs * sizeof(double)));
+            const TileSet* tsp = nullptr;
+            DWF_TRY(get_tiles(h, T, &tsp));
+            DWF_TRY(dev_alloc(part, (size_t)tsp->ntiles[1] * nrhs * sizeof(double)));
             DWF_TRY(dev_alloc(d2, (size_t)nsys * sizeof(double)));
             DWF_TRY(sys_dot(h, dr, dr, DWF_FP64, nrhs, static_cast<double*>(part.p),
                             static_cast<double*>(d2.p), rn, s));

@@ -385,19 +385,19 @@ static dwf_status nn_ws(dwf_handle* h, int nrhs, int C, bool train, NNWS** out) 
         cudaFree(w.gphi); cudaFree(w.wpart); cudaFree(w.gw); cudaFree(w.at); cudaFree(w.aw);
         w = NNWS();
         const int64_t f = full_floats(h, nrhs);
-        DWF_CUDA(cudaMalloc(&w.x0, f * 4));
-        DWF_CUDA(cudaMalloc(&w.R, (size_t)kNDir * f * 4));
-        DWF_CUDA(cudaMalloc(&w.phi, (size_t)C * f * 4));
-        DWF_CUDA(cudaMalloc(&w.psi, (size_t)kNDir * f * 4));
-        DWF_CUDA(cudaMalloc(&w.z, f * 4));
+        DWF_CUDA(dev_malloc(&w.x0, f * 4));
+        DWF_CUDA(dev_malloc(&w.R, (size_t)kNDir * f * 4));
+        DWF_CUDA(dev_malloc(&w.phi, (size_t)C * f * 4));
+        DWF_CUDA(dev_malloc(&w.psi, (size_t)kNDir * f * 4));
+        DWF_CUDA(dev_malloc(&w.z, f * 4));
         if (train) {
-            DWF_CUDA(cudaMalloc(&w.gphi, (size_t)C * f * 4));
+            DWF_CUDA(dev_malloc(&w.gphi, (size_t)C * f * 4));
             w.wblocks = 152 * 2;
-            DWF_CUDA(cudaMalloc(&w.wpart, (size_t)w.wblocks * C * kNDir * 32 * sizeof(double)));
-            DWF_CUDA(cudaMalloc(&w.gw, (w1_len(C) + w2_len(C)) * sizeof(double)));
+            DWF_CUDA(dev_malloc(&w.wpart, (size_t)w.wblocks * C * kNDir * 32 * sizeof(double)));
+            DWF_CUDA(dev_malloc(&w.gw, (w1_len(C) + w2_len(C)) * sizeof(double)));
             const size_t odd = (size_t)h->nsite[1] * 12 * h->p.Ls * nrhs * 2;
-            DWF_CUDA(cudaMalloc(&w.at, odd * 4));
-            DWF_CUDA(cudaMalloc(&w.aw, odd * 4));
+            DWF_CUDA(dev_malloc(&w.at, odd * 4));
+            DWF_CUDA(dev_malloc(&w.aw, odd * 4));
         }
         w.nrhs = nrhs;
         w.C = C;
@@ -432,7 +432,9 @@ static TransArgs trans_args(dwf_handle* h, int nrhs, int p) {
 static dwf_status launch_transport(dwf_handle* h, int nrhs, const float* in, float* out,
                                    const int* dirs, int ndir, bool sum, const float* const* ins,
                                    cudaStream_t s) {
-    const TileSet& ts = get_tiles(h, tile_for(h, nrhs));
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, tile_for(h, nrhs), &tsp));
+    const TileSet& ts = *tsp;
     for (int p = 0; p < 2; ++p) {
         if (ts.ntiles[p] == 0) continue;
         TransArgs a = trans_args(h, nrhs, p);
@@ -511,7 +513,7 @@ static dwf_status nn_forward(dwf_nn* K, dwf_handle* h, NNWS& w, int nrhs, cudaSt
     for (int d = 0; d < kNDir; ++d) ins[d] = w.psi + d * f;
     // device array of pointers
     static thread_local const float** d_ins = nullptr;
-    if (d_ins == nullptr) DWF_CUDA(cudaMalloc(&d_ins, kNDir * sizeof(float*)));
+    if (d_ins == nullptr) DWF_CUDA(dev_malloc(&d_ins, kNDir * sizeof(float*)));
     DWF_CUDA(cudaMemcpyAsync(d_ins, ins, sizeof(ins), cudaMemcpyHostToDevice, s));
     return launch_transport(h, nrhs, nullptr, w.z, kDirsFwd, kNDir, true, d_ins, s);
 }
@@ -548,11 +550,11 @@ dwf_status dwf_nn_create(dwf_nn** out, int channels) {
         K->w1[2 * (so * 4 + so)] = 1.f;
         K->w2[2 * (so * 4 + so)] = 1.f;
     }
-    if (cudaMalloc(&K->d_w1, n1 * 4) != cudaSuccess || cudaMalloc(&K->d_w2, n2 * 4) != cudaSuccess ||
-        cudaMalloc(&K->d_m, (n1 + n2) * 4) != cudaSuccess ||
-        cudaMalloc(&K->d_v, (n1 + n2) * 4) != cudaSuccess ||
-        cudaMalloc(&K->d_mix1, n1 * 4) != cudaSuccess || cudaMalloc(&K->d_mix2, n2 * 4) != cudaSuccess ||
-        cudaMalloc(&K->d_mix2h, n2 * 4) != cudaSuccess) {
+    if (dev_malloc(&K->d_w1, n1 * 4) != cudaSuccess || dev_malloc(&K->d_w2, n2 * 4) != cudaSuccess ||
+        dev_malloc(&K->d_m, (n1 + n2) * 4) != cudaSuccess ||
+        dev_malloc(&K->d_v, (n1 + n2) * 4) != cudaSuccess ||
+        dev_malloc(&K->d_mix1, n1 * 4) != cudaSuccess || dev_malloc(&K->d_mix2, n2 * 4) != cudaSuccess ||
+        dev_malloc(&K->d_mix2h, n2 * 4) != cudaSuccess) {
         set_error("dwf_nn_create: cudaMalloc failed");
         return DWF_ERR_CUDA;
     }
@@ -632,10 +634,12 @@ dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const flo
     DWF_CUDA(cudaMemcpyAsync(w.x0 + c0, r, c1 * 4, cudaMemcpyDeviceToDevice, s));
     DWF_TRY(nn_forward(K, h, w, nrhs, s));
     const int T = tile_for(h, nrhs);
-    const TileSet& ts = get_tiles(h, T);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, T, &tsp));
+    const TileSet& ts = *tsp;
     std::vector<double> h1(nrhs), h2(nrhs), h3(nrhs);
     double* d_scal;
-    DWF_CUDA(cudaMalloc(&d_scal, (size_t)(4 * nrhs + (ts.ntiles[1] + 1) * nrhs) * sizeof(double)));
+    DWF_CUDA(dev_malloc(&d_scal, (size_t)(4 * nrhs + (ts.ntiles[1] + 1) * nrhs) * sizeof(double)));
     double* d1 = d_scal;
     double* d2 = d_scal + nrhs;
     double* d_coef = d_scal + 2 * nrhs;

@@ -4,9 +4,8 @@
 //
 // Who needs it: code that may not call cudaMalloc on the path where it
 // applies the operator -- a host framework that owns all device memory
-// through its own pool and forbids raw allocations, a caller recording a
-// CUDA graph (cudaMalloc is illegal inside stream capture), or an embedding
-// that must keep the footprint of its calls fixed and known at load time.
+// through its own pool and forbids raw allocations, or an embedding that
+// must keep the footprint of its calls fixed and known at load time.
 // The array below is reserved when the module loads, on every GPU that loads
 // the library, and is held until the process exits.
 //
@@ -89,8 +88,9 @@ extern "C" dwf_status dwf_mpc_noalloc(dwf_handle* h, void* out, const void* in, 
                   need, kNoAllocTempBytes);
         return DWF_ERR_ARG;
     }
-    // the tile table must already exist: building one would allocate
-    if (h->tiles.find(tile_for(h, nrhs)) == h->tiles.end()) {
+    // the tile table must already exist: building one would allocate (the
+    // same tile size the launches below look up)
+    if (find_tiles(h, tile_or_default(tile_for(h, nrhs))) == nullptr) {
         set_error("dwf_mpc_noalloc: no tile table for nrhs = %d yet (call dwf_mpc or dwf_autotune "
                   "once first)", nrhs);
         return DWF_ERR_ARG;

@@ -18,11 +18,11 @@
 namespace dwf {
 
 // Sites per tile for every kernel of an operator chain with nrhs right-hand
-// sides: the autotuned value if there is one, else 16, at most 256 / N5 so
-// that a hop CTA (N5 / VL threads per site) never exceeds 256 threads.
+// sides: the value dwf_autotune or dwf_set_tile chose (never below kMinTile),
+// else 32, whose table every handle builds when it is created.
 int tile_for(dwf_handle* h, int nrhs) {
     auto it = h->tuned_T.find(nrhs);
-    if (it != h->tuned_T.end()) return it->second;
+    if (it != h->tuned_T.end() && it->second >= kMinTile) return it->second;
     return 32;
 }
 
@@ -54,7 +54,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     // candidates are timed with L2 flushed (solves stream more than L2 holds)
     const size_t flush_bytes = (size_t)256 << 20;
     void* flush = nullptr;
-    DWF_CUDA(cudaMalloc(&flush, flush_bytes));
+    DWF_CUDA(dev_malloc(&flush, flush_bytes));
     float best_ms = 1e30f;
     int best_T = tile_for(h, nrhs);
     int best_vl = 2;

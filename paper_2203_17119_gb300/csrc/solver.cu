@@ -125,7 +125,7 @@ __global__ void k_add2(double* out, const double* a, const double* b, int n) {
 
 static dwf_status ws_alloc(void** p, size_t bytes) {
     *p = nullptr;
-    DWF_CUDA(cudaMalloc(p, bytes ? bytes : 16));
+    DWF_CUDA(dev_malloc(p, bytes ? bytes : 16));
     return DWF_OK;
 }
 
@@ -205,7 +205,9 @@ static dwf_status cg_iteration(dwf_handle* h, SolverWS& w, SysView v, dwf_prec p
     const int nrhs = w.nrhs;
     // t = M_pc p from t1 = (b5 + c5 S5) p, |t|^2 = <p, A p>
     DWF_TRY(op_mpc_pre(h, w.t, w.p, w.tmp3, pv, po, nrhs, w.tmp1, w.tmp2, w.part, s));
-    const int* box_tb = get_tiles(h, tile_for(h, nrhs)).d_box_tile_begin[1];
+    const TileSet* ts = nullptr;
+    DWF_TRY(get_tiles(h, tile_for(h, nrhs), &ts));
+    const int* box_tb = ts->d_box_tile_begin[1];
     k_reduce_step<0><<<v.nsys, 1024, 0, s>>>(w.part, box_tb, nrhs, v, delta);
     note_launch();
     DWF_CUDA(cudaGetLastError());

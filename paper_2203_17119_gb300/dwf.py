@@ -81,6 +81,7 @@ def signatures():
         "dwf_check_device": [vp],
         "dwf_hop": [vp, vp, vp, i, i, i, i, vp],
         "dwf_launch_count": [C.POINTER(C.c_uint64)],
+        "dwf_alloc_count": [C.POINTER(C.c_uint64)],
         "dwf_autotune": [vp, i, i, C.POINTER(C.c_int)],
         "dwf_set_tile": [vp, i, i, i],
         "dwf_set_hop_kernel": [vp, i, i],
@@ -138,6 +139,13 @@ def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     n = C.c_uint64()
     _check(lib().dwf_launch_count(C.byref(n)))
+    return n.value
+
+
+def alloc_count() -> int:
+    """Device allocations (cudaMalloc) made by the library so far in this process."""
+    n = C.c_uint64()
+    _check(lib().dwf_alloc_count(C.byref(n)))
     return n.value
 
 

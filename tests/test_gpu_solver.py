@@ -146,3 +146,29 @@ def test_bf16_tensor_core_solve():
     st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.BF16)
     xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
     assert st[0]["status"] == 0 and O.true_residual(U, xf, b, MOBIUS) <= 1e-10
+
+
+def test_solver_time_caps():
+    """A wall-clock cap that runs out stops every solver with DWF_ERR_TIMEOUT
+    and leaves x at the last iterate: the true residual reported for it is
+    the one the oracle recomputes from the returned x (CGNE and GCR), or x is
+    the last multi-shift iterate (zero when the cap is hit before the first
+    iteration)."""
+    dims, Ls = (8, 8, 8, 8), 8
+    U, b, h, bf = _problem(dims, Ls, MOBIUS, "exp", seed=7)
+    cap = 1e-6
+    for name in ("cgne", "gcr"):
+        x = torch.zeros_like(bf)
+        if name == "cgne":
+            st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32, max_seconds=cap, allow_fail=True)
+        else:
+            st, rc = h.gcr_solve(x, bf, tol=1e-10, max_seconds=cap, allow_fail=True)
+        assert rc == 4 and st[0]["status"] == 4, (name, rc, st)
+        xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)
+        r = _residuals(U, MOBIUS, xf, b, None)[0]
+        assert 1e-10 < r and abs(r - st[0]["true_resid"]) <= 1e-6 * r, (name, r, st[0])
+    bo = bf[h.nsite[0]:].contiguous()
+    xs = torch.full((2,) + tuple(bo.shape), 7.0, dtype=torch.float64, device="cuda")
+    st, rc = h.multishift_solve(xs, bo, [0.01, 0.1], tol=1e-10, max_seconds=cap, allow_fail=True)
+    assert rc == 4
+    assert float(xs.abs().max()) == 0.0

@@ -189,3 +189,29 @@ def test_site_evaluation_matches_lattice():
                                atol=1e-13)
             assert np.allclose(O.eo_block_site(U, psi, MOBIUS, x, dag),
                                blk[x[3], x[2], x[1], x[0]], atol=1e-13)
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_mpc_site_evaluation_matches_block_operator(dagger):
+    """The per-site Dirichlet-block Schur operator (two hops of stencil) equals
+    mpc_in on the whole lattice at odd sites inside a box that wraps and at
+    its faces, and mpc itself for a box that is the whole lattice."""
+    dims, Ls = (4, 4, 6, 4), 4
+    rng = np.random.default_rng(23)
+    U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
+    psi = O.parity_part(inputs.gaussian_source(dims, Ls, rng=rng), 1)
+    box = ((3, 0, 4, 1), (3, 4, 5, 2))
+    mask = O.box_mask(dims, box)
+    full = O.mpc_in(U, psi, MOBIUS, mask, dagger)
+    inside = lambda s: bool(mask[s[3], s[2], s[1], s[0]])
+    cand = [(x, y, z, t) for t in range(dims[3]) for z in range(dims[2]) for y in range(dims[1])
+            for x in range(dims[0]) if (x + y + z + t) % 2 == 1 and inside((x, y, z, t))]
+    sites = cand[::7] + [cand[-1]]          # spread over the box, faces and wrap included
+    assert len(sites) >= 8
+    for x in sites:
+        got = O.mpc_in_site(U, psi, MOBIUS, x, inside, dagger)
+        assert np.allclose(got, full[x[3], x[2], x[1], x[0]], atol=1e-12), x
+    whole = O.mpc(U, psi, MOBIUS, dagger)
+    for x in [(1, 0, 0, 0), (2, 3, 5, 3)]:
+        got = O.mpc_in_site(U, psi, MOBIUS, x, lambda s: True, dagger)
+        assert np.allclose(got, whole[x[3], x[2], x[1], x[0]], atol=1e-12), x

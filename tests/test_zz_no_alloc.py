@@ -1,9 +1,9 @@
 """dwf_mpc_noalloc: the Schur operator for callers that may not allocate
 device memory when they apply it (a framework pool that owns all device
-memory, a CUDA-graph capture in progress, a fixed-footprint embedding).  Its
-temporaries live in the library's static device array, so it must give the
-same result as dwf_mpc, call after call, and refuse problems that do not fit.
-This file is collected last on purpose."""
+memory, a fixed-footprint embedding).  Its temporaries live in the library's
+static device array, so it must give the same result as dwf_mpc, call after
+call, allocate nothing, and refuse problems that do not fit.  This file is
+collected last on purpose."""
 
 import numpy as np
 import pytest
@@ -54,3 +54,25 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(G.DWFError) as e:
         h.mpc_noalloc(y, x, prec=G.FP64)
     assert e.value.status == 1 and "static scratch" in str(e.value)
+
+
+def test_noalloc_allocates_nothing():
+    """On a fresh handle, right after dwf_autotune, calls of dwf_mpc_noalloc
+    make no device allocation: the library's allocation count and the free
+    device memory stay where they were."""
+    dims, Ls, nrhs = (8, 8, 8, 8), 8, 1
+    U = inputs.gauge_field(dims, "exp", eps=0.3, seed=78)
+    h = G.Handle(dims, Ls, G.Action(1.8, 0.01, 1.5, 0.5), nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.autotune(nrhs, G.FP32)
+    x = torch.randn(h.cb_shape(1, nrhs), device="cuda")
+    y = h.empty_cb(1, nrhs, G.FP32)
+    h.mpc_noalloc(y, x, False, G.FP32, nrhs)    # first call on the device: symbol look-up
+    torch.cuda.synchronize()
+    n0 = G.alloc_count()
+    free0 = torch.cuda.mem_get_info()[0]
+    for dagger in (False, True, False):
+        h.mpc_noalloc(y, x, dagger, G.FP32, nrhs)
+    torch.cuda.synchronize()
+    assert G.alloc_count() == n0
+    assert torch.cuda.mem_get_info()[0] == free0
