@@ -175,7 +175,7 @@ dwf_status persistent_grid(const void* kern, int threads, size_t smem, int ntile
 
 // ------------------------------------------------------ launchers
 // hop kinds
-enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1 };
+enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1, EPI_POST = 2 };
 // site-local operator kinds
 enum LocalOp { L_B = 0, L_MOOEE = 1, L_MINV = 2, L_BMINV = 3, L_POST = 4, L_COPY = 5, L_PB = 6 };
 
@@ -194,8 +194,22 @@ struct HopCall {
     int VL = 0;              // lanes per thread (FP32 links: 1 or 2; 0 = default)
     int tc = 0;              // BF16 links: 1 = tensor-core kernel (hop_tc.cu)
     int chunk = 0;           // consecutive tiles per CTA before striding (0 = 1)
+    // EPI_POST (dagger only): the tail of M_pc^+ fused into the hop,
+    //   Ap = M_oo^+ xmoo + scale (b5 + c5 S5^+) Dh^+ in,
+    // with the CG update x += alpha p, r -= alpha Ap and per-tile |r|^2
+    // (FP32 vectors); Ap itself is not stored.  Needs site groups that do
+    // not straddle warps: hop_post_ok().
+    bool post = false;
+    void* cg_x = nullptr;
+    void* cg_r = nullptr;
+    const void* cg_p = nullptr;
+    const double* alpha = nullptr;
+    const int* run = nullptr;
 };
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
+// The fused M_pc^+ tail is available: FP32 or BF16 operator, FP32 vectors,
+// and N5 / (lanes per thread) dividing 32.
+bool hop_post_ok(const dwf_handle* h, dwf_prec op, dwf_prec vec, int nrhs, int VL);
 dwf_status launch_hop_tc(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s);
 dwf_status init_hop_tc_kernels();
 dwf_status init_hop_kernels();

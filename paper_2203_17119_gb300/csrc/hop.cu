@@ -37,9 +37,25 @@ struct HopArgs {
     int T, N5, Ls, nrhs, ntiles;
     int chunk;           // consecutive tiles a CTA takes before striding: neighbouring rows of
                          // the lattice on one SM, so y-neighbours are re-read from L1
-    double scale, d, e, mf;
+    double scale, d, e, mf, b5, c5;
     double* partial;
     int* err;
+    // EPI_POST: CG vectors (FP32) and per-system scalars
+    void* cg_x;
+    void* cg_r;
+    const void* cg_p;
+    const double* alpha;
+    const int* run;
+};
+
+// Lanes next to the first and last lane of this thread within its site
+// group, for S5 across threads: the thread holding the lane above the last
+// one (as its first lane) and the one holding the lane below the first one
+// (as its last lane), with the wall factor -mf where the shift wraps.
+struct LaneNbrs {
+    int src_up, src_dn;
+    unsigned mask;     // the site group's threads in the warp
+    float f_up, f_dn;
 };
 
 // One direction K (0..3: +mu, 4..7: -mu) for the VL lanes of one site; src
@@ -277,8 +293,97 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
 // per site, one FP64 add per site, off GB300's slow FP64 pipe).
 template <class Sout, class R, int VL, bool DAG, int EPI>
 __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t site, int lane0,
-                                            const R (&ar)[12][VL], const R (&ai)[12][VL]) {
+                                            const R (&ar)[12][VL], const R (&ai)[12][VL],
+                                            const LaneNbrs& nb, int box) {
     const R sc = (R)a.scale;
+    if constexpr (EPI == EPI_POST) {
+        static_assert(DAG, "the fused M_pc^+ tail follows the adjoint hop");
+        // B^+ acc = b5 acc + c5 S5^+ acc on this site's lanes: S5^+ takes
+        // lane s + 1 for the upper spins and s - 1 for the lower ones (walls
+        // -mf); the lanes beyond this thread's come from its neighbours in
+        // the site group
+        const R b5 = (R)a.b5, c5 = (R)a.c5;
+        R br[12][VL], bi[12][VL];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            if (c < 6) {
+                const R nr = __shfl_sync(nb.mask, ar[c][0], nb.src_up) * (R)nb.f_up;
+                const R ni = __shfl_sync(nb.mask, ai[c][0], nb.src_up) * (R)nb.f_up;
+#pragma unroll
+                for (int v = 0; v < VL; ++v) {
+                    const R sr = v < VL - 1 ? ar[c][(v + 1) % VL] : nr;
+                    const R si = v < VL - 1 ? ai[c][(v + 1) % VL] : ni;
+                    br[c][v] = b5 * ar[c][v] + c5 * sr;
+                    bi[c][v] = b5 * ai[c][v] + c5 * si;
+                }
+            } else {
+                const R nr = __shfl_sync(nb.mask, ar[c][VL - 1], nb.src_dn) * (R)nb.f_dn;
+                const R ni = __shfl_sync(nb.mask, ai[c][VL - 1], nb.src_dn) * (R)nb.f_dn;
+#pragma unroll
+                for (int v = 0; v < VL; ++v) {
+                    const R sr = v > 0 ? ar[c][(v + VL - 1) % VL] : nr;
+                    const R si = v > 0 ? ai[c][(v + VL - 1) % VL] : ni;
+                    br[c][v] = b5 * ar[c][v] + c5 * sr;
+                    bi[c][v] = b5 * ai[c][v] + c5 * si;
+                }
+            }
+        }
+        // Ap = M_oo^+ t + scale B^+ acc (t = xmoo; M_oo^+ = d + e S5^+ from
+        // memory), then x += alpha p, r -= alpha Ap and |r|^2
+        const int Ls = a.Ls;
+        const int s0 = lane0 % Ls;
+        const int rbase = lane0 - s0;
+        const int sys = box * a.nrhs + lane0 / Ls;
+        const R alpha = (R)a.alpha[sys];
+        const bool live = a.run == nullptr || a.run[sys] != 0;
+        const bool hi_wrap = (s0 + VL == Ls), lo_wrap = (s0 == 0);
+        const int l_above = hi_wrap ? rbase : lane0 + VL;
+        const int l_below = lo_wrap ? rbase + Ls - 1 : lane0 - 1;
+        const R mf = (R)a.mf, d = (R)a.d, e = (R)a.e;
+        const Sout* tb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
+        float* xb = reinterpret_cast<float*>(a.cg_x) + (site * 12 * N5 + lane0) * 2;
+        float* rb = reinterpret_cast<float*>(a.cg_r) + (site * 12 * N5 + lane0) * 2;
+        const float* pb = reinterpret_cast<const float*>(a.cg_p) + (site * 12 * N5 + lane0) * 2;
+        float nrm = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            R tr[VL], ti[VL];
+            load_lanes<Sout, VL, R>(tb + (int64_t)(c * N5 + lane0) * 2, tr, ti);
+            const bool up = c < 6;   // S5^+: upper spins read s + 1
+            R nr, ni;
+            load_c1<Sout, R>(tb + (int64_t)(c * N5 + (up ? l_above : l_below)) * 2, nr, ni);
+            const R fn = up ? (hi_wrap ? -mf : (R)1) : (lo_wrap ? -mf : (R)1);
+            float rr[VL], ri[VL];
+            load_lanes<float, VL, float>(rb + (int64_t)c * N5 * 2, rr, ri);
+            if (live) {
+                float xr[VL], xi[VL], pr[VL], pi[VL];
+                load_lanes<float, VL, float>(xb + (int64_t)c * N5 * 2, xr, xi);
+                load_lanes<float, VL, float>(pb + (int64_t)c * N5 * 2, pr, pi);
+#pragma unroll
+                for (int v = 0; v < VL; ++v) {
+                    R sr, si;
+                    if (up) {
+                        sr = v == VL - 1 ? fn * nr : tr[(v + 1) % VL];
+                        si = v == VL - 1 ? fn * ni : ti[(v + 1) % VL];
+                    } else {
+                        sr = v == 0 ? fn * nr : tr[(v + VL - 1) % VL];
+                        si = v == 0 ? fn * ni : ti[(v + VL - 1) % VL];
+                    }
+                    const R apr = d * tr[v] + e * sr + sc * br[c][v];
+                    const R api = d * ti[v] + e * si + sc * bi[c][v];
+                    xr[v] = fmaf((float)alpha, pr[v], xr[v]);
+                    xi[v] = fmaf((float)alpha, pi[v], xi[v]);
+                    rr[v] = fmaf(-(float)alpha, (float)apr, rr[v]);
+                    ri[v] = fmaf(-(float)alpha, (float)api, ri[v]);
+                }
+                store_lanes<float, VL, float>(xb + (int64_t)c * N5 * 2, xr, xi);
+                store_lanes<float, VL, float>(rb + (int64_t)c * N5 * 2, rr, ri);
+            }
+#pragma unroll
+            for (int v = 0; v < VL; ++v) nrm = fmaf(rr[v], rr[v], fmaf(ri[v], ri[v], nrm));
+        }
+        return (double)nrm;
+    }
     Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
     if (EPI == EPI_PLAIN) {
 #pragma unroll
@@ -392,7 +497,23 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const int sg = threadIdx.x / TPS;
     const int lane0 = (threadIdx.x - sg * TPS) * VL;
     const int rhs = lane0 / a.Ls;   // of this thread's lanes (threads without sites add 0)
-    const bool part = EPI == EPI_MOO && a.partial != nullptr;
+    const bool part = (EPI == EPI_MOO || EPI == EPI_POST) && a.partial != nullptr;
+    LaneNbrs nbrs{};
+    if constexpr (EPI == EPI_POST) {
+        // site groups are warp-aligned here (TPS divides 32, checked on the host)
+        const int wl = threadIdx.x & 31;
+        const int tig = lane0 / VL;
+        const int gb = wl - tig;
+        const int s_first = lane0 % a.Ls, s_last = (lane0 + VL - 1) % a.Ls;
+        const int rb = lane0 - s_first;
+        const int above = s_last == a.Ls - 1 ? rb : lane0 + VL;
+        const int below = s_first == 0 ? rb + a.Ls - 1 : lane0 - 1;
+        nbrs.src_up = gb + above / VL;
+        nbrs.src_dn = gb + below / VL;
+        nbrs.f_up = s_last == a.Ls - 1 ? -(float)a.mf : 1.f;
+        nbrs.f_dn = s_first == 0 ? -(float)a.mf : 1.f;
+        nbrs.mask = TPS >= 32 ? 0xffffffffu : (((1u << TPS) - 1u) << gb);
+    }
 
     int k = 0;
     for (int tile = tile_of(0); tile < nt; tile = tile_of(++k)) {
@@ -412,7 +533,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         const int* s_nbr_t = reinterpret_cast<const int*>(smem + b * buf_bytes + link_bytes);
         double tile_norm = 0.0;
         for (int sl = sg; sg < G && sl < count; sl += G) {
-            if (EPI == EPI_MOO) {
+            if (EPI == EPI_MOO || EPI == EPI_POST) {
                 // the M_oo input of this site's lanes, into L1 while the eight
                 // directions run: the epilogue's loads then hit L1 instead of
                 // paying twelve dependent trips to L2 / HBM
@@ -458,7 +579,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                 hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
             }
-            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai);
+            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai, nbrs, tl.x);
         }
         double* red = s_red + (size_t)b * nwarps * a.nrhs;
         if (part) {
@@ -510,6 +631,13 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     a.partial = c.partial;
     a.err = h->d_err;
     a.chunk = c.chunk > 0 ? c.chunk : 1;
+    a.b5 = h->p.b5;
+    a.c5 = h->p.c5;
+    a.cg_x = c.cg_x;
+    a.cg_r = c.cg_r;
+    a.cg_p = c.cg_p;
+    a.alpha = c.alpha;
+    a.run = c.run;
     const int TPS = a.N5 / VL;
     // site groups per CTA: as many as fit in 256 threads, at most T
     int groups = 256 / TPS;
@@ -525,7 +653,20 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     a.ntiles = nt;
     void (*kern)(const HopArgs);
     const bool moo = c.xmoo != nullptr;
-    if (c.dagger)
+    if (c.post) {
+        if constexpr (std::is_same<R, float>::value && std::is_same<Sout, float>::value) {
+            if (!c.dagger || !moo || 32 % TPS != 0 || c.cg_x == nullptr || c.cg_r == nullptr ||
+                c.cg_p == nullptr || c.alpha == nullptr) {
+                set_error("hop: fused M_pc^+ tail needs the adjoint, t, the CG vectors and "
+                          "site groups that divide a warp");
+                return DWF_ERR_ARG;
+            }
+            kern = k_hop<Sin, Sout, SL, R, VL, true, EPI_POST, CN5>;
+        } else {
+            set_error("hop: fused M_pc^+ tail needs FP32 arithmetic and FP32 vectors");
+            return DWF_ERR_UNSUPPORTED;
+        }
+    } else if (c.dagger)
         kern = moo ? k_hop<Sin, Sout, SL, R, VL, true, EPI_MOO, CN5>
                    : k_hop<Sin, Sout, SL, R, VL, true, EPI_PLAIN, CN5>;
     else
@@ -579,6 +720,11 @@ static cudaError_t hop_attr() {
         cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
         if (r != cudaSuccess) e = r;
     }
+    if constexpr (std::is_same<R, float>::value && std::is_same<Sout, float>::value) {
+        cudaError_t r = cudaFuncSetAttribute(k_hop<Sin, Sout, SL, R, VL, true, EPI_POST, CN5>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
+        if (r != cudaSuccess) e = r;
+    }
     return e;
 }
 
@@ -597,6 +743,14 @@ dwf_status init_hop_kernels() {
     DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2, 12>()));
     DWF_CUDA((hop_attr<bf16, bf16, bf16, float, 2, 16>()));
     return DWF_OK;
+}
+
+bool hop_post_ok(const dwf_handle* h, dwf_prec op, dwf_prec vec, int nrhs, int VL) {
+    if (vec != DWF_FP32 || (op != DWF_FP32 && op != DWF_BF16)) return false;
+    const int n5 = h->p.Ls * nrhs;
+    const int vl = op == DWF_BF16 ? 2 : (VL == 1 ? 1 : 2);
+    const int tps = n5 / vl;
+    return n5 % vl == 0 && tps <= 32 && 32 % tps == 0;
 }
 
 dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s) {

@@ -145,9 +145,28 @@ size_t cb_elems(const dwf_handle* h, int parity, int nrhs) {
 
 static bool shamir(const dwf_handle* h) { return h->p.c5 == 0.0; }
 
+// Lanes per thread of the FP32-arithmetic hop with nrhs right-hand sides.
+static int hop_vl(dwf_handle* h, dwf_prec link, int nrhs) {
+    if (link != DWF_FP32) return 2;
+    auto it = h->tuned_vl.find(nrhs);
+    return it == h->tuned_vl.end() ? 2 : it->second;
+}
+
+static HopCall hop_call(dwf_handle* h, const void* in, void* out, int out_parity, int dagger,
+                        dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
+                        const void* xmoo, double* partial);
+
 dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
                   dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
                   const void* xmoo, double* partial, cudaStream_t s) {
+    return launch_hop(h, hop_call(h, in, out, out_parity, dagger, link, pin, pout, nrhs, scale, xmoo,
+                                  partial), s);
+}
+
+// The hop launch of an operator chain: tuned tile, lanes, kernel and tile order.
+static HopCall hop_call(dwf_handle* h, const void* in, void* out, int out_parity, int dagger,
+                        dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
+                        const void* xmoo, double* partial) {
     HopCall c;
     c.in = in;
     c.out = out;
@@ -173,7 +192,7 @@ dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int 
         auto it = h->tuned_chunk.find(nrhs);
         c.chunk = it == h->tuned_chunk.end() ? 1 : it->second;
     }
-    return launch_hop(h, c, s);
+    return c;
 }
 
 dwf_status op_local(dwf_handle* h, LocalOp op, void* out, const void* in, const void* in2,
@@ -234,6 +253,17 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
     }
     DWF_TRY(op_hop(h, tmpB, in, 0, 1, po, pv, po, nrhs, 1.0, nullptr, nullptr, s));
     DWF_TRY(op_local(h, L_BMINV, tmpA, tmpB, nullptr, 0, 1, po, po, po, nrhs, 1.0, nullptr, s));
+    HopCall hc = hop_call(h, tmpA, nullptr, 1, 1, po, po, pv, nrhs, -0.25, in, partial);
+    if (cg != nullptr && hc.tc == 0 && hop_post_ok(h, po, pv, nrhs, hop_vl(h, po, nrhs))) {
+        // the tail M_oo^+ in - (1/4) B^+ (.) and the CG update in the last hop's epilogue
+        hc.post = true;
+        hc.cg_x = cg->x;
+        hc.cg_r = cg->r;
+        hc.cg_p = cg->p;
+        hc.alpha = cg->alpha;
+        hc.run = cg->run;
+        return launch_hop(h, hc, s);
+    }
     DWF_TRY(op_hop(h, tmpB, tmpA, 1, 1, po, po, po, nrhs, 1.0, nullptr, nullptr, s));
     LocalCall c{};
     c.op = L_POST;
