@@ -494,6 +494,16 @@ dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, i
  * step.  Whole-lattice handles only. */
 dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const float* e, int nrhs,
                              int loss_kind, double lr, double* loss, void* stream);
+/* One training pair of K from an FP64 solve of D x = b (nrhs = 1): with the
+ * solution x* and a recorded iterate x_k (odd cb FP64 fields),
+ *   e = (x* - x_k) / |x* - x_k|,   r = M_pc^+ M_pc e   (FP64 operator),
+ * written as odd cb FP32 fields (r, e); *norm (host) receives |x* - x_k|,
+ * and when it is 0 nothing is written.  The pair satisfies the normal
+ * equations M_pc^+ M_pc e = r that flexible GCR is preconditioned for.
+ * Whole-lattice handles; uses the handle's scratch fields, allocates three
+ * odd cb FP64 fields for the call and synchronises the stream. */
+dwf_status dwf_nn_make_pair(dwf_handle* h, const double* x_star, const double* x_k, float* r, float* e,
+                            double* norm, void* stream);
 /* Gradient of the last train step on handle h, layout of the weights. */
 dwf_status dwf_nn_last_grad(dwf_handle* h, double* g, size_t n_complex);
 

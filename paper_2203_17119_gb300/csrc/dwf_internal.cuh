@@ -175,7 +175,7 @@ dwf_status persistent_grid(const void* kern, int threads, size_t smem, int ntile
 
 // ------------------------------------------------------ launchers
 // hop kinds
-enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1, EPI_POST = 2 };
+enum HopEpi { EPI_PLAIN = 0, EPI_MOO = 1, EPI_POST = 2, EPI_BMINV = 3 };
 // site-local operator kinds
 enum LocalOp { L_B = 0, L_MOOEE = 1, L_MINV = 2, L_BMINV = 3, L_POST = 4, L_COPY = 5, L_PB = 6 };
 
@@ -200,6 +200,10 @@ struct HopCall {
     // (FP32 vectors); Ap itself is not stored.  Needs site groups that do
     // not straddle warps: hop_post_ok().
     bool post = false;
+    // EPI_BMINV: out = scale (b5 + c5 S5)(d + e S5)^-1 Dh in (adjoint: with
+    // S5^+), the site-local factor between the two hops of M_pc applied in the
+    // epilogue by scans across the site's lanes; same condition as EPI_POST
+    bool bminv = false;
     void* cg_x = nullptr;
     void* cg_r = nullptr;
     const void* cg_p = nullptr;
@@ -210,6 +214,9 @@ dwf_status launch_hop(dwf_handle* h, const HopCall& c, cudaStream_t s);
 // The fused M_pc^+ tail is available: FP32 or BF16 operator, FP32 vectors,
 // and N5 / (lanes per thread) dividing 32.
 bool hop_post_ok(const dwf_handle* h, dwf_prec op, dwf_prec vec, int nrhs, int VL);
+// The fused site-local factor between the hops of M_pc is available: FP32
+// arithmetic (FP32 or BF16 operator) and N5 / (lanes per thread) dividing 32.
+bool hop_bminv_ok(const dwf_handle* h, dwf_prec op, int nrhs, int VL);
 dwf_status launch_hop_tc(dwf_handle* h, const HopCall& c, const TileSet& ts, cudaStream_t s);
 dwf_status init_hop_tc_kernels();
 dwf_status init_hop_kernels();

@@ -38,6 +38,7 @@ struct HopArgs {
     int chunk;           // consecutive tiles a CTA takes before striding: neighbouring rows of
                          // the lattice on one SM, so y-neighbours are re-read from L1
     double scale, d, e, mf, b5, c5;
+    double fa, inv_d, inv_den;   // EPI_BMINV: a = -e/d, 1/d, 1/(d (1 + mf a^Ls))
     double* partial;
     int* err;
     // EPI_POST: CG vectors (FP32) and per-system scalars
@@ -47,6 +48,76 @@ struct HopArgs {
     const double* alpha;
     const int* run;
 };
+
+// Scans across the lanes of one right-hand side (Ls lanes held by Ls / VL
+// consecutive threads of a warp) for the fifth-dimension factor between the
+// hops of M_pc, B M^-1 = (b5 + c5 S)(d + e S)^-1 per chirality, S the
+// twisted shift S_- (reads lane s - 1, wall -mf) or S_+ (s + 1).  With
+// a = -e/d, S_-^Ls = -mf and (1 - a S)^-1 = sum_{k<Ls} (a S)^k / (1 + mf a^Ls):
+//   (d + e S_-)^-1 x |_s = P_s / d - mf a^(s+1) P_(Ls-1) / (d (1 + mf a^Ls)),
+//   P_s = sum_{t<=s} a^(s-t) x_t,
+// a decayed prefix sum (in-thread, then across threads by shuffles); S_+ is
+// the mirror image with suffix sums Q_s = sum_{t>=s} a^(t-s) x_t and
+// a^(Ls-s) Q_0.
+template <int VL>
+struct ScanCtx {
+    unsigned mask;          // the site group's threads
+    int j, nthr, seg0;      // thread index in the rhs segment, threads per segment, its first lane
+    float a, inv_d, wc;     // a, 1/d, mf / (d (1 + mf a^Ls))
+    float mf, b5, c5;
+    float astep[5];         // a^(VL o) for scan strides o = 1, 2, 4, 8, 16
+    float pdn[VL], pup[VL]; // a^(s+1), a^(Ls-s) per lane
+    float cdn[VL], cup[VL]; // carry factors a^(v+1), a^(VL-v)
+};
+
+template <int VL, bool DN>
+__device__ __forceinline__ void scan_bminv(const ScanCtx<VL>& k, float (&x)[VL]) {
+    float p[VL];
+    if (DN) {
+        p[0] = x[0];
+#pragma unroll
+        for (int v = 1; v < VL; ++v) p[v] = fmaf(k.a, p[v - 1], x[v]);
+    } else {
+        p[VL - 1] = x[VL - 1];
+#pragma unroll
+        for (int v = VL - 2; v >= 0; --v) p[v] = fmaf(k.a, p[v + 1], x[v]);
+    }
+    // inclusive scan of the thread totals over the segment (Hillis-Steele)
+    const int me = k.seg0 + k.j;
+    float tot = DN ? p[VL - 1] : p[0];
+    int lvl = 0;
+    for (int o = 1; o < k.nthr; o <<= 1, ++lvl) {
+        const bool has = DN ? k.j >= o : k.j + o < k.nthr;
+        const float v = __shfl_sync(k.mask, tot, has ? (DN ? me - o : me + o) : me);
+        if (has) tot = fmaf(k.astep[lvl], v, tot);
+    }
+    // carry in from the neighbouring thread's inclusive total
+    const bool hc = DN ? k.j > 0 : k.j + 1 < k.nthr;
+    const float carry = __shfl_sync(k.mask, tot, hc ? (DN ? me - 1 : me + 1) : me);
+    if (hc) {
+#pragma unroll
+        for (int v = 0; v < VL; ++v) p[v] = fmaf(DN ? k.cdn[v] : k.cup[v], carry, p[v]);
+    }
+    // the wall term: P at the segment's last lane (Q at its first)
+    const float T = __shfl_sync(k.mask, DN ? p[VL - 1] : p[0], DN ? k.seg0 + k.nthr - 1 : k.seg0);
+    float y[VL];
+#pragma unroll
+    for (int v = 0; v < VL; ++v) y[v] = fmaf(-k.wc * (DN ? k.pdn[v] : k.pup[v]), T, p[v] * k.inv_d);
+    // (b5 + c5 S) y
+    float nb;
+    if (DN) {
+        const bool in = k.j > 0;
+        nb = __shfl_sync(k.mask, y[VL - 1], in ? me - 1 : k.seg0 + k.nthr - 1) * (in ? 1.f : -k.mf);
+    } else {
+        const bool in = k.j + 1 < k.nthr;
+        nb = __shfl_sync(k.mask, y[0], in ? me + 1 : k.seg0) * (in ? 1.f : -k.mf);
+    }
+#pragma unroll
+    for (int v = 0; v < VL; ++v) {
+        const float sv = DN ? (v > 0 ? y[(v + VL - 1) % VL] : nb) : (v < VL - 1 ? y[(v + 1) % VL] : nb);
+        x[v] = fmaf(k.c5, sv, k.b5 * y[v]);
+    }
+}
 
 // Lanes next to the first and last lane of this thread within its site
 // group, for S5 across threads: the thread holding the lane above the last
@@ -294,8 +365,29 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
 template <class Sout, class R, int VL, bool DAG, int EPI>
 __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t site, int lane0,
                                             const R (&ar)[12][VL], const R (&ai)[12][VL],
-                                            const LaneNbrs& nb, int box) {
+                                            const LaneNbrs& nb, int box, const ScanCtx<VL>& sk) {
     const R sc = (R)a.scale;
+    if constexpr (EPI == EPI_BMINV) {
+        // out = scale B M^-1 acc: non-adjoint upper spins see S_-, lower S_+
+        Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float xr[VL], xi[VL];
+#pragma unroll
+            for (int v = 0; v < VL; ++v) { xr[v] = (float)ar[c][v]; xi[v] = (float)ai[c][v]; }
+            if ((c < 6) != DAG) {
+                scan_bminv<VL, true>(sk, xr);
+                scan_bminv<VL, true>(sk, xi);
+            } else {
+                scan_bminv<VL, false>(sk, xr);
+                scan_bminv<VL, false>(sk, xi);
+            }
+#pragma unroll
+            for (int v = 0; v < VL; ++v) { xr[v] *= (float)sc; xi[v] *= (float)sc; }
+            store_lanes<Sout, VL, float, true>(out + (int64_t)c * N5 * 2, xr, xi);
+        }
+        return 0.0;
+    }
     if constexpr (EPI == EPI_POST) {
         static_assert(DAG, "the fused M_pc^+ tail follows the adjoint hop");
         // B^+ acc = b5 acc + c5 S5^+ acc on this site's lanes: S5^+ takes
@@ -340,10 +432,12 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t si
         const int l_above = hi_wrap ? rbase : lane0 + VL;
         const int l_below = lo_wrap ? rbase + Ls - 1 : lane0 - 1;
         const R mf = (R)a.mf, d = (R)a.d, e = (R)a.e;
-        const Sout* tb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
-        float* xb = reinterpret_cast<float*>(a.cg_x) + (site * 12 * N5 + lane0) * 2;
-        float* rb = reinterpret_cast<float*>(a.cg_r) + (site * 12 * N5 + lane0) * 2;
-        const float* pb = reinterpret_cast<const float*>(a.cg_p) + (site * 12 * N5 + lane0) * 2;
+        // distinct fields: no aliasing, so the loads of later components can
+        // be issued ahead of the stores of earlier ones
+        const Sout* __restrict__ tb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
+        float* __restrict__ xb = reinterpret_cast<float*>(a.cg_x) + (site * 12 * N5 + lane0) * 2;
+        float* __restrict__ rb = reinterpret_cast<float*>(a.cg_r) + (site * 12 * N5 + lane0) * 2;
+        const float* __restrict__ pb = reinterpret_cast<const float*>(a.cg_p) + (site * 12 * N5 + lane0) * 2;
         float nrm = 0.f;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
@@ -384,7 +478,7 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t si
         }
         return (double)nrm;
     }
-    Sout* out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
+    Sout* __restrict__ out = reinterpret_cast<Sout*>(a.out) + (site * 12 * N5 + lane0) * 2;
     if (EPI == EPI_PLAIN) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
@@ -400,7 +494,7 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t si
     }
     // M_oo x = d x + e S5 x on this site's lanes; S5 (non-dagger):
     // upper spins x_{s-1}, lower spins x_{s+1}, walls -mf.
-    const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
+    const Sout* __restrict__ xb = reinterpret_cast<const Sout*>(a.xmoo) + (site * 12 * N5) * 2;
     const int Ls = a.Ls;
     const int s0 = lane0 % Ls;
     const int rbase = lane0 - s0;
@@ -498,6 +592,38 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
     const int lane0 = (threadIdx.x - sg * TPS) * VL;
     const int rhs = lane0 / a.Ls;   // of this thread's lanes (threads without sites add 0)
     const bool part = (EPI == EPI_MOO || EPI == EPI_POST) && a.partial != nullptr;
+    ScanCtx<VL> sk{};
+    if constexpr (EPI == EPI_BMINV) {
+        const int wl = threadIdx.x & 31;
+        const int Ls = a.Ls;
+        const int tig = lane0 / VL;
+        const int gb = wl - tig;
+        sk.mask = TPS >= 32 ? 0xffffffffu : (((1u << TPS) - 1u) << gb);
+        sk.nthr = Ls / VL;
+        sk.j = (lane0 % Ls) / VL;
+        sk.seg0 = wl - sk.j;
+        sk.a = (float)a.fa;
+        sk.inv_d = (float)a.inv_d;
+        sk.wc = (float)(a.mf * a.inv_den);
+        sk.mf = (float)a.mf;
+        sk.b5 = (float)a.b5;
+        sk.c5 = (float)a.c5;
+        float av = 1.f;
+#pragma unroll
+        for (int v = 0; v < VL; ++v) av *= sk.a;
+#pragma unroll
+        for (int l = 0; l < 5; ++l) { sk.astep[l] = av; av *= av; }
+        const int s0 = lane0 % Ls;
+#pragma unroll
+        for (int v = 0; v < VL; ++v) {
+            float pd = 1.f, pu = 1.f, cd = 1.f, cu = 1.f;
+            for (int q = 0; q < s0 + v + 1; ++q) pd *= sk.a;
+            for (int q = 0; q < Ls - s0 - v; ++q) pu *= sk.a;
+            for (int q = 0; q < v + 1; ++q) cd *= sk.a;
+            for (int q = 0; q < VL - v; ++q) cu *= sk.a;
+            sk.pdn[v] = pd; sk.pup[v] = pu; sk.cdn[v] = cd; sk.cup[v] = cu;
+        }
+    }
     LaneNbrs nbrs{};
     if constexpr (EPI == EPI_POST) {
         // site groups are warp-aligned here (TPS divides 32, checked on the host)
@@ -579,7 +705,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                 hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
             }
-            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai, nbrs, tl.x);
+            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai, nbrs, tl.x, sk);
         }
         double* red = s_red + (size_t)b * nwarps * a.nrhs;
         if (part) {
@@ -633,6 +759,9 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
     a.chunk = c.chunk > 0 ? c.chunk : 1;
     a.b5 = h->p.b5;
     a.c5 = h->p.c5;
+    a.fa = h->f5[0].a;
+    a.inv_d = h->f5[0].inv_d;
+    a.inv_den = h->f5[0].inv_den;
     a.cg_x = c.cg_x;
     a.cg_r = c.cg_r;
     a.cg_p = c.cg_p;
@@ -664,6 +793,18 @@ static dwf_status launch_t(dwf_handle* h, const HopCall& c, const TileSet& ts, c
             kern = k_hop<Sin, Sout, SL, R, VL, true, EPI_POST, CN5>;
         } else {
             set_error("hop: fused M_pc^+ tail needs FP32 arithmetic and FP32 vectors");
+            return DWF_ERR_UNSUPPORTED;
+        }
+    } else if (c.bminv) {
+        if constexpr (std::is_same<R, float>::value) {
+            if (moo || 32 % TPS != 0) {
+                set_error("hop: fused B M_ee^-1 needs site groups that divide a warp");
+                return DWF_ERR_ARG;
+            }
+            kern = c.dagger ? k_hop<Sin, Sout, SL, R, VL, true, EPI_BMINV, CN5>
+                            : k_hop<Sin, Sout, SL, R, VL, false, EPI_BMINV, CN5>;
+        } else {
+            set_error("hop: fused B M_ee^-1 needs FP32 arithmetic");
             return DWF_ERR_UNSUPPORTED;
         }
     } else if (c.dagger)
@@ -725,6 +866,14 @@ static cudaError_t hop_attr() {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
         if (r != cudaSuccess) e = r;
     }
+    if constexpr (std::is_same<R, float>::value) {
+        cudaError_t r = cudaFuncSetAttribute(k_hop<Sin, Sout, SL, R, VL, false, EPI_BMINV, CN5>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
+        if (r != cudaSuccess) e = r;
+        r = cudaFuncSetAttribute(k_hop<Sin, Sout, SL, R, VL, true, EPI_BMINV, CN5>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kHopMaxSmem);
+        if (r != cudaSuccess) e = r;
+    }
     return e;
 }
 
@@ -747,6 +896,14 @@ dwf_status init_hop_kernels() {
 
 bool hop_post_ok(const dwf_handle* h, dwf_prec op, dwf_prec vec, int nrhs, int VL) {
     if (vec != DWF_FP32 || (op != DWF_FP32 && op != DWF_BF16)) return false;
+    const int n5 = h->p.Ls * nrhs;
+    const int vl = op == DWF_BF16 ? 2 : (VL == 1 ? 1 : 2);
+    const int tps = n5 / vl;
+    return n5 % vl == 0 && tps <= 32 && 32 % tps == 0;
+}
+
+bool hop_bminv_ok(const dwf_handle* h, dwf_prec op, int nrhs, int VL) {
+    if (op != DWF_FP32 && op != DWF_BF16) return false;
     const int n5 = h->p.Ls * nrhs;
     const int vl = op == DWF_BF16 ? 2 : (VL == 1 ? 1 : 2);
     const int tps = n5 / vl;

@@ -603,6 +603,54 @@ dwf_status dwf_nn_get_weights(const dwf_nn* K, double* w, size_t n) {
     return DWF_OK;
 }
 
+// One training pair from an FP64 solve: e = (x* - x_k) / |x* - x_k|,
+// r = M_pc^+ M_pc e (FP64 operator), both written in FP32.
+dwf_status dwf_nn_make_pair(dwf_handle* h, const double* x_star, const double* x_k, float* r,
+                            float* e, double* norm, void* stream) {
+    DWF_TRY(check_handle(h));
+    if (!x_star || !x_k || !r || !e || !norm || !h->have_gauge || h->dirichlet) {
+        set_error("dwf_nn_make_pair: bad argument (whole-lattice handle with a gauge field, "
+                  "non-null fields)");
+        return DWF_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t no = cb_elems(h, 1, 1);
+    const int T = tile_for(h, 1);
+    const TileSet* tsp = nullptr;
+    DWF_TRY(get_tiles(h, T, &tsp));
+    double* buf = nullptr;
+    const size_t nd = (size_t)tsp->ntiles[1] + 1;
+    DWF_CUDA(dev_malloc(&buf, (3 * no * 2 + nd) * sizeof(double)));
+    double* e64 = buf;
+    double* t64 = buf + 2 * no;
+    double* r64 = buf + 4 * no;
+    double* part = buf + 6 * no;
+    double* d_n2 = part + tsp->ntiles[1];
+    double n2 = 0.0;
+    dwf_status st = DWF_OK;
+    auto run = [&]() -> dwf_status {
+        DWF_CUDA(cudaMemcpyAsync(e64, x_star, no * 16, cudaMemcpyDeviceToDevice, s));
+        DWF_TRY(launch_axpby(h, 1, 1, nullptr, -1.0, x_k, DWF_FP64, nullptr, 1.0, e64, DWF_FP64, nullptr, T, s));
+        DWF_TRY(launch_dot_partial(h, 1, e64, e64, DWF_FP64, DWF_FP64, 1, part, T, s));
+        DWF_TRY(launch_reduce_sys(h, 1, part, 1, d_n2, T, s));
+        DWF_CUDA(cudaMemcpyAsync(&n2, d_n2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        *norm = std::sqrt(n2);
+        if (!(n2 > 0.0)) return DWF_OK;
+        DWF_TRY(launch_axpby(h, 1, 1, nullptr, 0.0, e64, DWF_FP64, nullptr, 1.0 / *norm, e64, DWF_FP64,
+                             nullptr, T, s));
+        DWF_TRY(op_mpc(h, t64, e64, 0, DWF_FP64, DWF_FP64, 1, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
+        DWF_TRY(op_mpc(h, r64, t64, 1, DWF_FP64, DWF_FP64, 1, h->d_tmp, h->d_tmp2, nullptr, nullptr, s));
+        DWF_TRY(launch_convert(r, DWF_FP32, r64, DWF_FP64, no, s));
+        DWF_TRY(launch_convert(e, DWF_FP32, e64, DWF_FP64, no, s));
+        DWF_CUDA(cudaStreamSynchronize(s));
+        return DWF_OK;
+    };
+    st = run();
+    cudaFree(buf);
+    return st;
+}
+
 // out = K in on the odd checkerboard (FP32 cb fields, nrhs lanes)
 dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs, void* stream) {
     DWF_TRY(check_handle(h));

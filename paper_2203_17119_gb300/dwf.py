@@ -113,6 +113,7 @@ def signatures():
         "dwf_nn_apply": [vp, vp, vp, vp, i, vp],
         "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
         "dwf_nn_last_grad": [vp, vp, C.c_size_t],
+        "dwf_nn_make_pair": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
     }
 
 
@@ -456,6 +457,15 @@ class Handle:
         v = [C.c_int() for _ in range(4)]
         _check(lib().dwf_get_tuning(self._h, nrhs, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def make_pair(self, r, e, x_star, x_k, stream=None):
+        """One training pair of the learned preconditioner (dwf_nn_make_pair):
+        e = (x* - x_k)/|x* - x_k|, r = M_pc^+ M_pc e into the FP32 odd cb
+        tensors r, e; returns |x* - x_k| (0: nothing written)."""
+        n = C.c_double()
+        _check(lib().dwf_nn_make_pair(self._h, _ptr(x_star), _ptr(x_k), _ptr(r), _ptr(e), C.byref(n),
+                                      _stream(stream)))
+        return n.value
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))

@@ -40,18 +40,12 @@ def make_pairs(h, b_canon, n_iterates=64, record_every=4, tol=1e-10):
     xs = x[h.nsite[0]:].contiguous()
     r_out, e_out = [], []
     for k in range(n):
-        e = (xs - rec[k]).contiguous()
-        nrm = float(e.norm())
-        if nrm == 0.0:
+        r = torch.empty(h.cb_shape(1), dtype=torch.float32, device=b.device)
+        e = torch.empty_like(r)
+        if h.make_pair(r, e, xs, rec[k]) == 0.0:
             continue
-        e /= nrm
-        t = torch.empty_like(e)
-        r = torch.empty_like(e)
-        h.mpc(t, e, prec=G.FP64)
-        h.mpc(r, t, dagger=True, prec=G.FP64)
-        r_out.append(r.float())
-        e_out.append(e.float())
-    torch.cuda.synchronize()
+        r_out.append(r)
+        e_out.append(e)
     return torch.stack(r_out), torch.stack(e_out)
 
 
