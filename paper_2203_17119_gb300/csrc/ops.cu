@@ -228,19 +228,25 @@ dwf_status op_dslash_eo(dwf_handle* h, void* out, const void* in, int p, int dag
     return op_local(h, L_B, out, tmp, nullptr, p, 1, prec, prec, prec, nrhs, -0.5, nullptr, s);
 }
 
-// outA = (b5 + c5 S5)(d + e S5)^-1 Dh_{eo} in (adjoint chain: with S5^+ and
-// Dh^+), the first half of M_pc (M_pc^+): one hop with the site-local factor
-// in its epilogue where the site's lanes share a warp, else the hop into
-// tmpB and the separate site-local pass.
-static dwf_status hop_then_bminv(dwf_handle* h, void* outA, const void* in, int dagger, dwf_prec po,
-                                 dwf_prec pin, int nrhs, double scale, void* tmpB, cudaStream_t s) {
-    HopCall hc = hop_call(h, in, outA, 0, dagger, po, pin, po, nrhs, scale, nullptr, nullptr);
+// (b5 + c5 S5)(d + e S5)^-1 Dh_{eo} in (adjoint chain: with S5^+ and Dh^+),
+// the first half of M_pc (M_pc^+), into one of the temporaries tmpA, tmpB
+// (returned in *res; `in` may be one of them and is never overwritten while
+// it is read): one hop with the site-local factor in its epilogue where the
+// site's lanes share a warp, else the hop and the separate site-local pass.
+static dwf_status hop_then_bminv(dwf_handle* h, const void* in, int dagger, dwf_prec po,
+                                 dwf_prec pin, int nrhs, double scale, void* tmpA, void* tmpB,
+                                 void** res, cudaStream_t s) {
+    void* first = (in == tmpA) ? tmpB : tmpA;
+    void* second = (first == tmpA) ? tmpB : tmpA;
+    HopCall hc = hop_call(h, in, first, 0, dagger, po, pin, po, nrhs, scale, nullptr, nullptr);
     if (hc.tc == 0 && hop_bminv_ok(h, po, nrhs, hop_vl(h, po, nrhs))) {
         hc.bminv = true;
+        *res = first;
         return launch_hop(h, hc, s);
     }
-    DWF_TRY(op_hop(h, tmpB, in, 0, dagger, po, pin, po, nrhs, scale, nullptr, nullptr, s));
-    return op_local(h, L_BMINV, outA, tmpB, nullptr, 0, dagger, po, po, po, nrhs, 1.0, nullptr, s);
+    DWF_TRY(launch_hop(h, hc, s));
+    *res = second;
+    return op_local(h, L_BMINV, second, first, nullptr, 0, dagger, po, po, po, nrhs, 1.0, nullptr, s);
 }
 
 // Schur operator on the odd checkerboard.  pv: precision of in/out (and of
@@ -262,11 +268,14 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
             psrc = po;
             sc1 = 1.0;
         }
-        DWF_TRY(hop_then_bminv(h, tmpA, src, 0, po, psrc, nrhs, sc1, tmpB, s));
-        return op_hop(h, out, tmpA, 1, 0, po, po, pv, nrhs, -0.25, in, partial, s);
+        void* mid = nullptr;
+        DWF_TRY(hop_then_bminv(h, src, 0, po, psrc, nrhs, sc1, tmpA, tmpB, &mid, s));
+        return op_hop(h, out, mid, 1, 0, po, po, pv, nrhs, -0.25, in, partial, s);
     }
-    DWF_TRY(hop_then_bminv(h, tmpA, in, 1, po, pv, nrhs, 1.0, tmpB, s));
-    HopCall hc = hop_call(h, tmpA, nullptr, 1, 1, po, po, pv, nrhs, -0.25, in, partial);
+    void* mid = nullptr;
+    DWF_TRY(hop_then_bminv(h, in, 1, po, pv, nrhs, 1.0, tmpA, tmpB, &mid, s));
+    void* other = (mid == tmpA) ? tmpB : tmpA;
+    HopCall hc = hop_call(h, mid, nullptr, 1, 1, po, po, pv, nrhs, -0.25, in, partial);
     if (cg != nullptr && hc.tc == 0 && hop_post_ok(h, po, pv, nrhs, hop_vl(h, po, nrhs))) {
         // the tail M_oo^+ in - (1/4) B^+ (.) and the CG update in the last hop's epilogue
         hc.post = true;
@@ -277,11 +286,11 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
         hc.run = cg->run;
         return launch_hop(h, hc, s);
     }
-    DWF_TRY(op_hop(h, tmpB, tmpA, 1, 1, po, po, po, nrhs, 1.0, nullptr, nullptr, s));
+    DWF_TRY(op_hop(h, other, mid, 1, 1, po, po, po, nrhs, 1.0, nullptr, nullptr, s));
     LocalCall c{};
     c.op = L_POST;
     c.in = in;
-    c.in2 = tmpB;
+    c.in2 = other;
     c.out = out;
     c.parity = 1;
     c.dagger = 1;
@@ -308,8 +317,9 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
 dwf_status op_mpc_pre(dwf_handle* h, void* out, const void* p, const void* t1, dwf_prec pv,
                       dwf_prec po, int nrhs, void* tmpA, void* tmpB, double* partial,
                       cudaStream_t s) {
-    DWF_TRY(hop_then_bminv(h, tmpA, t1, 0, po, po, nrhs, 1.0, tmpB, s));
-    return op_hop(h, out, tmpA, 1, 0, po, po, pv, nrhs, -0.25, p, partial, s);
+    void* mid = nullptr;
+    DWF_TRY(hop_then_bminv(h, t1, 0, po, po, nrhs, 1.0, tmpA, tmpB, &mid, s));
+    return op_hop(h, out, mid, 1, 0, po, po, pv, nrhs, -0.25, p, partial, s);
 }
 
 // Full operator on full fields (both parities): D or D^+.
