@@ -112,6 +112,7 @@ typedef struct {
 
 typedef struct dwf_handle dwf_handle;
 typedef struct dwf_nn dwf_nn;
+typedef struct dwf_mg dwf_mg;
 
 /* ------------------------------------------------------------- set-up */
 
@@ -467,6 +468,60 @@ dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int or
  * FP64 inner products.  reliable_updates in stats counts restarts. */
 dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
+
+/* ------------------------------------------------ multigrid (Sec. 4)
+ * Two-level aggregation multigrid for A = M_pc^+ M_pc of a handle (each
+ * Dirichlet box on a box handle: the local systems of Sec. 4), set up from
+ * near-null vectors the caller filters with dwf_chebyshev_filter (the
+ * recursively built filter functions Sec. 4 proposes for the set-up); the
+ * paper describes no more of the method, so the rest is the standard
+ * construction: aggregates are 4D blocks (extents `block`, dividing every
+ * box's extents) of the odd sites of each box with all their Ls and
+ * spin-colour components; the prolongator P holds the vectors restricted to
+ * each block and orthonormalised there by modified Gram-Schmidt in vector
+ * order (P^+ P = 1); the coarse operator A_c = P^+ A P (Galerkin) is dense,
+ * built by nblocks applications of A with nvec lanes and inverted once on the
+ * host (at most 4096 coarse unknowns = blocks x nvec).  The preconditioner
+ * is the V(1,1) cycle z = S r; z += P A_c^-1 P^+ (r - A z); z += S (r - A z)
+ * with a smoother S: none, the Chebyshev iteration for A z = r on [lo, hi]
+ * (steps - 1 applications of A), or the learned network K.  FP32 fields and
+ * operator, FP64 coarse algebra. */
+
+/* Block tables and workspace for nvec vectors (1 <= nvec <= nrhs_max of h);
+ * the handle must outlive the preconditioner.  DWF_ERR_ARG if a block extent
+ * does not divide a box extent or the coarse space is too large. */
+dwf_status dwf_mg_create(dwf_mg** mg, dwf_handle* h, const int block[4], int nvec);
+dwf_status dwf_mg_destroy(dwf_mg* mg);
+/* Build P and A_c^-1 from V: an odd cb FP32 field with nvec lanes
+ * ([site][12][k][s], the layout of nvec right-hand sides), read during the
+ * call.  Synchronous.  DWF_ERR_ARG if the vectors are linearly dependent on a
+ * block or A_c is singular. */
+dwf_status dwf_mg_setup(dwf_mg* mg, const float* V, void* stream);
+/* Smoother of the V-cycle: kind 0 none, 1 Chebyshev iteration (steps >= 1,
+ * 0 < lo < hi bracketing the part of the spectrum to damp), 2 the network K
+ * (whole-lattice handles). */
+dwf_status dwf_mg_set_smoother(dwf_mg* mg, int kind, int steps, double lo, double hi, dwf_nn* K);
+/* z = M^-1 r (V(1,1) cycle): odd cb FP32 fields, one right-hand side,
+ * distinct.  Asynchronous on `stream`; allocates nothing. */
+dwf_status dwf_mg_apply(dwf_mg* mg, float* z, const float* r, void* stream);
+/* c = P^+ f (device, nblocks x nvec complex FP64, block-major) and f = P c
+ * for one right-hand side: the transfer operators, for tests and users. */
+dwf_status dwf_mg_restrict(dwf_mg* mg, double* c, const float* f, void* stream);
+dwf_status dwf_mg_prolong(dwf_mg* mg, float* f, const double* c, void* stream);
+/* Number of blocks and of coarse unknowns (blocks x nvec); either pointer
+ * may be NULL. */
+dwf_status dwf_mg_info(const dwf_mg* mg, int* nblocks, int* ncoarse);
+/* Copy (device to device, on `stream`) what = 0: the orthonormal basis (an
+ * nvec-lane odd cb FP32 field), what = 1: A_c (row-major complex FP64, rows
+ * and columns (block, k), k fastest) into the caller's buffer dst. */
+dwf_status dwf_mg_copy(const dwf_mg* mg, int what, void* dst, void* stream);
+/* The handle a set-up preconditioner belongs to. */
+dwf_status dwf_mg_handle(const dwf_mg* mg, dwf_handle** h);
+/* dwf_gcr_solve (one right-hand side) with the multigrid preconditioner:
+ * flexible GCR on A x_o = M_pc^+ b'_o with z_j = M^-1 r_j, same residual
+ * rules, stats and fallback. */
+dwf_status dwf_gcr_solve_mg(dwf_handle* h, double* x, const double* b, dwf_mg* mg,
+                            const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
 
 /* ------------------------------------------------ learned preconditioner
  * K: two linear gauge-covariant parallel-transport layers (1 -> 16 -> 1

@@ -279,7 +279,24 @@ dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dw
         set_error("dwf_gcr_solve: x and b must not alias");
         return DWF_ERR_ARG;
     }
-    return gcr_solve(h, x, b, nrhs, K, sp, stats, (cudaStream_t)stream);
+    return gcr_solve(h, x, b, nrhs, K, nullptr, sp, stats, (cudaStream_t)stream);
+}
+
+dwf_status dwf_mg_handle(const dwf_mg* mg, dwf_handle** h);
+
+dwf_status dwf_gcr_solve_mg(dwf_handle* h, double* x, const double* b, dwf_mg* mg,
+                            const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_TRY(check_handle(h));
+    dwf_handle* hm = nullptr;
+    if (mg == nullptr || dwf_mg_handle(mg, &hm) != DWF_OK || hm != h) {
+        set_error("dwf_gcr_solve_mg: the multigrid preconditioner must be set up on this handle");
+        return DWF_ERR_ARG;
+    }
+    if (x != nullptr && x == b) {
+        set_error("dwf_gcr_solve_mg: x and b must not alias");
+        return DWF_ERR_ARG;
+    }
+    return gcr_solve(h, x, b, 1, nullptr, mg, sp, stats, (cudaStream_t)stream);
 }
 
 dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,

@@ -323,7 +323,7 @@ dwf_status unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf_pre
 void free_solver_ws(dwf_handle* h);
 void free_nn_ws(dwf_handle* h);
 void free_gcr_ws(dwf_handle* h);
-dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
+dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K, dwf_mg* mg,
                      const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user);
 dwf_status cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
                       const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user);

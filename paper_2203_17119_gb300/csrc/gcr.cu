@@ -136,8 +136,9 @@ static dwf_status gcr_ws(dwf_handle* h, int nrhs, int k, GcrWS** out) {
 
 dwf_status nn_apply_internal(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs,
                              cudaStream_t s);
+dwf_status mg_apply(dwf_mg* mg, float* z, const float* r, cudaStream_t s);
 
-dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
+dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K, dwf_mg* mg,
                      const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t user) {
     auto t0 = std::chrono::steady_clock::now();
     if (!h->have_gauge || !x || !b || !sp || nrhs < 1 || nrhs > h->nrhs_max || !(sp->tol > 0)) {
@@ -261,7 +262,8 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
         for (int j = 0; j < k; ++j) {
             float* qj = w.q + (size_t)j * no * 2;
             float* zj = w.zz + (size_t)j * no * 2;
-            if (K) DWF_TRY(nn_apply_internal(K, h, zj, w.r, nrhs, s));
+            if (mg) DWF_TRY(mg_apply(mg, zj, w.r, s));
+            else if (K) DWF_TRY(nn_apply_internal(K, h, zj, w.r, nrhs, s));
             else DWF_CUDA(cudaMemcpyAsync(zj, w.r, no * 8, cudaMemcpyDeviceToDevice, s));
             DWF_TRY(op_mpc(h, w.t32, zj, 0, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));
             DWF_TRY(op_mpc(h, qj, w.t32, 1, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));

@@ -85,11 +85,16 @@ __device__ __forceinline__ void scan_bminv(const ScanCtx<VL>& k, float (&x)[VL])
     // inclusive scan of the thread totals over the segment (Hillis-Steele)
     const int me = k.seg0 + k.j;
     float tot = DN ? p[VL - 1] : p[0];
-    int lvl = 0;
-    for (int o = 1; o < k.nthr; o <<= 1, ++lvl) {
-        const bool has = DN ? k.j >= o : k.j + o < k.nthr;
-        const float v = __shfl_sync(k.mask, tot, has ? (DN ? me - o : me + o) : me);
-        if (has) tot = fmaf(k.astep[lvl], v, tot);
+    // unrolled over the five possible strides (compile-time index into astep:
+    // the context stays in registers); strides beyond the segment are skipped
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 1 << lvl;
+        if (o < k.nthr) {
+            const bool has = DN ? k.j >= o : k.j + o < k.nthr;
+            const float v = __shfl_sync(k.mask, tot, has ? (DN ? me - o : me + o) : me);
+            if (has) tot = fmaf(k.astep[lvl], v, tot);
+        }
     }
     // carry in from the neighbouring thread's inclusive total
     const bool hc = DN ? k.j > 0 : k.j + 1 < k.nthr;
@@ -362,7 +367,12 @@ __device__ __forceinline__ void hop_dir(const Sin* __restrict__ in, const int* s
 // Output of one site's VL lanes: PLAIN out = scale * acc; MOO out = M_oo x +
 // scale * acc, returning the lanes' |out|^2 (FP32 arithmetic: summed in FP32
 // per site, one FP64 add per site, off GB300's slow FP64 pipe).
-template <class Sout, class R, int VL, bool DAG, int EPI>
+// Site groups (N5 / VL threads) known at compile time to divide a warp: the
+// epilogues take a site's neighbouring fifth-dimension lane by shuffle.
+template <int VL, int CN5>
+constexpr bool kLaneShfl = CN5 > 0 && CN5 % VL == 0 && CN5 / VL <= 32 && 32 % (CN5 / VL) == 0;
+
+template <class Sout, class R, int VL, bool DAG, int EPI, int CN5>
 __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t site, int lane0,
                                             const R (&ar)[12][VL], const R (&ai)[12][VL],
                                             const LaneNbrs& nb, int box, const ScanCtx<VL>& sk) {
@@ -444,9 +454,15 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t si
             R tr[VL], ti[VL];
             load_lanes<Sout, VL, R>(tb + (int64_t)(c * N5 + lane0) * 2, tr, ti);
             const bool up = c < 6;   // S5^+: upper spins read s + 1
-            R nr, ni;
-            load_c1<Sout, R>(tb + (int64_t)(c * N5 + (up ? l_above : l_below)) * 2, nr, ni);
-            const R fn = up ? (hi_wrap ? -mf : (R)1) : (lo_wrap ? -mf : (R)1);
+            R nr, ni, fn;
+            if constexpr (kLaneShfl<VL, CN5>) {
+                nr = __shfl_sync(nb.mask, up ? tr[0] : tr[VL - 1], up ? nb.src_up : nb.src_dn);
+                ni = __shfl_sync(nb.mask, up ? ti[0] : ti[VL - 1], up ? nb.src_up : nb.src_dn);
+                fn = (R)(up ? nb.f_up : nb.f_dn);
+            } else {
+                load_c1<Sout, R>(tb + (int64_t)(c * N5 + (up ? l_above : l_below)) * 2, nr, ni);
+                fn = up ? (hi_wrap ? -mf : (R)1) : (lo_wrap ? -mf : (R)1);
+            }
             float rr[VL], ri[VL];
             load_lanes<float, VL, float>(rb + (int64_t)c * N5 * 2, rr, ri);
             if (live) {
@@ -514,9 +530,16 @@ __device__ __forceinline__ double hop_store(const HopArgs& a, int N5, int64_t si
         load_lanes<Sout, VL, R>(xb + (int64_t)(c * N5 + lane0) * 2, xr, xi);
         // upper spins use S_- (x_{s-1}) unless dagger, lower S_+
         const bool use_below = (c < 6) != DAG;
-        R nr, ni;
-        load_c1<Sout, R>(xb + (int64_t)(c * N5 + (use_below ? l_below : l_above)) * 2, nr, ni);
-        const R fn = use_below ? f_below : f_above;
+        R nr, ni, fn;
+        if constexpr (kLaneShfl<VL, CN5>) {
+            // the neighbouring lane is held by the adjacent thread of the site group
+            nr = __shfl_sync(nb.mask, use_below ? xr[VL - 1] : xr[0], use_below ? nb.src_dn : nb.src_up);
+            ni = __shfl_sync(nb.mask, use_below ? xi[VL - 1] : xi[0], use_below ? nb.src_dn : nb.src_up);
+            fn = (R)(use_below ? nb.f_dn : nb.f_up);
+        } else {
+            load_c1<Sout, R>(xb + (int64_t)(c * N5 + (use_below ? l_below : l_above)) * 2, nr, ni);
+            fn = use_below ? f_below : f_above;
+        }
         R orr[VL], oi[VL];
         float part = 0.f;
 #pragma unroll
@@ -625,7 +648,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         }
     }
     LaneNbrs nbrs{};
-    if constexpr (EPI == EPI_POST) {
+    if constexpr (EPI == EPI_POST || (EPI == EPI_MOO && kLaneShfl<VL, CN5>)) {
         // site groups are warp-aligned here (TPS divides 32, checked on the host)
         const int wl = threadIdx.x & 31;
         const int tig = lane0 / VL;
@@ -659,15 +682,17 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
         const int* s_nbr_t = reinterpret_cast<const int*>(smem + b * buf_bytes + link_bytes);
         double tile_norm = 0.0;
         for (int sl = sg; sg < G && sl < count; sl += G) {
-            if (EPI == EPI_MOO || EPI == EPI_POST) {
-                // the M_oo input of this site's lanes, into L1 while the eight
-                // directions run: the epilogue's loads then hit L1 instead of
-                // paying twelve dependent trips to L2 / HBM
-                const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + ((int64_t)(begin + sl) * 12 * N5 + lane0) * 2;
+            // the M_oo input of this site's lanes, into L1 while the last two
+            // directions run (earlier, the lines are evicted by the neighbour
+            // traffic before the epilogue reads them)
+            auto prefetch_moo = [&]() {
+                if (EPI == EPI_MOO || EPI == EPI_POST) {
+                    const Sout* xb = reinterpret_cast<const Sout*>(a.xmoo) + ((int64_t)(begin + sl) * 12 * N5 + lane0) * 2;
 #pragma unroll
-                for (int c = 0; c < 12; ++c)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(xb + (int64_t)c * N5 * 2));
-            }
+                    for (int c = 0; c < 12; ++c)
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(xb + (int64_t)c * N5 * 2));
+                }
+            };
             R ar[12][VL], ai[12][VL];
             const Sin* in = reinterpret_cast<const Sin*>(a.in);
             const int* nb = s_nbr_t + sl * 8;
@@ -684,6 +709,7 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                 hop_dir2<5, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
                 hop_dir2<2, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
                 hop_dir2<6, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
+                prefetch_moo();
                 hop_dir2<3, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
                 hop_dir2<7, DAG, Sin, SL>(in, nb, lk, N5, lane0, pr, pi);
 #pragma unroll
@@ -702,10 +728,11 @@ __global__ void __launch_bounds__(256, (VL == 1 && sizeof(R) == 4) ? 3 : 2) k_ho
                 hop_dir<5, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<2, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<6, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
+                prefetch_moo();
                 hop_dir<3, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
                 hop_dir<7, DAG, Sin, SL, R, VL>(in, nb, lk, N5, lane0, ar, ai);
             }
-            tile_norm += hop_store<Sout, R, VL, DAG, EPI>(a, N5, begin + sl, lane0, ar, ai, nbrs, tl.x, sk);
+            tile_norm += hop_store<Sout, R, VL, DAG, EPI, CN5>(a, N5, begin + sl, lane0, ar, ai, nbrs, tl.x, sk);
         }
         double* red = s_red + (size_t)b * nwarps * a.nrhs;
         if (part) {

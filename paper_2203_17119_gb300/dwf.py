@@ -114,6 +114,17 @@ def signatures():
         "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
         "dwf_nn_last_grad": [vp, vp, C.c_size_t],
         "dwf_nn_make_pair": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
+        "dwf_mg_create": [C.POINTER(vp), vp, C.POINTER(C.c_int), i],
+        "dwf_mg_destroy": [vp],
+        "dwf_mg_setup": [vp, vp, vp],
+        "dwf_mg_set_smoother": [vp, i, i, d, d, vp],
+        "dwf_mg_apply": [vp, vp, vp, vp],
+        "dwf_mg_restrict": [vp, vp, vp, vp],
+        "dwf_mg_prolong": [vp, vp, vp, vp],
+        "dwf_mg_info": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "dwf_mg_copy": [vp, i, vp, vp],
+        "dwf_mg_handle": [vp, C.POINTER(vp)],
+        "dwf_gcr_solve_mg": [vp, vp, vp, vp, C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
     }
 
 
@@ -342,6 +353,16 @@ class Handle:
             _check(rc)
         return [s.as_dict() for s in st], rc
 
+    def gcr_solve_mg(self, x, b, mg, tol=1e-10, maxiter=100000, restart=16, max_seconds=0.0,
+                     stream=None, allow_fail=False):
+        """Flexible GCR with the multigrid preconditioner ``mg`` (an ``MG``)."""
+        sp = SolverParams(tol, maxiter, 0.1, restart, 0, FP32, max_seconds, 8, None, 0, 0)
+        st = (SolverStats * max(len(self.boxes), 1))()
+        rc = lib().dwf_gcr_solve_mg(self._h, _ptr(x), _ptr(b), mg._m, C.byref(sp), st, _stream(stream))
+        if not allow_fail:
+            _check(rc)
+        return [v.as_dict() for v in st], rc
+
     def multishift_solve(self, x, b, shifts, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64,
                          max_seconds=0.0, stream=None, allow_fail=False):
         """(M_pc^+ M_pc + sigma_s) x_s = b for every shift: ``b`` an odd cb FP64
@@ -469,6 +490,77 @@ class Handle:
 
     def check_device(self):
         return _check(lib().dwf_check_device(self._h))
+
+
+class MG:
+    """Two-level multigrid preconditioner of A = M_pc^+ M_pc (``dwf_mg``) on a
+    handle: blocks (x, y, z, t) extents, nvec near-null vectors."""
+
+    SMOOTHER = {"none": 0, "chebyshev": 1, "nn": 2}
+
+    def __init__(self, h: "Handle", block, nvec):
+        m = C.c_void_p()
+        _check(lib().dwf_mg_create(C.byref(m), h._h, (C.c_int * 4)(*block), int(nvec)))
+        self._m = m
+        self.h = h
+        self.nvec = int(nvec)
+        self.block = tuple(block)
+        self._K = None
+
+    def close(self):
+        if getattr(self, "_m", None):
+            lib().dwf_mg_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup(self, V, stream=None):
+        """V: odd cb FP32 field with nvec lanes, shape cb_shape(1, nvec)."""
+        _check(lib().dwf_mg_setup(self._m, _ptr(V), _stream(stream)))
+
+    def set_smoother(self, kind="none", steps=0, lo=0.0, hi=0.0, K=None):
+        self._K = K
+        _check(lib().dwf_mg_set_smoother(self._m, self.SMOOTHER[kind], int(steps), float(lo), float(hi),
+                                         K._k if K is not None else None))
+
+    def apply(self, z, r, stream=None):
+        _check(lib().dwf_mg_apply(self._m, _ptr(z), _ptr(r), _stream(stream)))
+        return z
+
+    def sizes(self):
+        nb, nc = C.c_int(), C.c_int()
+        _check(lib().dwf_mg_info(self._m, C.byref(nb), C.byref(nc)))
+        return nb.value, nc.value
+
+    def restrict(self, f, stream=None):
+        nb, nc = self.sizes()
+        c = torch.empty((nb, self.nvec, 2), dtype=torch.float64, device="cuda")
+        _check(lib().dwf_mg_restrict(self._m, _ptr(c), _ptr(f), _stream(stream)))
+        return c
+
+    def prolong(self, c, stream=None):
+        f = self.h.empty_cb(1, 1, FP32)
+        _check(lib().dwf_mg_prolong(self._m, _ptr(f), _ptr(c), _stream(stream)))
+        return f
+
+    def basis(self):
+        """Copy of the orthonormal basis: odd cb FP32 field with nvec lanes."""
+        out = torch.empty(self.h.cb_shape(1, self.nvec), dtype=torch.float32, device="cuda")
+        _check(lib().dwf_mg_copy(self._m, 0, _ptr(out), _stream(None)))
+        torch.cuda.synchronize()
+        return out
+
+    def coarse_operator(self):
+        """A_c = P^+ A P as a complex128 numpy array (nc x nc, (block, k) order)."""
+        nb, nc = self.sizes()
+        out = torch.empty((nc, nc, 2), dtype=torch.float64, device="cuda")
+        _check(lib().dwf_mg_copy(self._m, 1, _ptr(out), _stream(None)))
+        torch.cuda.synchronize()
+        return torch.view_as_complex(out.cpu()).numpy()
 
 
 class NN:
