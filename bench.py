@@ -874,6 +874,73 @@ def run_large(args):
         torch.cuda.empty_cache()
 
 
+def run_mg(args):
+    """Two-level multigrid for the local solves (--mg [NVEC] [ORDER] [BLOCK]):
+    Shamir D_Omega of the 14^4 interior box of the 16^4 x Ls=12 lattice (the
+    setting of Sec. 4).  Set-up = Chebyshev filter of NVEC Gaussian vectors
+    (ORDER applications of A, [hi/50, hi], hi = 1.05 x the top of the spectrum
+    from power iteration) + block aggregation (blocks BLOCK^4) + Galerkin
+    coarse operator; solve = flexible GCR with the V-cycle (Chebyshev
+    smoother, 3 steps on [hi/10, hi]) to 1e-10.  Against one red-black solve:
+    the mixed-precision CGNE and plain FP64 CG of the same system."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    nvec = int(args.mg[0]) if args.mg else 12
+    order = int(args.mg[1]) if len(args.mg) > 1 else 30
+    blk = int(args.mg[2]) if len(args.mg) > 2 else 7
+    rng = np.random.default_rng(SMALL_SEED)
+    U = inputs.gauge_field(SMALL_DIMS, "exp", eps=EPS, rng=rng)
+    src = inputs.gaussian_source(SMALL_DIMS, SMALL_LS, rng=rng)
+    h = G.Handle(SMALL_DIMS, SMALL_LS, G.Action(M5, SMALL_MF, 1.0, 0.0), boxes=[SMALL_BAND], nrhs_max=nvec)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.autotune(1, G.FP32)
+    b = h.pack(torch.from_numpy(np.ascontiguousarray(_box_source(src, SMALL_BAND))).cuda())
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(SMALL_SEED)
+    # top of the spectrum of A (FP32 power iteration)
+    x = torch.randn(h.cb_shape(1), device="cuda", generator=g)
+    t, y = torch.empty_like(x), torch.empty_like(x)
+    lam = 0.0
+    for _ in range(30):
+        x /= x.norm()
+        h.mpc(t, x, prec=G.FP32)
+        h.mpc(y, t, dagger=True, prec=G.FP32)
+        lam = float((x * y).sum())
+        x, y = y, x
+    hi = 1.05 * lam
+    res = {"workload": "Shamir DWF D_Omega, 16^4 x Ls=12 (M5=1.8, m_f=0.01), Omega = the 14^4 interior box",
+           "nvec": nvec, "filter_order": order, "block": [blk] * 4, "lam_max": lam}
+
+    def setup():
+        V0 = torch.randn(h.cb_shape(1, nvec), device="cuda", generator=g)
+        V = torch.empty_like(V0)
+        h.chebyshev_filter(V, V0, order, hi / 50, hi, prec=G.FP32, nrhs=nvec)
+        mg = G.MG(h, (blk,) * 4, nvec)
+        mg.setup(V)
+        mg.set_smoother("chebyshev", 3, hi / 10, hi)
+        return mg
+
+    mg = setup()                       # warm-up (kernels, workspaces)
+    (mg, ms) = _event_ms(setup, stream)
+    res["setup_ms"] = round(ms, 2)
+    res["coarse_unknowns"] = mg.sizes()[1]
+    for name, fn in (("gcr_mg", lambda xx: h.gcr_solve_mg(xx, b, mg, tol=1e-10)),
+                     ("gcr_plain", lambda xx: h.gcr_solve(xx, b, tol=1e-10)),
+                     ("cgne_mixed", lambda xx: h.cgne_solve(xx, b, tol=1e-10, inner=G.FP32)),
+                     ("cgne_fp64", lambda xx: h.cgne_solve(xx, b, tol=1e-10, inner=G.FP64))):
+        xx = torch.zeros_like(b)
+        fn(xx)
+        xx.zero_()
+        (st, ms) = _event_ms(lambda: fn(xx), stream)
+        res[name] = {"ms": round(ms, 2), "iters": st[0][0]["iters"], "true_resid": st[0][0]["true_resid"],
+                     "fallback_to_cg": st[0][0]["recorded"] == -1}
+    res["setup_plus_solve_ms"] = round(res["setup_ms"] + res["gcr_mg"]["ms"], 2)
+    res["vs_one_red_black_solve"] = round(res["cgne_mixed"]["ms"] / res["setup_plus_solve_ms"], 3)
+    print(json.dumps(res))
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -944,6 +1011,8 @@ def main():
                     help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--multishift", nargs="+", metavar="ARG",
                     help="NSHIFT [f64|f32]: multi-shift CG against single-shift solves")
+    ap.add_argument("--mg", nargs="*", metavar="ARG",
+                    help="multigrid local solve: [NVEC] [ORDER] [BLOCK] (Sec. 4 setting)")
     ap.add_argument("--large", action="store_true",
                     help="32^4 x 16 m_f = 0.005 solves of D and of D_Omega, bands 1, 2, 4")
     ap.add_argument("--chebyshev", nargs="*", metavar="ARG",
@@ -987,6 +1056,9 @@ def main():
         return
     if args.large:
         run_large(args)
+        return
+    if args.mg is not None:
+        run_mg(args)
         return
     if args.hop:
         run_hop(args)

@@ -257,6 +257,18 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
  * tile_sites (nullable) receives the choice. */
 dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites);
 
+/* Persisted autotuning.  dwf_autotune_save writes every choice dwf_autotune
+ * made on this handle to the text file `path`, one line per key
+ *   <device name>/<SMs>|<Lx>,<Ly>,<Lz>,<Lt>|<Ls>|<boxes or "whole">|p<prec>|n<nrhs>
+ * followed by tile, lanes, tensor-core kernel and chunk; lines of other keys
+ * already in the file are kept.  dwf_autotune_load looks up this handle's key
+ * for (nrhs, prec) and, if present (*found = 1), applies it as dwf_set_tile &
+ * co. would (building the tile table); a missing file or key leaves the
+ * handle unchanged with *found = 0.  DWF_ERR_ARG on I/O failures or an entry
+ * out of range. */
+dwf_status dwf_autotune_save(const dwf_handle* h, const char* path);
+dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec prec, int* found);
+
 /* Manual counterpart of dwf_autotune: sites per tile (kMinTile = 4 .. 256,
  * limited by the FP64 hop's shared memory) and lanes per thread of the FP32
  * hop (1 or 2) for every later call with this nrhs.  Builds the tile table
@@ -537,6 +549,12 @@ dwf_status dwf_nn_create(dwf_nn** K, int channels);
 dwf_status dwf_nn_destroy(dwf_nn* K);
 dwf_status dwf_nn_set_weights(dwf_nn* K, const double* w, size_t n_complex);
 dwf_status dwf_nn_get_weights(const dwf_nn* K, double* w, size_t n_complex);
+/* Write K's weights to the file `path` ("DWFNN001", int32 channels, int32 0,
+ * int64 n, then n complex128 in dwf_nn_set_weights order, this host's byte
+ * order) / read them back into K (same channel count).  DWF_ERR_ARG on an I/O
+ * failure or a file of another network. */
+dwf_status dwf_nn_save(const dwf_nn* K, const char* path);
+dwf_status dwf_nn_load(dwf_nn* K, const char* path);
 /* out = K in, odd cb FP32 fields with nrhs lanes (host workspace grows on
  * first use per handle and nrhs). */
 dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs,

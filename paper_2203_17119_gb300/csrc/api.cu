@@ -5,11 +5,14 @@
 
 #include "dev_common.cuh"
 #include <map>
+#include <string>
+#include <vector>
 
 #include "dwf_internal.cuh"
 
 namespace dwf {
 const char* last_error();
+std::string tuning_key(const dwf_handle* h, int nrhs, int prec);
 }
 
 using namespace dwf;
@@ -75,6 +78,7 @@ dwf_status dwf_box_sites(const dwf_handle* h, int box, int parity, int64_t* offs
 }
 
 dwf_status dwf_set_gauge(dwf_handle* h, const double* U, void* stream) {
+    DWF_RANGE("dwf_set_gauge");
     DWF_TRY(check_handle(h));
     if (U == nullptr) {
         set_error("dwf_set_gauge: null gauge pointer");
@@ -84,6 +88,7 @@ dwf_status dwf_set_gauge(dwf_handle* h, const double* U, void* stream) {
 }
 
 dwf_status dwf_pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_prec prec, void* stream) {
+    DWF_RANGE("dwf_pack");
     DWF_TRY(check_handle(h));
     if (!dst || !src || bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
         set_error("dwf_pack: bad argument");
@@ -93,6 +98,7 @@ dwf_status dwf_pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_p
 }
 
 dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf_prec prec, void* stream) {
+    DWF_RANGE("dwf_unpack");
     DWF_TRY(check_handle(h));
     if (!dst || !src || bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
         set_error("dwf_unpack: bad argument");
@@ -103,6 +109,7 @@ dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf
 
 dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
                          dwf_prec prec, int nrhs, void* stream) {
+    DWF_RANGE("dwf_dslash_eo");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_dslash_eo"));
     if (out_parity != 0 && out_parity != 1) {
         set_error("dwf_dslash_eo: out_parity must be 0 or 1");
@@ -114,6 +121,7 @@ dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parit
 
 dwf_status dwf_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger, dwf_prec prec,
                    int nrhs, void* stream) {
+    DWF_RANGE("dwf_hop");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_hop"));
     if (out_parity != 0 && out_parity != 1) {
         set_error("dwf_hop: out_parity must be 0 or 1");
@@ -124,6 +132,7 @@ dwf_status dwf_hop(dwf_handle* h, void* out, const void* in, int out_parity, int
 }
 
 dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites) {
+    DWF_RANGE("dwf_autotune");
     DWF_TRY(check_handle(h));
     if (bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
         set_error("dwf_autotune: bad precision or nrhs");
@@ -153,6 +162,92 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
     DWF_TRY(get_tiles(h, tile_sites, &ts));
     h->tuned_T[nrhs] = tile_sites;
     h->tuned_vl[nrhs] = lanes_per_thread;
+    return DWF_OK;
+}
+
+dwf_status dwf_autotune_save(const dwf_handle* h, const char* path) {
+    DWF_TRY(check_handle(h));
+    if (path == nullptr) {
+        set_error("dwf_autotune_save: null path");
+        return DWF_ERR_ARG;
+    }
+    // existing lines with other keys are kept; this handle's tunings replace theirs
+    std::map<std::string, std::string> lines;
+    std::vector<std::string> order;
+    if (FILE* f = fopen(path, "r")) {
+        char buf[1024];
+        while (fgets(buf, sizeof(buf), f)) {
+            std::string l(buf);
+            while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+            const size_t sp = l.find(' ');
+            if (l.empty() || sp == std::string::npos) continue;
+            const std::string k = l.substr(0, sp);
+            if (!lines.count(k)) order.push_back(k);
+            lines[k] = l;
+        }
+        fclose(f);
+    }
+    for (const auto& kv : h->tuned_prec) {
+        const int nrhs = kv.first;
+        const std::string k = tuning_key(h, nrhs, kv.second);
+        auto get = [&](const std::map<int, int>& m, int dflt) {
+            auto it = m.find(nrhs);
+            return it == m.end() ? dflt : it->second;
+        };
+        char buf[128];
+        snprintf(buf, sizeof(buf), " %d %d %d %d", get(h->tuned_T, 32), get(h->tuned_vl, 2), get(h->tuned_tc, 0),
+                 get(h->tuned_chunk, 1));
+        if (!lines.count(k)) order.push_back(k);
+        lines[k] = k + buf;
+    }
+    FILE* f = fopen(path, "w");
+    if (!f) {
+        set_error("dwf_autotune_save: cannot open %s for writing", path);
+        return DWF_ERR_ARG;
+    }
+    bool ok = true;
+    for (const std::string& k : order) ok = ok && fprintf(f, "%s\n", lines[k].c_str()) > 0;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("dwf_autotune_save: write to %s failed", path);
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
+}
+
+dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec prec, int* found) {
+    DWF_TRY(check_handle(h));
+    if (path == nullptr || found == nullptr || bad_prec(prec) || nrhs < 1 || nrhs > h->nrhs_max) {
+        set_error("dwf_autotune_load: bad argument");
+        return DWF_ERR_ARG;
+    }
+    *found = 0;
+    FILE* f = fopen(path, "r");
+    if (!f) return DWF_OK;   // no file yet: nothing cached
+    const std::string key = tuning_key(h, nrhs, (int)prec);
+    char buf[1024];
+    int T = 0, vl = 0, tc = 0, ck = 0;
+    while (fgets(buf, sizeof(buf), f)) {
+        std::string l(buf);
+        const size_t sp = l.find(' ');
+        if (sp == std::string::npos || l.compare(0, sp, key) != 0 || sp != key.size()) continue;
+        if (sscanf(l.c_str() + sp, "%d %d %d %d", &T, &vl, &tc, &ck) == 4) *found = 1;
+    }
+    fclose(f);
+    if (!*found) return DWF_OK;
+    if (T < kMinTile || T > 256 || (vl != 1 && vl != 2) || (tc != 0 && tc != 1) || ck < 1 || ck > 64 ||
+        hop_smem(T, 8, 8, nrhs) > (size_t)kHopMaxSmem) {
+        *found = 0;
+        set_error("dwf_autotune_load: entry for this handle in %s is out of range", path);
+        return DWF_ERR_ARG;
+    }
+    const TileSet* ts = nullptr;
+    DWF_TRY(get_tiles(h, T, &ts));
+    h->tuned_T[nrhs] = T;
+    h->tuned_vl[nrhs] = vl;
+    h->tuned_tc[nrhs] = tc;
+    h->tuned_chunk[nrhs] = ck;
+    h->tuned_prec[nrhs] = (int)prec;
     return DWF_OK;
 }
 
@@ -214,6 +309,7 @@ dwf_status dwf_alloc_count(uint64_t* n) {
 
 dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity, int dagger, dwf_prec prec,
                      int nrhs, void* stream) {
+    DWF_RANGE("dwf_mooee");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mooee"));
     if (parity != 0 && parity != 1) {
         set_error("dwf_mooee: parity must be 0 or 1");
@@ -225,6 +321,7 @@ dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity, int d
 
 dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity, int dagger,
                          dwf_prec prec, int nrhs, void* stream) {
+    DWF_RANGE("dwf_mooee_inv");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mooee_inv"));
     if (parity != 0 && parity != 1) {
         set_error("dwf_mooee_inv: parity must be 0 or 1");
@@ -236,6 +333,7 @@ dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity, i
 
 dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec, int nrhs,
                    void* stream) {
+    DWF_RANGE("dwf_mpc");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mpc"));
     return op_mpc(h, out, in, dagger ? 1 : 0, prec, prec, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr,
                   (cudaStream_t)stream);
@@ -243,12 +341,14 @@ dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_pre
 
 dwf_status dwf_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec, int nrhs,
                        void* stream) {
+    DWF_RANGE("dwf_apply_d");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_apply_d"));
     return op_apply_d(h, out, in, dagger ? 1 : 0, prec, nrhs, h->d_tmp, (cudaStream_t)stream);
 }
 
 dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec prec,
                                int nrhs, void* stream) {
+    DWF_RANGE("dwf_dirichlet_block");
     DWF_TRY(check_handle(h));
     if (!h->dirichlet) {
         set_error("dwf_dirichlet_block: handle was created for the whole lattice (no boxes)");
@@ -260,6 +360,7 @@ dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dag
 
 dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
                           const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_cgne_solve");
     DWF_TRY(check_handle(h));
     if (sp != nullptr && bad_prec(sp->inner_prec)) {
         set_error("dwf_cgne_solve: bad inner precision");
@@ -274,6 +375,7 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
 
 dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_gcr_solve");
     DWF_TRY(check_handle(h));
     if (x != nullptr && x == b) {
         set_error("dwf_gcr_solve: x and b must not alias");
@@ -286,6 +388,7 @@ dwf_status dwf_mg_handle(const dwf_mg* mg, dwf_handle** h);
 
 dwf_status dwf_gcr_solve_mg(dwf_handle* h, double* x, const double* b, dwf_mg* mg,
                             const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_gcr_solve_mg");
     DWF_TRY(check_handle(h));
     dwf_handle* hm = nullptr;
     if (mg == nullptr || dwf_mg_handle(mg, &hm) != DWF_OK || hm != h) {
@@ -302,12 +405,14 @@ dwf_status dwf_gcr_solve_mg(dwf_handle* h, double* x, const double* b, dwf_mg* m
 dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
                                 int nshift, int nrhs, const dwf_solver_params* sp,
                                 dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_multishift_solve");
     DWF_TRY(check_handle(h));
     return multishift_solve(h, x, b, shifts, nshift, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
 dwf_status dwf_boundary_project(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
                                 int nrhs, void* stream) {
+    DWF_RANGE("dwf_boundary_project");
     DWF_TRY(check_handle(h));
     return boundary_project(h, omega, out, in, nrhs, (cudaStream_t)stream);
 }
@@ -315,12 +420,14 @@ dwf_status dwf_boundary_project(dwf_handle* h, const dwf_box* omega, double* out
 dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const double* in,
                              int nrhs, const dwf_solver_params* sp, dwf_solver_stats* stats,
                              void* stream) {
+    DWF_RANGE("dwf_boundary_rinv");
     DWF_TRY(check_handle(h));
     return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
 dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, const double* in, int nrhs,
                           const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_boundary_r");
     DWF_TRY(check_handle(h));
     return boundary_r(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
@@ -328,6 +435,7 @@ dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, cons
 dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const dwf_box* omega, double* out,
                                     const double* phi, int nrhs, const dwf_box* active, int accumulate,
                                     const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_boundary_ratio_force");
     DWF_TRY(check_handle(h_light));
     DWF_TRY(check_handle(h_pv));
     return boundary_ratio_force(h_light, h_pv, omega, out, phi, nrhs, active, accumulate, sp, stats,
@@ -337,6 +445,7 @@ dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const
 dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, const double* phi, int nrhs,
                               const dwf_box* active, int accumulate, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_boundary_force");
     DWF_TRY(check_handle(h));
     return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
@@ -348,18 +457,21 @@ dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, d
 dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
                               const double* residues, int n, int nrhs, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_rational_apply");
     DWF_TRY(check_handle(h));
     return rational_apply(h, out, in, a0, shifts, residues, n, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
 dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int order, double lo, double hi,
                                 dwf_prec prec, int nrhs, void* stream) {
+    DWF_RANGE("dwf_chebyshev_filter");
     DWF_TRY(check_handle(h));
     return chebyshev_filter(h, out, in, order, lo, hi, prec, nrhs, (cudaStream_t)stream);
 }
 
 dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                      const dwf_box* active, int accumulate, void* stream) {
+    DWF_RANGE("dwf_force");
     DWF_TRY(check_handle(h));
     return force_bilinear(h, out, X, Y, prec, nrhs, active, accumulate, (cudaStream_t)stream);
 }

@@ -11,8 +11,19 @@
 #include <vector>
 
 #include "dwf.h"
+#include "nvtx3/nvToolsExt.h"
 
 namespace dwf {
+
+// An NVTX range around one library call (visible to profilers and tracers;
+// header-only NVTX v3: without an attached tool it costs a branch).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define DWF_RANGE(name) ::dwf::NvtxRange dwf_range_(name)
 
 using bf16 = __nv_bfloat16;
 
@@ -153,6 +164,8 @@ struct dwf_handle {
     std::map<int, int> tuned_tc;
     // hop tile order: nrhs -> consecutive tiles per CTA before striding by the grid
     std::map<int, int> tuned_chunk;
+    // precision the tuning of nrhs was measured with (dwf_autotune)
+    std::map<int, int> tuned_prec;
     // boundary operator tables of the last Omega (boundary.cu)
     void* boundary_cache = nullptr;
 };

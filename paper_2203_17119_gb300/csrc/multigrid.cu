@@ -480,6 +480,7 @@ dwf_status dwf_mg_destroy(dwf_mg* mg) {
 }
 
 dwf_status dwf_mg_setup(dwf_mg* mg, const float* V, void* stream) {
+    DWF_RANGE("dwf_mg_setup");
     if (mg == nullptr || V == nullptr) {
         set_error("dwf_mg_setup: null argument");
         return DWF_ERR_ARG;
@@ -553,6 +554,7 @@ dwf_status dwf_mg_set_smoother(dwf_mg* mg, int kind, int steps, double lo, doubl
 }
 
 dwf_status dwf_mg_apply(dwf_mg* mg, float* z, const float* r, void* stream) {
+    DWF_RANGE("dwf_mg_apply");
     if (mg == nullptr || z == nullptr || r == nullptr || z == r) {
         set_error("dwf_mg_apply: null or aliasing argument");
         return DWF_ERR_ARG;

@@ -603,10 +603,67 @@ dwf_status dwf_nn_get_weights(const dwf_nn* K, double* w, size_t n) {
     return DWF_OK;
 }
 
+// Weight file: the 8 bytes "DWFNN001", int32 channels, int32 0, int64 number
+// of complex weights n, then n complex128 (re, im) in the order of
+// dwf_nn_set_weights, little-endian as written by this host.
+static const char kNNMagic[8] = {'D', 'W', 'F', 'N', 'N', '0', '0', '1'};
+
+dwf_status dwf_nn_save(const dwf_nn* K, const char* path) {
+    if (!K || !path) {
+        set_error("dwf_nn_save: null argument");
+        return DWF_ERR_ARG;
+    }
+    const size_t n = (w1_len(K->C) + w2_len(K->C)) / 2;
+    std::vector<double> w(2 * n);
+    DWF_TRY(dwf_nn_get_weights(K, w.data(), n));
+    FILE* f = fopen(path, "wb");
+    if (!f) {
+        set_error("dwf_nn_save: cannot open %s for writing", path);
+        return DWF_ERR_ARG;
+    }
+    const int32_t hdr[2] = {K->C, 0};
+    const int64_t nn = (int64_t)n;
+    bool ok = fwrite(kNNMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(&nn, sizeof(nn), 1, f) == 1 && fwrite(w.data(), sizeof(double), w.size(), f) == w.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("dwf_nn_save: write to %s failed", path);
+        return DWF_ERR_ARG;
+    }
+    return DWF_OK;
+}
+
+dwf_status dwf_nn_load(dwf_nn* K, const char* path) {
+    if (!K || !path) {
+        set_error("dwf_nn_load: null argument");
+        return DWF_ERR_ARG;
+    }
+    FILE* f = fopen(path, "rb");
+    if (!f) {
+        set_error("dwf_nn_load: cannot open %s", path);
+        return DWF_ERR_ARG;
+    }
+    char magic[8];
+    int32_t hdr[2];
+    int64_t nn = 0;
+    const size_t n = (w1_len(K->C) + w2_len(K->C)) / 2;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kNNMagic, 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+              fread(&nn, sizeof(nn), 1, f) == 1 && hdr[0] == K->C && nn == (int64_t)n;
+    std::vector<double> w(2 * n);
+    ok = ok && fread(w.data(), sizeof(double), w.size(), f) == w.size();
+    fclose(f);
+    if (!ok) {
+        set_error("dwf_nn_load: %s is not a weight file of a %d-channel network", path, K->C);
+        return DWF_ERR_ARG;
+    }
+    return dwf_nn_set_weights(K, w.data(), n);
+}
+
 // One training pair from an FP64 solve: e = (x* - x_k) / |x* - x_k|,
 // r = M_pc^+ M_pc e (FP64 operator), both written in FP32.
 dwf_status dwf_nn_make_pair(dwf_handle* h, const double* x_star, const double* x_k, float* r,
                             float* e, double* norm, void* stream) {
+    DWF_RANGE("dwf_nn_make_pair");
     DWF_TRY(check_handle(h));
     if (!x_star || !x_k || !r || !e || !norm || !h->have_gauge || h->dirichlet) {
         set_error("dwf_nn_make_pair: bad argument (whole-lattice handle with a gauge field, "
@@ -653,6 +710,7 @@ dwf_status dwf_nn_make_pair(dwf_handle* h, const double* x_star, const double* x
 
 // out = K in on the odd checkerboard (FP32 cb fields, nrhs lanes)
 dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs, void* stream) {
+    DWF_RANGE("dwf_nn_apply");
     DWF_TRY(check_handle(h));
     if (!K || !out || !in || nrhs < 1 || nrhs > h->nrhs_max || !h->have_gauge) {
         set_error("dwf_nn_apply: bad argument");
@@ -665,6 +723,7 @@ dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, i
 // loss = mean_k |K r_k - e_k|^2 / |e_k|^2 (returned, before the step).
 dwf_status dwf_nn_train_step(dwf_nn* K, dwf_handle* h, const float* r, const float* e, int nrhs,
                              int loss_kind, double lr, double* loss, void* stream) {
+    DWF_RANGE("dwf_nn_train_step");
     DWF_TRY(check_handle(h));
     if (!K || !r || !e || nrhs < 1 || nrhs > h->nrhs_max || !h->have_gauge || h->dirichlet) {
         set_error("dwf_nn_train_step: bad argument");

@@ -63,6 +63,7 @@ using namespace dwf;
 
 extern "C" dwf_status dwf_mpc_noalloc(dwf_handle* h, void* out, const void* in, int dagger,
                                       dwf_prec prec, int nrhs, void* stream) {
+    DWF_RANGE("dwf_mpc_noalloc");
     DWF_TRY(check_handle(h));
     if (out == nullptr || in == nullptr || out == in) {
         set_error("dwf_mpc_noalloc: null or aliasing field pointers");

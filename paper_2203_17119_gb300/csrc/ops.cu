@@ -10,6 +10,9 @@
 // of the same twisted shift).  Shamir (c5 = 0) skips the (b5 + c5 S5) passes
 // and folds b5 into the hop scale.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "dev_common.cuh"
@@ -131,6 +134,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
     h->tuned_chunk[nrhs] = best_chunk;
+    h->tuned_prec[nrhs] = (int)prec;
     if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;
     if (prec == DWF_BF16) h->tuned_tc[nrhs] = best_vl < 0 ? 1 : 0;
     if (best) *best = best_T;
@@ -138,6 +142,30 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
 }
 
 static int tileT(dwf_handle* h, int, dwf_prec, int nrhs) { return tile_for(h, nrhs); }
+
+// Key of a tuning in the autotune file: the device, the domain (lattice, Ls,
+// boxes), the precision and nrhs -- what the measured choice depends on.
+std::string tuning_key(const dwf_handle* h, int nrhs, int prec) {
+    cudaDeviceProp dp{};
+    cudaGetDeviceProperties(&dp, h->device);
+    std::string name(dp.name);
+    for (char& ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s/%d|%d,%d,%d,%d|%d|", name.c_str(), dp.multiProcessorCount, h->p.dims[0],
+             h->p.dims[1], h->p.dims[2], h->p.dims[3], h->p.Ls);
+    std::string k(buf);
+    if (h->dirichlet)
+        for (const dwf_box& b : h->boxes) {
+            snprintf(buf, sizeof(buf), "%d,%d,%d,%d:%d,%d,%d,%d;", b.origin[0], b.origin[1], b.origin[2], b.origin[3],
+                     b.extent[0], b.extent[1], b.extent[2], b.extent[3]);
+            k += buf;
+        }
+    else
+        k += "whole";
+    snprintf(buf, sizeof(buf), "|p%d|n%d", prec, nrhs);
+    return k + buf;
+}
 
 size_t cb_elems(const dwf_handle* h, int parity, int nrhs) {
     return (size_t)h->nsite[parity] * 12 * h->p.Ls * nrhs;   // complex elements

@@ -114,6 +114,10 @@ def signatures():
         "dwf_nn_train_step": [vp, vp, vp, vp, i, i, d, C.POINTER(C.c_double), vp],
         "dwf_nn_last_grad": [vp, vp, C.c_size_t],
         "dwf_nn_make_pair": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
+        "dwf_nn_save": [vp, C.c_char_p],
+        "dwf_autotune_save": [vp, C.c_char_p],
+        "dwf_autotune_load": [vp, C.c_char_p, i, i, C.POINTER(C.c_int)],
+        "dwf_nn_load": [vp, C.c_char_p],
         "dwf_mg_create": [C.POINTER(vp), vp, C.POINTER(C.c_int), i],
         "dwf_mg_destroy": [vp],
         "dwf_mg_setup": [vp, vp, vp],
@@ -341,6 +345,16 @@ class Handle:
         _check(lib().dwf_autotune(self._h, nrhs, prec, C.byref(t)))
         return t.value
 
+
+    def autotune_save(self, path):
+        """Append / update this handle's tunings in the autotune file ``path``."""
+        _check(lib().dwf_autotune_save(self._h, os.fsencode(path)))
+
+    def autotune_load(self, path, nrhs=1, prec=FP32):
+        """Apply the cached tuning for (nrhs, prec) if ``path`` has one; True if found."""
+        f = C.c_int()
+        _check(lib().dwf_autotune_load(self._h, os.fsencode(path), nrhs, prec, C.byref(f)))
+        return bool(f.value)
     def gcr_solve(self, x, b, K=None, nrhs=1, tol=1e-10, maxiter=100000, restart=16,
                   max_seconds=0.0, stream=None, allow_fail=False):
         """Flexible GCR with the learned preconditioner ``K`` (an ``NN``) or none."""
@@ -623,11 +637,9 @@ class NN:
         return g[:n1].reshape(11, self.C, 1, 4, 4), g[n1:].reshape(11, 1, self.C, 4, 4)
 
     def save(self, path):
-        import numpy as np
-        W1, W2 = self.get_weights()
-        np.savez(path, W1=W1, W2=W2)
+        """dwf_nn_save: the weights to a file."""
+        _check(lib().dwf_nn_save(self._k, os.fsencode(path)))
 
     def load(self, path):
-        import numpy as np
-        z = np.load(path)
-        self.set_weights(z["W1"], z["W2"])
+        """dwf_nn_load: the weights from a file written by save."""
+        _check(lib().dwf_nn_load(self._k, os.fsencode(path)))

@@ -12,7 +12,7 @@ as right-hand-side lanes of one field.  All arithmetic runs in the library
 moves tensors and loops.
 
     python -m paper_2203_17119_gb300.train --train-dims 16 16 16 16 --train-Ls 12 \\
-        --sources 64 --iterates 64 --out K.npz --eval-dims 24 24 24 24 --eval-Ls 16
+        --sources 64 --iterates 64 --out K.dwfnn --eval-dims 24 24 24 24 --eval-Ls 16
 """
 
 from __future__ import annotations
@@ -94,7 +94,7 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--mf", type=float, default=0.005)
-    ap.add_argument("--out", default="K.npz")
+    ap.add_argument("--out", default="K.dwfnn")
     ap.add_argument("--eval-dims", type=int, nargs=4, default=None)
     ap.add_argument("--eval-Ls", type=int, default=16)
     ap.add_argument("--loss", default="a2", choices=["error", "energy", "a2"])

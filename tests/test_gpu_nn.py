@@ -166,3 +166,23 @@ def test_training_generalises_and_gcr_converges():
         assert st[0]["status"] == 0 and st[0]["true_resid"] <= 1e-10
         its[name] = st[0]["iters"]
     print("held-out energy loss", before, "->", after, "GCR iterations", its)
+
+
+def test_weights_file_round_trip(tmp_path):
+    """dwf_nn_save / dwf_nn_load: the weights come back exactly (in the FP32
+    copy the network holds), and a file of another kind is refused."""
+    rng = np.random.default_rng(71)
+    W1, W2 = rand_weights(rng)
+    K = G.NN()
+    K.set_weights(W1, W2)
+    path = str(tmp_path / "k.dwfnn")
+    K.save(path)
+    K2 = G.NN()
+    K2.load(path)
+    a1, a2 = K.get_weights()
+    b1, b2 = K2.get_weights()
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
+    bad = tmp_path / "bad.dwfnn"
+    bad.write_bytes(b"not a weight file")
+    with pytest.raises(G.DWFError):
+        K2.load(str(bad))

@@ -228,3 +228,32 @@ def test_tensor_core_hop(case, dagger):
     assert LY.rel_l2(got[1][0], want_mpc) <= TOL_MPC[G.BF16]
     assert LY.rel_l2(got[1][1], want_eo) <= TOL[G.BF16]
     assert LY.rel_l2(got[1][0], got[0][0]) <= TOL_MPC[G.BF16]
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """dwf_autotune_save writes the tuned choice; a fresh handle of the same
+    domain picks it up with dwf_autotune_load (and gives the same operator);
+    another nrhs or domain finds nothing."""
+    dims, Ls = (4, 4, 4, 8), 8
+    U = inputs.gauge_field(dims, "exp", eps=0.3, seed=73)
+    act = G.Action(1.8, 0.01, 1.5, 0.5)
+    h = G.Handle(dims, Ls, act, nrhs_max=2)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    h.autotune(1, G.FP32)
+    path = str(tmp_path / "tune.txt")
+    h.autotune_save(path)
+    h2 = G.Handle(dims, Ls, act, nrhs_max=2)
+    h2.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    assert h2.autotune_load(path, 1, G.FP32)
+    assert h2.tuning(1) == h.tuning(1)
+    assert not h2.autotune_load(path, 2, G.FP32)
+    assert not h2.autotune_load(path, 1, G.BF16)
+    h3 = G.Handle((4, 4, 4, 4), Ls, act)
+    h3.set_gauge(torch.from_numpy(inputs.gauge_field((4, 4, 4, 4), "haar", seed=1).reshape(-1)).cuda())
+    assert not h3.autotune_load(path, 1, G.FP32)
+    x = torch.randn(h.cb_shape(1), device="cuda")
+    y1, y2 = h.empty_cb(1, 1, G.FP32), h2.empty_cb(1, 1, G.FP32)
+    h.mpc(y1, x, prec=G.FP32)
+    h2.mpc(y2, x, prec=G.FP32)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
