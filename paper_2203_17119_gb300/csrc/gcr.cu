@@ -69,6 +69,103 @@ __global__ void k_caxpy(const int4* __restrict__ tiles, int nrhs, int Ls, const 
     }
 }
 
+// Partial sums per (i, tile, rhs) of <Q_i, v>, i = blockIdx.y: the inner
+// products of classical Gram-Schmidt against all previous directions at once.
+__global__ void __launch_bounds__(512) k_multi_cdot_partial(const int4* __restrict__ tiles, int ntiles, int nrhs,
+                                                            int Ls, const float* __restrict__ Q, size_t fstride,
+                                                            const float* __restrict__ v, double* pre,
+                                                            double* pim) {
+    __shared__ double s_red[512];
+    const int i = blockIdx.y;
+    const float* a = Q + (size_t)i * fstride;
+    const int4 tl = tiles[blockIdx.x];
+    const int rows = tl.z * 12 * nrhs;
+    const int64_t off = (int64_t)tl.y * 12 * nrhs * Ls;
+    double accr = 0.0, acci = 0.0;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+        const float* pa = a + 2 * (off + (int64_t)row * Ls);
+        const float* pb = v + 2 * (off + (int64_t)row * Ls);
+        float sr = 0.f, si = 0.f;
+        for (int s = 0; s < Ls; ++s) {
+            const float ar = pa[2 * s], ai = pa[2 * s + 1], br = pb[2 * s], bi = pb[2 * s + 1];
+            sr += ar * br + ai * bi;
+            si += ar * bi - ai * br;
+        }
+        accr += sr;
+        acci += si;
+    }
+    const int nr = nrhs;
+    auto rhs = [&](int t) { return t < rows ? t % nr : -1; };
+    const size_t o = ((size_t)i * ntiles + blockIdx.x) * nrhs;
+    block_rhs_reduce(accr, s_red, nrhs, rhs, pre + o);
+    block_rhs_reduce(acci, s_red, nrhs, rhs, pim + o);
+}
+
+// c[i][sys] = sgn * sum over the box's tiles of the partials (0 for systems
+// that are not active), i = blockIdx.y; fixed-order tree.
+__global__ void k_multi_reduce(const double* __restrict__ pre, const double* __restrict__ pim,
+                               const int* __restrict__ box_tb, int ntiles, int nrhs, const int* __restrict__ act,
+                               double sgn, double* cre, double* cim) {
+    __shared__ double sr[256], si[256];
+    const int sys = blockIdx.x, i = blockIdx.y;
+    const int nsys = gridDim.x;
+    const int box = sys / nrhs, r = sys % nrhs;
+    const int t0 = box_tb[box], t1 = box_tb[box + 1];
+    double ar = 0.0, ai = 0.0;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const size_t o = ((size_t)i * ntiles + t) * nrhs + r;
+        ar += pre[o];
+        ai += pim[o];
+    }
+    sr[threadIdx.x] = ar;
+    si[threadIdx.x] = ai;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sr[threadIdx.x] += sr[threadIdx.x + w];
+            si[threadIdx.x] += si[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool on = act[sys] != 0;
+        cre[(size_t)i * nsys + sys] = on ? sgn * sr[0] : 0.0;
+        cim[(size_t)i * nsys + sys] = on ? sgn * si[0] : 0.0;
+    }
+}
+
+// y -= sum_{i<j} c_i Q_i and z -= sum_{i<j} c_i Z_i (complex c per system).
+__global__ void k_multi_caxpy(const int4* __restrict__ tiles, int nrhs, int Ls, int nsys, int j,
+                              const double* __restrict__ cre, const double* __restrict__ cim,
+                              const float* __restrict__ Q, const float* __restrict__ Z, size_t fstride,
+                              float* __restrict__ y, float* __restrict__ z) {
+    const int4 tl = tiles[blockIdx.x];
+    const int n = tl.z * 12 * nrhs * Ls;
+    const int64_t off = (int64_t)tl.y * 12 * nrhs * Ls;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int sys = tl.x * nrhs + (e / Ls) % nrhs;
+        float2 yv = reinterpret_cast<float2*>(y)[off + e];
+        float2 zv = reinterpret_cast<float2*>(z)[off + e];
+        for (int i = 0; i < j; ++i) {
+            const float cr = (float)cre[(size_t)i * nsys + sys], ci = (float)cim[(size_t)i * nsys + sys];
+            const float2 q = reinterpret_cast<const float2*>(Q + (size_t)i * fstride)[off + e];
+            const float2 w = reinterpret_cast<const float2*>(Z + (size_t)i * fstride)[off + e];
+            yv.x -= cr * q.x - ci * q.y;
+            yv.y -= cr * q.y + ci * q.x;
+            zv.x -= cr * w.x - ci * w.y;
+            zv.y -= cr * w.y + ci * w.x;
+        }
+        reinterpret_cast<float2*>(y)[off + e] = yv;
+        reinterpret_cast<float2*>(z)[off + e] = zv;
+    }
+}
+
+// inv[sys] = active and n2 > 0 ? 1 / sqrt(n2) : 0
+__global__ void k_inv_norm(const double* __restrict__ n2, const int* __restrict__ act, int nsys, double* inv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nsys) inv[i] = (act[i] != 0 && n2[i] > 0.0) ? 1.0 / sqrt(n2[i]) : 0.0;
+}
+
 struct GcrWS {
     int nrhs = 0, k = 0;
     float* q = nullptr;   // k fields
@@ -87,6 +184,9 @@ struct GcrWS {
     float* t32 = nullptr;
     double* part = nullptr;
     double* scal = nullptr;   // per-system scalars [8][nsys]
+    double* mpart = nullptr;  // Gram-Schmidt partials [2][k][ntiles][nrhs]
+    double* mcoef = nullptr;  // Gram-Schmidt coefficients [2][k][nsys]
+    int* act = nullptr;       // per-system active flags (device)
 };
 
 static std::map<dwf_handle*, GcrWS> g_gcr;
@@ -96,7 +196,7 @@ void free_gcr_ws(dwf_handle* h) {
     if (it == g_gcr.end()) return;
     GcrWS& w = it->second;
     void* p[] = {w.q, w.zz, w.r, w.xlo, w.tA, w.tB, w.x64, w.bp64, w.t64a, w.t64b, w.t64c, w.full64,
-                 w.t64d, w.t32, w.part, w.scal};
+                 w.t64d, w.t32, w.part, w.scal, w.mpart, w.mcoef, w.act};
     for (void* q : p) cudaFree(q);
     g_gcr.erase(it);
 }
@@ -125,6 +225,9 @@ static dwf_status gcr_ws(dwf_handle* h, int nrhs, int k, GcrWS** out) {
         const int64_t nsmax = h->nsite[0] > h->nsite[1] ? h->nsite[0] : h->nsite[1];
         DWF_CUDA(dev_malloc(&v.part, (size_t)2 * (nsmax / kMinTile + h->nbox + 1) * nrhs * 8));
         DWF_CUDA(dev_malloc(&v.scal, (size_t)8 * h->nbox * nrhs * 8));
+        DWF_CUDA(dev_malloc(&v.mpart, (size_t)2 * k * (nsmax / kMinTile + h->nbox + 1) * nrhs * 8));
+        DWF_CUDA(dev_malloc(&v.mcoef, (size_t)2 * k * h->nbox * nrhs * 8));
+        DWF_CUDA(dev_malloc(&v.act, (size_t)h->nbox * nrhs * sizeof(int)));
         v.nrhs = nrhs;
         v.k = k;
         *out = &v;
@@ -257,8 +360,36 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
         if (!any) break;
         DWF_TRY(launch_convert(w.r, DWF_FP32, w.t64d, DWF_FP64, no, s));
         DWF_CUDA(cudaMemsetAsync(w.xlo, 0, no * 8, s));
-        // inner GCR cycle
-        std::vector<std::complex<double>> c(nsys);
+        // inner GCR cycle: Gram-Schmidt, normalisation and the x, r updates run
+        // with device-side coefficients; the host reads |r|^2 once per step
+        {
+            std::vector<int> a(active.begin(), active.end());
+            DWF_CUDA(cudaMemcpyAsync(w.act, a.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
+            DWF_CUDA(cudaStreamSynchronize(s));   // a is a host temporary
+        }
+        const size_t fs = no * 2;                 // floats per field
+        const int ntl = ts.ntiles[1];
+        const int* box_tb = ts.d_box_tile_begin[1];
+        double* mre = w.mcoef;
+        double* mim = w.mcoef + (size_t)k * nsys;
+        double* ppre = w.mpart;
+        double* ppim = w.mpart + (size_t)k * ntl * nrhs;
+        double* a_re = w.scal + 4 * (size_t)nsys;   // <q_j, r> and its negative
+        double* a_im = w.scal + 5 * (size_t)nsys;
+        double* an_re = w.scal + 6 * (size_t)nsys;
+        double* an_im = w.scal + 7 * (size_t)nsys;
+        // one classical Gram-Schmidt pass of (q_j, z_j) against the j previous pairs
+        auto project = [&](int j, float* qj, float* zj) -> dwf_status {
+            k_multi_cdot_partial<<<dim3(ntl, j), cdot_threads, 0, s>>>(ts.d_tiles[1], ntl, nrhs, h->p.Ls, w.q, fs, qj,
+                                                                      ppre, ppim);
+            note_launch();
+            k_multi_reduce<<<dim3(nsys, j), 256, 0, s>>>(ppre, ppim, box_tb, ntl, nrhs, w.act, 1.0, mre, mim);
+            note_launch();
+            k_multi_caxpy<<<ntl, 256, 0, s>>>(ts.d_tiles[1], nrhs, h->p.Ls, nsys, j, mre, mim, w.q, w.zz, fs, qj, zj);
+            note_launch();
+            DWF_CUDA(cudaGetLastError());
+            return DWF_OK;
+        };
         for (int j = 0; j < k; ++j) {
             float* qj = w.q + (size_t)j * no * 2;
             float* zj = w.zz + (size_t)j * no * 2;
@@ -267,26 +398,32 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
             else DWF_CUDA(cudaMemcpyAsync(zj, w.r, no * 8, cudaMemcpyDeviceToDevice, s));
             DWF_TRY(op_mpc(h, w.t32, zj, 0, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));
             DWF_TRY(op_mpc(h, qj, w.t32, 1, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));
-            for (int i = 0; i < j; ++i) {
-                const float* qi = w.q + (size_t)i * no * 2;
-                const float* zi = w.zz + (size_t)i * no * 2;
-                DWF_TRY(cdot(qi, qj));
-                for (int m = 0; m < nsys; ++m) c[m] = active[m] ? -std::complex<double>(hre[m], him[m]) : 0.0;
-                DWF_TRY(caxpy(c, qi, qj));
-                DWF_TRY(caxpy(c, zi, zj));
+            if (j > 0) {
+                // twice (classical Gram-Schmidt with reorthogonalisation): as
+                // stable as the modified form, with all inner products at once
+                DWF_TRY(project(j, qj, zj));
+                DWF_TRY(project(j, qj, zj));
             }
-            std::vector<double> qn2(nsys);
-            DWF_TRY(norm2(1, qj, DWF_FP32, qn2));
-            std::vector<double> inv(nsys);
-            for (int m = 0; m < nsys; ++m) inv[m] = (active[m] && qn2[m] > 0) ? 1.0 / std::sqrt(qn2[m]) : 0.0;
-            DWF_CUDA(cudaMemcpyAsync(s_c2, inv.data(), nsys * 8, cudaMemcpyHostToDevice, s));
+            // q_j, z_j /= |q_j|
+            DWF_TRY(launch_dot_partial(h, 1, qj, qj, DWF_FP32, DWF_FP32, nrhs, pre, T, s));
+            DWF_TRY(launch_reduce_sys(h, 1, pre, nrhs, s_re, T, s));
+            k_inv_norm<<<(nsys + 127) / 128, 128, 0, s>>>(s_re, w.act, nsys, s_c2);
+            note_launch();
             DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, 0.0, nullptr, DWF_FP32, s_c2, 0.0, qj, DWF_FP32, nullptr, T, s));
             DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, 0.0, nullptr, DWF_FP32, s_c2, 0.0, zj, DWF_FP32, nullptr, T, s));
-            DWF_TRY(cdot(qj, w.r));
-            for (int m = 0; m < nsys; ++m) c[m] = active[m] ? std::complex<double>(hre[m], him[m]) : 0.0;
-            DWF_TRY(caxpy(c, zj, w.xlo));
-            for (int m = 0; m < nsys; ++m) c[m] = -c[m];
-            DWF_TRY(caxpy(c, qj, w.r));
+            // a = <q_j, r>: x += a z_j, r -= a q_j
+            k_multi_cdot_partial<<<dim3(ntl, 1), cdot_threads, 0, s>>>(ts.d_tiles[1], ntl, nrhs, h->p.Ls, qj, fs, w.r,
+                                                                      ppre, ppim);
+            note_launch();
+            k_multi_reduce<<<dim3(nsys, 1), 256, 0, s>>>(ppre, ppim, box_tb, ntl, nrhs, w.act, 1.0, a_re, a_im);
+            note_launch();
+            k_multi_reduce<<<dim3(nsys, 1), 256, 0, s>>>(ppre, ppim, box_tb, ntl, nrhs, w.act, -1.0, an_re, an_im);
+            note_launch();
+            k_caxpy<<<ntl, 256, 0, s>>>(ts.d_tiles[1], nrhs, h->p.Ls, a_re, a_im, zj, w.xlo);
+            note_launch();
+            k_caxpy<<<ntl, 256, 0, s>>>(ts.d_tiles[1], nrhs, h->p.Ls, an_re, an_im, qj, w.r);
+            note_launch();
+            DWF_CUDA(cudaGetLastError());
             total_iters++;
             std::vector<double> rr(nsys);
             DWF_TRY(norm2(1, w.r, DWF_FP32, rr));

@@ -130,9 +130,10 @@ def test_gcr_solve(use_k):
 def test_training_generalises_and_gcr_converges():
     """Pairs (r, e) from the iterates of FP64 CGNE solves; Adam on the
     energy-norm loss must lower the held-out loss of the 1/d^2-initialised
-    network by >= 30% (A^2-norm loss: the residual left by one GCR step), and
-    GCR with the trained K must reach 1e-10 (by itself or through its CG
-    fallback), with the iteration counts reported."""
+    network by >= 30% (A^2-norm loss: the residual left by one GCR step);
+    GCR with the trained K must reach 1e-10 by itself (no CG fallback) on a
+    held-out source, in fewer iterations than GCR without the network (or
+    where GCR without it needs the fallback)."""
     from paper_2203_17119_gb300 import train as TR
     dims, Ls, nrhs = (4, 4, 4, 8), 8, 4
     rng, U, h = setup(dims, Ls, nrhs, 15, kind="exp")
@@ -159,13 +160,18 @@ def test_training_generalises_and_gcr_converges():
     assert after < 0.7 * before, (before, after)
     b = inputs.gaussian_source(dims, Ls, rng=rng)
     bf = torch.view_as_real(torch.from_numpy(LY.to_full([[b]], dims, None))).cuda().contiguous()
-    its = {}
+    its, fell = {}, {}
     for name, KK in (("trained", K), ("none", None)):
         x = torch.zeros_like(bf)
         st, rc = h1.gcr_solve(x, bf, K=KK, tol=1e-10, max_seconds=300)
         assert st[0]["status"] == 0 and st[0]["true_resid"] <= 1e-10
+        xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
+        assert O.true_residual(U, xf, b, MOBIUS) <= 1e-10
         its[name] = st[0]["iters"]
-    print("held-out energy loss", before, "->", after, "GCR iterations", its)
+        fell[name] = st[0]["recorded"] == -1
+    print("held-out A^2 loss", before, "->", after, "GCR iterations", its, "CG fallback", fell)
+    assert not fell["trained"]
+    assert fell["none"] or its["trained"] < its["none"], its
 
 
 def test_weights_file_round_trip(tmp_path):
