@@ -260,7 +260,7 @@ dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites)
 /* Persisted autotuning.  dwf_autotune_save writes every choice dwf_autotune
  * made on this handle to the text file `path`, one line per key
  *   <device name>/<SMs>|<Lx>,<Ly>,<Lz>,<Lt>|<Ls>|<boxes or "whole">|p<prec>|n<nrhs>
- * followed by tile, lanes, tensor-core kernel and chunk; lines of other keys
+ * followed by tile, lanes, tensor-core kernel, chunk and fusion; lines of other keys
  * already in the file are kept.  dwf_autotune_load looks up this handle's key
  * for (nrhs, prec) and, if present (*found = 1), applies it as dwf_set_tile &
  * co. would (building the tile table); a missing file or key leaves the
@@ -285,6 +285,18 @@ dwf_status dwf_set_tile(dwf_handle* h, int nrhs, int tile_sites, int lanes_per_t
  * dwf_autotune(prec = DWF_BF16) picks between the two.  DWF_ERR_ARG on
  * values out of range. */
 dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel);
+
+/* Where a site's Ls * nrhs lanes fit the threads of one warp (N5 / lanes per
+ * thread dividing 32), the site-local factors of the Schur operator can run
+ * in the epilogues of the hops instead of separate passes: the
+ * (b5 + c5 S5)(d + e S5)^-1 between the two hops of M_pc and M_pc^+ (its
+ * closed form as decayed prefix sums over the fifth dimension, computed with
+ * warp shuffles) and, inside CGNE, the tail M_oo^+ t - (1/4)(b5 + c5 S5^+)(.)
+ * with the CG update.  fuse = 1 selects that form for every later call with
+ * this nrhs, 0 the separate passes (the default); dwf_autotune times both.
+ * Same results to rounding.  DWF_ERR_ARG unless fuse is 0 or 1. */
+dwf_status dwf_set_fusion(dwf_handle* h, int nrhs, int fuse);
+dwf_status dwf_get_fusion(const dwf_handle* h, int nrhs, int* fuse);
 
 /* Tile order of the hop for every later call with this nrhs: each CTA of
  * the persistent grid takes `chunk` consecutive tiles (neighbouring lattice

@@ -195,8 +195,8 @@ dwf_status dwf_autotune_save(const dwf_handle* h, const char* path) {
             return it == m.end() ? dflt : it->second;
         };
         char buf[128];
-        snprintf(buf, sizeof(buf), " %d %d %d %d", get(h->tuned_T, 32), get(h->tuned_vl, 2), get(h->tuned_tc, 0),
-                 get(h->tuned_chunk, 1));
+        snprintf(buf, sizeof(buf), " %d %d %d %d %d", get(h->tuned_T, 32), get(h->tuned_vl, 2), get(h->tuned_tc, 0),
+                 get(h->tuned_chunk, 1), get(h->tuned_fuse, 0));
         if (!lines.count(k)) order.push_back(k);
         lines[k] = k + buf;
     }
@@ -226,16 +226,17 @@ dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec
     if (!f) return DWF_OK;   // no file yet: nothing cached
     const std::string key = tuning_key(h, nrhs, (int)prec);
     char buf[1024];
-    int T = 0, vl = 0, tc = 0, ck = 0;
+    int T = 0, vl = 0, tc = 0, ck = 0, fu = 0;
     while (fgets(buf, sizeof(buf), f)) {
         std::string l(buf);
         const size_t sp = l.find(' ');
         if (sp == std::string::npos || l.compare(0, sp, key) != 0 || sp != key.size()) continue;
-        if (sscanf(l.c_str() + sp, "%d %d %d %d", &T, &vl, &tc, &ck) == 4) *found = 1;
+        if (sscanf(l.c_str() + sp, "%d %d %d %d %d", &T, &vl, &tc, &ck, &fu) == 5) *found = 1;
     }
     fclose(f);
     if (!*found) return DWF_OK;
     if (T < kMinTile || T > 256 || (vl != 1 && vl != 2) || (tc != 0 && tc != 1) || ck < 1 || ck > 64 ||
+        (fu != 0 && fu != 1) ||
         hop_smem(T, 8, 8, nrhs) > (size_t)kHopMaxSmem) {
         *found = 0;
         set_error("dwf_autotune_load: entry for this handle in %s is out of range", path);
@@ -247,6 +248,7 @@ dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec
     h->tuned_vl[nrhs] = vl;
     h->tuned_tc[nrhs] = tc;
     h->tuned_chunk[nrhs] = ck;
+    h->tuned_fuse[nrhs] = fu;
     h->tuned_prec[nrhs] = (int)prec;
     return DWF_OK;
 }
@@ -258,6 +260,27 @@ dwf_status dwf_set_hop_kernel(dwf_handle* h, int nrhs, int kernel) {
         return DWF_ERR_ARG;
     }
     h->tuned_tc[nrhs] = kernel;
+    return DWF_OK;
+}
+
+dwf_status dwf_set_fusion(dwf_handle* h, int nrhs, int fuse) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max || (fuse != 0 && fuse != 1)) {
+        set_error("dwf_set_fusion: nrhs in [1, nrhs_max], fuse 0 or 1");
+        return DWF_ERR_ARG;
+    }
+    h->tuned_fuse[nrhs] = fuse;
+    return DWF_OK;
+}
+
+dwf_status dwf_get_fusion(const dwf_handle* h, int nrhs, int* fuse) {
+    DWF_TRY(check_handle(h));
+    if (nrhs < 1 || nrhs > h->nrhs_max || fuse == nullptr) {
+        set_error("dwf_get_fusion: bad argument");
+        return DWF_ERR_ARG;
+    }
+    auto it = h->tuned_fuse.find(nrhs);
+    *fuse = it == h->tuned_fuse.end() ? 0 : it->second;
     return DWF_OK;
 }
 

@@ -166,6 +166,9 @@ struct dwf_handle {
     std::map<int, int> tuned_chunk;
     // precision the tuning of nrhs was measured with (dwf_autotune)
     std::map<int, int> tuned_prec;
+    // nrhs -> 1: the site-local factors of M_pc / M_pc^+ run in the hop
+    // epilogues where the site groups allow it (EPI_BMINV, EPI_POST)
+    std::map<int, int> tuned_fuse;
     // boundary operator tables of the last Omega (boundary.cu)
     void* boundary_cache = nullptr;
 };

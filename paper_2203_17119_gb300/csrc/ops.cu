@@ -54,6 +54,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     const auto saved_vl = h->tuned_vl;
     const auto saved_tc = h->tuned_tc;
     const auto saved_chunk = h->tuned_chunk;
+    const auto saved_fuse = h->tuned_fuse;
     // candidates are timed with L2 flushed (solves stream more than L2 holds)
     const size_t flush_bytes = (size_t)256 << 20;
     void* flush = nullptr;
@@ -69,12 +70,17 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
                                                     : std::vector<int>{0};
     const int chunks[] = {1, 8};
     int best_chunk = 1;
+    int best_fuse = 0;
+    // the fused epilogues exist for FP32-arithmetic chains whose site groups
+    // divide a warp: time both forms there
+    const bool can_fuse = chain && hop_bminv_ok(h, prec, nrhs, 2);
     int n_sm = 152;
     {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     }
+    for (int fu = 0; fu <= (can_fuse ? 1 : 0); ++fu)
     for (int ck : chunks)
     for (int vl : vls)
     for (int T : cands) {
@@ -103,6 +109,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
             if (chain) {
                 h->tuned_T[nrhs] = T;
                 h->tuned_chunk[nrhs] = ck;
+                h->tuned_fuse[nrhs] = fu;
                 if (vl > 0) h->tuned_vl[nrhs] = vl;
                 if (prec == DWF_BF16) h->tuned_tc[nrhs] = vl < 0 ? 1 : 0;
                 st = op_mpc(h, t2 + bytes, t2, 0, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
@@ -120,7 +127,7 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         if (st != DWF_OK) break;
         std::sort(ts.begin(), ts.end());
         const float med = ts[ts.size() / 2];
-        if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; best_chunk = ck; }
+        if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; best_chunk = ck; best_fuse = fu; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -131,10 +138,12 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
     h->tuned_vl = saved_vl;
     h->tuned_tc = saved_tc;
     h->tuned_chunk = saved_chunk;
+    h->tuned_fuse = saved_fuse;
     if (st != DWF_OK) return st;
     h->tuned_T[nrhs] = best_T;
     h->tuned_chunk[nrhs] = best_chunk;
     h->tuned_prec[nrhs] = (int)prec;
+    h->tuned_fuse[nrhs] = best_fuse;
     if (prec == DWF_FP32) h->tuned_vl[nrhs] = best_vl;
     if (prec == DWF_BF16) h->tuned_tc[nrhs] = best_vl < 0 ? 1 : 0;
     if (best) *best = best_T;
@@ -183,6 +192,13 @@ static int hop_vl(dwf_handle* h, dwf_prec link, int nrhs) {
 static HopCall hop_call(dwf_handle* h, const void* in, void* out, int out_parity, int dagger,
                         dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
                         const void* xmoo, double* partial);
+
+// Whether the chains of nrhs right-hand sides run the site-local factors in
+// the hop epilogues (chosen by dwf_autotune or dwf_set_fusion; default off).
+static bool fused(const dwf_handle* h, int nrhs) {
+    auto it = h->tuned_fuse.find(nrhs);
+    return it != h->tuned_fuse.end() && it->second != 0;
+}
 
 dwf_status op_hop(dwf_handle* h, void* out, const void* in, int out_parity, int dagger,
                   dwf_prec link, dwf_prec pin, dwf_prec pout, int nrhs, double scale,
@@ -267,7 +283,7 @@ static dwf_status hop_then_bminv(dwf_handle* h, const void* in, int dagger, dwf_
     void* first = (in == tmpA) ? tmpB : tmpA;
     void* second = (first == tmpA) ? tmpB : tmpA;
     HopCall hc = hop_call(h, in, first, 0, dagger, po, pin, po, nrhs, scale, nullptr, nullptr);
-    if (hc.tc == 0 && hop_bminv_ok(h, po, nrhs, hop_vl(h, po, nrhs))) {
+    if (hc.tc == 0 && fused(h, nrhs) && hop_bminv_ok(h, po, nrhs, hop_vl(h, po, nrhs))) {
         hc.bminv = true;
         *res = first;
         return launch_hop(h, hc, s);
@@ -304,7 +320,7 @@ dwf_status op_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_prec
     DWF_TRY(hop_then_bminv(h, in, 1, po, pv, nrhs, 1.0, tmpA, tmpB, &mid, s));
     void* other = (mid == tmpA) ? tmpB : tmpA;
     HopCall hc = hop_call(h, mid, nullptr, 1, 1, po, po, pv, nrhs, -0.25, in, partial);
-    if (cg != nullptr && hc.tc == 0 && hop_post_ok(h, po, pv, nrhs, hop_vl(h, po, nrhs))) {
+    if (cg != nullptr && hc.tc == 0 && fused(h, nrhs) && hop_post_ok(h, po, pv, nrhs, hop_vl(h, po, nrhs))) {
         // the tail M_oo^+ in - (1/4) B^+ (.) and the CG update in the last hop's epilogue
         hc.post = true;
         hc.cg_x = cg->x;

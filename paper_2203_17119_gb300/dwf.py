@@ -116,6 +116,8 @@ def signatures():
         "dwf_nn_make_pair": [vp, vp, vp, vp, vp, C.POINTER(C.c_double), vp],
         "dwf_nn_save": [vp, C.c_char_p],
         "dwf_autotune_save": [vp, C.c_char_p],
+        "dwf_set_fusion": [vp, i, i],
+        "dwf_get_fusion": [vp, i, C.POINTER(C.c_int)],
         "dwf_autotune_load": [vp, C.c_char_p, i, i, C.POINTER(C.c_int)],
         "dwf_nn_load": [vp, C.c_char_p],
         "dwf_mg_create": [C.POINTER(vp), vp, C.POINTER(C.c_int), i],
@@ -482,6 +484,15 @@ class Handle:
     def set_hop_kernel(self, nrhs=1, kernel=1):
         """BF16-operator hop for this nrhs: 0 = FP32 SIMT, 1 = tensor cores."""
         _check(lib().dwf_set_hop_kernel(self._h, nrhs, kernel))
+
+    def set_fusion(self, nrhs=1, fuse=True):
+        """dwf_set_fusion: site-local factors of M_pc in the hop epilogues (where possible)."""
+        _check(lib().dwf_set_fusion(self._h, nrhs, 1 if fuse else 0))
+
+    def fusion(self, nrhs=1):
+        f = C.c_int()
+        _check(lib().dwf_get_fusion(self._h, nrhs, C.byref(f)))
+        return bool(f.value)
 
     def set_hop_chunk(self, nrhs=1, chunk=1):
         """Consecutive tiles per CTA of the hop before striding by the grid."""

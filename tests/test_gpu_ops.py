@@ -161,20 +161,27 @@ def test_pack_unpack_layout(case, prec):
 @pytest.mark.parametrize("tile,vl,chunk", [(4, 1, 1), (8, 2, 1), (48, 1, 1), (64, 2, 1),
                                             (4, 2, 8), (8, 1, 3)])
 def test_tile_and_lane_variants(tile, vl, chunk):
-    """Every (tile size, lanes per thread, tile order) choice the autotuner can
-    make gives the same operator: hop-based dslash_eo and M_pc in FP32 and FP64."""
+    """Every (tile size, lanes per thread, tile order, epilogue fusion) choice
+    the autotuner can make gives the same operator: hop-based dslash_eo and
+    M_pc (both adjoints) in FP32 and FP64, with the site-local factor of M_pc
+    in the hop epilogue (8 lanes x 2 rhs: the site groups divide a warp) and
+    without."""
     dims, Ls, prm, boxes, nrhs, U, masks, psi, h = _setup("mobius_boxes_odd_wrap")
     h.set_tile(nrhs, tile, vl)
     h.set_hop_chunk(nrhs, chunk)
     po = [[O.parity_part(f, 1) for f in row] for row in psi]
     src = LY.to_cb(po, dims, boxes, 1)
-    want = LY.to_cb([[O.mpc_in(U, f, prm, masks[b]) for f in po[b]] for b in range(len(po))],
-                    dims, boxes, 1)
-    for prec in (G.FP64, G.FP32):
-        out = h.empty_cb(1, nrhs, prec)
-        h.mpc(out, _gpu(src, prec), False, prec, nrhs)
-        torch.cuda.synchronize()
-        assert LY.rel_l2(_host(out), want) <= TOL_MPC[prec], prec
+    for dagger in (False, True):
+        want = LY.to_cb([[O.mpc_in(U, f, prm, masks[b], dagger) for f in po[b]] for b in range(len(po))],
+                        dims, boxes, 1)
+        for fuse in (False, True):
+            h.set_fusion(nrhs, fuse)
+            for prec in (G.FP64, G.FP32, G.BF16):
+                out = h.empty_cb(1, nrhs, prec)
+                h.mpc(out, _gpu(src, prec), dagger, prec, nrhs)
+                torch.cuda.synchronize()
+                assert LY.rel_l2(_host(out), want) <= TOL_MPC[prec], (prec, dagger, fuse)
+    h.set_fusion(nrhs, False)
     want0 = LY.to_cb([[O.eo_block_in(U, f, prm, masks[b], 0) for f in psi[b]]
                       for b in range(len(psi))], dims, boxes, 0)
     out = h.empty_cb(0, nrhs, G.FP32)

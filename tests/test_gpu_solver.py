@@ -177,13 +177,15 @@ def test_solver_time_caps():
 @pytest.mark.parametrize("prm", [MOBIUS, SHAMIR], ids=["mobius", "shamir"])
 @pytest.mark.parametrize("inner,vl", [(G.FP32, 1), (G.FP32, 2), (G.BF16, 2)])
 def test_mixed_solve_ls16_fused_adjoint_tail(prm, inner, vl):
-    """Ls = 16 (one right-hand side: 16 or 8 threads per site, the site groups
-    in which the last adjoint hop of every CG iteration also applies
-    M_oo^+ - (1/4)(b5 + c5 S5^+) and the CG update): the mixed solve reaches
-    1e-10 by the oracle's residual."""
+    """Ls = 16 (one right-hand side: 16 or 8 threads per site, site groups in
+    which, with the epilogue fusion on, the first hop of M_pc and M_pc^+
+    applies (b5 + c5 S5)(d + e S5)^-1 and the last adjoint hop of every CG
+    iteration M_oo^+ - (1/4)(b5 + c5 S5^+) with the CG update): the mixed
+    solve reaches 1e-10 by the oracle's residual."""
     dims, Ls = (4, 4, 4, 8), 16
     U, b, h, bf = _problem(dims, Ls, prm, "exp", seed=1005)
     h.set_tile(1, 8, vl)
+    h.set_fusion(1, True)
     x = torch.zeros_like(bf)
     st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=inner)
     assert rc == 0

@@ -189,9 +189,10 @@ def _sampled_check(h, dom, U, prm, Ls, nrhs, fin, precs, cfgs, n_sample, seed, o
                 if cfg is None:
                     h.autotune(nrhs, G.FP32)
                 else:
-                    T, vl, chunk = cfg
+                    T, vl, chunk, fuse = cfg
                     h.set_tile(nrhs, T, vl)
                     h.set_hop_chunk(nrhs, chunk)
+                    h.set_fusion(nrhs, fuse)
                 for prec in precs:
                     src = fin.to(G._DTYPE[prec])
                     out = h.empty_cb(p_out, nrhs, prec)
@@ -229,6 +230,7 @@ def test_16x12_whole_field(lat16, cfg):
     dims, Ls, U, h = lat16
     h.set_tile(1, cfg[0], cfg[1])
     h.set_hop_chunk(1, cfg[2])
+    h.set_fusion(1, False)
     for p_out in (0, 1):
         fin = _randn(h.cb_shape(1 - p_out), 17 + p_out)
         psi = LY.from_cb(_host(fin), dims, None, 1 - p_out, Ls)[0][0]
@@ -254,7 +256,8 @@ def test_16x12_whole_field(lat16, cfg):
 def test_32x16_sampled():
     """The paper's per-GPU volume: 32^4 x Ls=16 FP32 and BF16 dslash_eo and
     M_pc at sampled sites, in the bench's bare-hop configuration (64-site
-    tiles, two lanes per thread, chunks of 8) and the autotuned one."""
+    tiles, two lanes per thread, chunks of 8), with the site-local factor of
+    M_pc in the hop epilogue (32-site tiles), and the autotuned one."""
     dims, Ls = (32, 32, 32, 32), 16
     U = inputs.gauge_field(dims, "haar", seed=1003)
     h = G.Handle(dims, Ls, _action(MOBIUS_LIGHT))
@@ -262,8 +265,8 @@ def test_32x16_sampled():
     dom = Domain(dims, None)
     fin = _randn(h.cb_shape(1), 31)
     res = _sampled_check(h, dom, U, MOBIUS_LIGHT, Ls, 1, fin, (G.FP32, G.BF16),
-                         [(64, 2, 8), None], 256, 5, ("eo", "mpc"))
-    assert len(res) == 2 * 2 * 2 * 2
+                         [(64, 2, 8, False), (32, 2, 1, True), None], 256, 5, ("eo", "mpc"))
+    assert len(res) == 2 * 2 * 3 * 2
 
 
 # ------------------------------------------- 24^4 x 16, six boxes x 16 rhs
@@ -284,7 +287,7 @@ def test_six_boxes_16rhs_sampled(six_boxes):
     dims, Ls, nrhs, U, h, dom = six_boxes
     fin = _randn(h.cb_shape(1, nrhs), 41)
     res = _sampled_check(h, dom, U, MOBIUS, Ls, nrhs, fin, (G.FP32, G.BF16),
-                         [(8, 2, 1), (16, 1, 8)], 192, 9, ("eo", "mpc"))
+                         [(8, 2, 1, False), (16, 1, 8, False)], 192, 9, ("eo", "mpc"))
     assert len(res) == 2 * 2 * 2 * 2
 
 
