@@ -941,6 +941,50 @@ def run_mg(args):
     print(json.dumps(res))
 
 
+def run_learned(args):
+    """The learned preconditioner at the configuration it is quoted on
+    (--learned [SOURCES] [ITERATES]): K trained on the GPU (library kernels)
+    on (residual, error) pairs from FP64 solves at 16^4 x Ls=12, m_f = 0.005,
+    then used at 24^4 x Ls=16, m_f = 0.005: GCR with K, GCR without it, GCR
+    with the two-level multigrid (Chebyshev smoother / K as smoother), mixed
+    CG and FP64 CG to 1e-10 on a held-out source."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    from paper_2203_17119_gb300 import train as TR
+    sources = int(args.learned[0]) if args.learned else 16
+    iterates = int(args.learned[1]) if len(args.learned) > 1 else 64
+    act = G.Action(M5, 0.005, B5, C5)
+    dims, Ls, batch = SMALL_DIMS, SMALL_LS, 4
+    rng = np.random.default_rng(1004)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
+    Ut = torch.from_numpy(U.reshape(-1)).cuda()
+    h1 = G.Handle(dims, Ls, act, nrhs_max=1)
+    h1.set_gauge(Ut)
+    hb = G.Handle(dims, Ls, act, nrhs_max=batch)
+    hb.set_gauge(Ut)
+    K = TR.initial_network(B5 * (4 - M5) + 1)
+    t0 = time.time()
+    npairs, loss0, loss1 = 0, None, None
+    for s in range(sources):
+        b = inputs.gaussian_source(dims, Ls, rng=rng)
+        r, e = TR.make_pairs(h1, torch.from_numpy(b.reshape(-1)).cuda(), iterates, record_every=4)
+        npairs += r.shape[0]
+        losses = TR.train(K, hb, r, e, steps=16, batch=batch, lr=1e-3, seed=s, loss_kind="a2")
+        loss0 = losses[0] if loss0 is None else loss0
+        loss1 = losses[-1]
+        del r, e
+    train_s = time.time() - t0
+    del h1, hb, Ut
+    torch.cuda.empty_cache()
+    ev = TR.evaluate(K, (24, 24, 24, 24), 16, act)
+    print(json.dumps({"workload": "learned preconditioner: trained at 16^4 x Ls=12, used at 24^4 x Ls=16, "
+                                  "Moebius m_f=0.005, exp(i 0.3 H) links",
+                      "train_pairs": npairs, "train_seconds": round(train_s, 1),
+                      "train_loss_first_last": [loss0, loss1], "eval": ev}))
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -1011,6 +1055,8 @@ def main():
                     help="six uneven Dirichlet boxes in 24^4 x 16: NRHS [f32|bf16]")
     ap.add_argument("--multishift", nargs="+", metavar="ARG",
                     help="NSHIFT [f64|f32]: multi-shift CG against single-shift solves")
+    ap.add_argument("--learned", nargs="*", metavar="ARG",
+                    help="train K at 16^4 x 12, evaluate at 24^4 x 16: [SOURCES] [ITERATES]")
     ap.add_argument("--mg", nargs="*", metavar="ARG",
                     help="multigrid local solve: [NVEC] [ORDER] [BLOCK] (Sec. 4 setting)")
     ap.add_argument("--large", action="store_true",
@@ -1059,6 +1105,9 @@ def main():
         return
     if args.mg is not None:
         run_mg(args)
+        return
+    if args.learned is not None:
+        run_learned(args)
         return
     if args.hop:
         run_hop(args)
