@@ -875,13 +875,13 @@ def run_large(args):
 
 
 def run_mg(args):
-    """Two-level multigrid for the local solves (--mg [NVEC] [ORDER] [BLOCK]):
+    """Two-level multigrid for the local solves (--mg [NVEC] [ORDER] [BLOCK] [STEPS]):
     Shamir D_Omega of the 14^4 interior box of the 16^4 x Ls=12 lattice (the
     setting of Sec. 4).  Set-up = Chebyshev filter of NVEC Gaussian vectors
     (ORDER applications of A, [hi/50, hi], hi = 1.05 x the top of the spectrum
     from power iteration) + block aggregation (blocks BLOCK^4) + Galerkin
     coarse operator; solve = flexible GCR with the V-cycle (Chebyshev
-    smoother, 3 steps on [hi/10, hi]) to 1e-10.  Against one red-black solve:
+    smoother, STEPS steps on [hi/10, hi]) to 1e-10.  Against one red-black solve:
     the mixed-precision CGNE and plain FP64 CG of the same system."""
     import numpy as np
     import torch
@@ -911,7 +911,10 @@ def run_mg(args):
         x, y = y, x
     hi = 1.05 * lam
     res = {"workload": "Shamir DWF D_Omega, 16^4 x Ls=12 (M5=1.8, m_f=0.01), Omega = the 14^4 interior box",
-           "nvec": nvec, "filter_order": order, "block": [blk] * 4, "lam_max": lam}
+           "nvec": nvec, "filter_order": order, "block": [blk] * 4, "lam_max": lam,
+           "smoother": f"Chebyshev iteration, {int(args.mg[3]) if len(args.mg) > 3 else 3} steps on [hi/10, hi]"}
+
+    steps = int(args.mg[3]) if len(args.mg) > 3 else 3
 
     def setup():
         V0 = torch.randn(h.cb_shape(1, nvec), device="cuda", generator=g)
@@ -919,7 +922,7 @@ def run_mg(args):
         h.chebyshev_filter(V, V0, order, hi / 50, hi, prec=G.FP32, nrhs=nvec)
         mg = G.MG(h, (blk,) * 4, nvec)
         mg.setup(V)
-        mg.set_smoother("chebyshev", 3, hi / 10, hi)
+        mg.set_smoother("chebyshev", steps, hi / 10, hi)
         return mg
 
     mg = setup()                       # warm-up (kernels, workspaces)

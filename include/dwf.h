@@ -502,8 +502,8 @@ dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dw
  * construction: aggregates are 4D blocks (extents `block`, dividing every
  * box's extents) of the odd sites of each box with all their Ls and
  * spin-colour components; the prolongator P holds the vectors restricted to
- * each block and orthonormalised there by modified Gram-Schmidt in vector
- * order (P^+ P = 1); the coarse operator A_c = P^+ A P (Galerkin) is dense,
+ * each block and orthonormalised there by Gram-Schmidt in vector order
+ * (classical, twice; P^+ P = 1); the coarse operator A_c = P^+ A P (Galerkin) is dense,
  * built by nblocks applications of A with nvec lanes and inverted once on the
  * host (at most 4096 coarse unknowns = blocks x nvec).  The preconditioner
  * is the V(1,1) cycle z = S r; z += P A_c^-1 P^+ (r - A z); z += S (r - A z)

@@ -7,7 +7,8 @@
 //   aggregates  4D blocks of the odd sites of each box (all Ls and spin-colour
 //               components of a block together)
 //   P           the near-null vectors restricted to each block and
-//               orthonormalised there by modified Gram-Schmidt (P^+ P = 1)
+//               orthonormalised there in vector order (classical Gram-Schmidt
+//               with reorthogonalisation, P^+ P = 1)
 //   A_c         P^+ A P (Galerkin), dense, inverted once on the host
 //   M^-1 r      V(1,1) cycle: z = S r; z += P A_c^-1 P^+ (r - A z);
 //               z += S (r - A z), smoother S none, a Chebyshev iteration on
@@ -84,83 +85,94 @@ __device__ __forceinline__ size_t mg_elem(const int* sites, int e, int Ls, int n
     return ((size_t)((size_t)site * 12 + c) * nlane + lane) * Ls + s;
 }
 
-// Modified Gram-Schmidt of the nvec basis vectors within each block (one CTA
-// per block): B_k -= <B_j, B_k> B_j for j < k in order, then B_k /= |B_k|.
-__global__ void __launch_bounds__(kMgThreads) k_mg_orth(float2* basis, const int* __restrict__ off,
-                                                        const int* __restrict__ sites, int nvec, int Ls,
-                                                        int* err) {
+// out[b][j] = <B_j, B_k> over block b for j0 <= j < j0 + gridDim.y (one CTA
+// per (block, j)): the inner products of Gram-Schmidt, all blocks at once.
+__global__ void __launch_bounds__(kMgThreads) k_mg_bdot(const float2* __restrict__ basis, const int* __restrict__ off,
+                                                        const int* __restrict__ sites, int nvec, int Ls, int k,
+                                                        int j0, double2* out) {
     __shared__ double2 sh[32];
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, j = j0 + blockIdx.y;
     const int* bs = sites + off[b];
     const int nel = (off[b + 1] - off[b]) * 12 * Ls;
-    for (int k = 0; k < nvec; ++k) {
-        for (int j = 0; j <= k; ++j) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-                int site;
-                const float2 u = basis[mg_elem(bs, e, Ls, nvec, j, site)];
-                const float2 w = basis[mg_elem(bs, e, Ls, nvec, k, site)];
-                acc.x += (double)u.x * w.x + (double)u.y * w.y;     // conj(u) w
-                acc.y += (double)u.x * w.y - (double)u.y * w.x;
-            }
-            const double2 d = block_sum2(acc, sh);
-            if (j < k) {
-                const float dr = (float)d.x, di = (float)d.y;
-                for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-                    int site;
-                    const float2 u = basis[mg_elem(bs, e, Ls, nvec, j, site)];
-                    const size_t ik = mg_elem(bs, e, Ls, nvec, k, site);
-                    float2 w = basis[ik];
-                    w.x -= dr * u.x - di * u.y;
-                    w.y -= dr * u.y + di * u.x;
-                    basis[ik] = w;
-                }
-            } else {
-                if (!(d.x > 0.0)) {
-                    if (threadIdx.x == 0) atomicOr(err, 1);
-                    return;
-                }
-                const float inv = (float)(1.0 / sqrt(d.x));
-                for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-                    int site;
-                    const size_t ik = mg_elem(bs, e, Ls, nvec, k, site);
-                    float2 w = basis[ik];
-                    w.x *= inv;
-                    w.y *= inv;
-                    basis[ik] = w;
-                }
-            }
-            __syncthreads();
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        int site;
+        const float2 u = basis[mg_elem(bs, e, Ls, nvec, j, site)];
+        const float2 w = basis[mg_elem(bs, e, Ls, nvec, k, site)];
+        acc.x += (double)(u.x * w.x + u.y * w.y);     // conj(u) w
+        acc.y += (double)(u.x * w.y - u.y * w.x);
+    }
+    const double2 d = block_sum2(acc, sh);
+    if (threadIdx.x == 0) out[(size_t)b * nvec + j] = d;
+}
+
+// B_k -= sum_{j<k} d[b][j] B_j on every odd site (b its block): one
+// classical Gram-Schmidt projection (thread per complex element of B_k).
+__global__ void k_mg_bproj(float2* basis, const int* __restrict__ site_block, const double2* __restrict__ d,
+                           int64_t nsites, int nvec, int Ls, int k) {
+    const int64_t n = nsites * 12 * Ls;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ls);
+        const int64_t sc = i / Ls;                      // site * 12 + component
+        const int b = site_block[sc / 12];
+        float2* row = basis + (size_t)sc * nvec * Ls + s;
+        float2 w = row[(size_t)k * Ls];
+        for (int j = 0; j < k; ++j) {
+            const double2 c = d[(size_t)b * nvec + j];
+            const float2 u = row[(size_t)j * Ls];
+            w.x -= (float)c.x * u.x - (float)c.y * u.y;
+            w.y -= (float)c.x * u.y + (float)c.y * u.x;
         }
+        row[(size_t)k * Ls] = w;
     }
 }
 
-// c[r][b][k] = <B_k on block b, f_r> (one CTA per block; f has nrhs lanes).
+// B_k /= |B_k| per block (d[b][k] holds |B_k|^2 on block b); a vanishing
+// norm sets the error word and leaves the vector.
+__global__ void k_mg_bscale(float2* basis, const int* __restrict__ site_block, const double2* __restrict__ d,
+                            int64_t nsites, int nvec, int Ls, int k, int* err) {
+    const int64_t n = nsites * 12 * Ls;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Ls);
+        const int64_t sc = i / Ls;
+        const int b = site_block[sc / 12];
+        const double n2 = d[(size_t)b * nvec + k].x;
+        if (!(n2 > 0.0)) {
+            atomicOr(err, 1);
+            continue;
+        }
+        const float inv = (float)(1.0 / sqrt(n2));
+        float2* w = basis + ((size_t)sc * nvec + k) * Ls + s;
+        w->x *= inv;
+        w->y *= inv;
+    }
+}
+
+// c[r][b][k] = <B_k on block b, f_r>: one CTA per (block, k, rhs).
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(const float2* __restrict__ basis,
                                                             const float2* __restrict__ f,
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ sites, int nvec,
                                                             int nrhs, int Ls, int nb, double2* c) {
     __shared__ double2 sh[32];
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, k = blockIdx.y, r = blockIdx.z;
     const int* bs = sites + off[b];
     const int nel = (off[b + 1] - off[b]) * 12 * Ls;
-    for (int r = 0; r < nrhs; ++r)
-        for (int k = 0; k < nvec; ++k) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-                int site;
-                const float2 u = basis[mg_elem(bs, e, Ls, nvec, k, site)];
-                const int q = e / (12 * Ls);
-                const int rem = e - q * 12 * Ls;
-                const int cc = rem / Ls, s = rem - cc * Ls;
-                const float2 w = f[((size_t)((size_t)site * 12 + cc) * nrhs + r) * Ls + s];
-                acc.x += (double)(u.x * w.x + u.y * w.y);
-                acc.y += (double)(u.x * w.y - u.y * w.x);
-            }
-            const double2 d = block_sum2(acc, sh);
-            if (threadIdx.x == 0) c[((size_t)r * nb + b) * nvec + k] = d;
-        }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        int site;
+        const float2 u = basis[mg_elem(bs, e, Ls, nvec, k, site)];
+        const int q = e / (12 * Ls);
+        const int rem = e - q * 12 * Ls;
+        const int cc = rem / Ls, s = rem - cc * Ls;
+        const float2 w = f[((size_t)((size_t)site * 12 + cc) * nrhs + r) * Ls + s];
+        acc.x += (double)(u.x * w.x + u.y * w.y);
+        acc.y += (double)(u.x * w.y - u.y * w.x);
+    }
+    const double2 d = block_sum2(acc, sh);
+    if (threadIdx.x == 0) c[((size_t)r * nb + b) * nvec + k] = d;
 }
 
 // f_r (+)= sum_k c[r][block(site)][k] B_k  (thread per complex element).
@@ -237,8 +249,9 @@ static int mg_grid(int64_t n) {
 }
 
 static dwf_status mg_restrict(dwf_mg* mg, double2* c, const float* f, int nrhs, cudaStream_t s) {
-    k_mg_restrict<<<mg->nb, kMgThreads, 0, s>>>(mg->d_basis, reinterpret_cast<const float2*>(f), mg->d_blk_off,
-                                                mg->d_blk_sites, mg->nvec, nrhs, mg->h->p.Ls, mg->nb, c);
+    k_mg_restrict<<<dim3(mg->nb, mg->nvec, nrhs), kMgThreads, 0, s>>>(
+        mg->d_basis, reinterpret_cast<const float2*>(f), mg->d_blk_off, mg->d_blk_sites, mg->nvec, nrhs,
+        mg->h->p.Ls, mg->nb, c);
     note_launch();
     DWF_CUDA(cudaGetLastError());
     return DWF_OK;
@@ -497,8 +510,24 @@ dwf_status dwf_mg_setup(dwf_mg* mg, const float* V, void* stream) {
     mg->ready = false;
     DWF_CUDA(cudaMemcpyAsync(mg->d_basis, V, no * nvec * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     DWF_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
-    k_mg_orth<<<nb, kMgThreads, 0, s>>>(mg->d_basis, mg->d_blk_off, mg->d_blk_sites, nvec, Ls, h->d_err);
-    note_launch();
+    // block Gram-Schmidt in vector order: for each k two classical projections
+    // against B_0..B_{k-1} (as stable as the modified form), then the norm
+    double2* dots = mg->d_c;   // nb x nvec complex (set-up scratch)
+    const int64_t ns = h->nsite[1];
+    const int g = mg_grid(ns * 12 * Ls);
+    for (int k = 0; k < nvec; ++k) {
+        for (int pass = 0; pass < 2 && k > 0; ++pass) {
+            k_mg_bdot<<<dim3(nb, k), kMgThreads, 0, s>>>(mg->d_basis, mg->d_blk_off, mg->d_blk_sites, nvec, Ls, k, 0,
+                                                         dots);
+            k_mg_bproj<<<g, 256, 0, s>>>(mg->d_basis, mg->d_site_block, dots, ns, nvec, Ls, k);
+            note_launch();
+            note_launch();
+        }
+        k_mg_bdot<<<dim3(nb, 1), kMgThreads, 0, s>>>(mg->d_basis, mg->d_blk_off, mg->d_blk_sites, nvec, Ls, k, k, dots);
+        k_mg_bscale<<<g, 256, 0, s>>>(mg->d_basis, mg->d_site_block, dots, ns, nvec, Ls, k, h->d_err);
+        note_launch();
+        note_launch();
+    }
     DWF_CUDA(cudaGetLastError());
     // Galerkin A_c, nvec columns (b0, k) at a time as the lanes of one A application
     float* F = mg->d_f[0];
