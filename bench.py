@@ -717,6 +717,95 @@ def run_force(args):
                       "oracle_sample": "8^4 x Ls, one call, time per site scaled to the lattice"}))
 
 
+def run_one_flavour(args):
+    """One-flavour DD-RHMC boundary term (--one-flavour [f64|f32] [N]) on the
+    16^4 x 12 Moebius workload cut into two t-slabs of 16^3 x 8 (Omega and
+    Omega-bar: D_dirichlet = D_Omega (+) D_Omega-bar): the type (N, N) fits of
+    x^(1/4), x^(-1/2) and x^(-1/4) (dwf_rational_power) on [1e-6, 1.1 lam_max],
+    then the heat bath phi = A_d^(-1/4) A^(1/4) eta, the action (checked:
+    S(phi) = |eta|^2 up to the fits) and the link force, wall-clock per call
+    with the multi-shift solves to 1e-10 (f32: FP32 operator with FP64 defect
+    correction)."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    opt = args.one_flavour
+    prec_name = opt[0] if opt else "f32"
+    n = int(opt[1]) if len(opt) > 1 else 20
+    inner = G.PREC[prec_name]
+    tol = 1e-10
+    dims, Ls = SMALL_DIMS, SMALL_LS
+    rng = np.random.default_rng(SMALL_SEED)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
+    act = G.Action(M5, SMALL_MF, B5, C5)
+    cut = [((0, 0, 0, 0), (dims[0], dims[1], dims[2], dims[3] // 2))]
+    h = G.Handle(dims, Ls, act)
+    hd = G.Handle(dims, Ls, act, cut=cut)
+    Ut = torch.from_numpy(U.reshape(-1)).cuda()
+    h.set_gauge(Ut)
+    hd.set_gauge(Ut)
+    for hh in (h, hd):
+        hh.autotune(1, G.FP32)
+
+    def lam_max(hh, iters=40):
+        x = torch.randn(hh.cb_shape(1), dtype=torch.float64, device="cuda")
+        t, y = torch.empty_like(x), torch.empty_like(x)
+        lam = 0.0
+        for _ in range(iters):
+            x /= x.norm()
+            hh.mpc(t, x)
+            hh.mpc(y, t, dagger=True)
+            lam = float((x * y).sum())
+            x, y = y, x
+        return lam
+
+    hi = 1.1 * max(lam_max(h), lam_max(hd))
+    lo = 1e-6
+    t = time.time()
+    fits = {a: G.rational_power(a, n, lo, hi) for a in (0.25, -0.25, -0.5)}
+    fit_s = time.time() - t
+    rat = {a: (f[0], f[1], f[2]) for a, f in fits.items()}
+    eta = torch.empty(h.cb_shape(1), dtype=torch.float64, device="cuda")
+    eta.normal_()
+    phi = torch.empty_like(eta)
+    out = torch.zeros(U.size * 2, dtype=torch.float64, device="cuda")
+    del U
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.time() - t0, r
+
+    # warm-up of every path, then one timed call each
+    h.one_flavour_heatbath(hd, phi, eta, rat[-0.25], rat[0.25], tol=tol, inner=inner)
+    t_hb, st_hb = timed(lambda: h.one_flavour_heatbath(hd, phi, eta, rat[-0.25], rat[0.25], tol=tol, inner=inner))
+    t_act, (S, st_act) = timed(lambda: h.one_flavour_action(hd, phi, rat[0.25], rat[-0.5], tol=tol, inner=inner))
+    h.one_flavour_force(hd, out, phi, rat[0.25], rat[-0.5], tol=tol, inner=inner)
+    t_f, st_f = timed(lambda: h.one_flavour_force(hd, out, phi, rat[0.25], rat[-0.5], tol=tol, inner=inner))
+    e2 = float((eta * eta).sum())
+
+    def iters(st, counts):
+        out_, k = [], 0
+        for c in counts:
+            out_.append(max(s["iters"] for s in st[k:k + c]))
+            k += c
+        return out_
+
+    print(json.dumps({
+        "workload": f"one-flavour DD-RHMC term, {SMALL_WORKLOAD}, Omega / Omega-bar the two 16^3 x 8 t-slabs",
+        "prec": prec_name, "poles": n, "spectrum": [lo, hi], "fit_seconds": fit_s,
+        "fit_delta": {str(a): f[3] for a, f in fits.items()},
+        "heatbath_s": t_hb, "action_s": t_act, "force_s": t_f,
+        "action_over_eta2_minus_1": S[0] / e2 - 1.0,
+        "cg_iters": {"heatbath": iters(st_hb, [n, n]), "action": iters(st_act, [n, n]),
+                     "force": iters(st_f, [n, n, n])},
+        "max_true_resid": max(s["true_resid"] for s in st_f),
+        "force_norm": float(out.norm())}))
+
+
 def run_boundary(args):
     """DD-HMC boundary operator at the default workload (--boundary [f32|f64]):
     Omega = the interior 14^4 box of the width-2 band.  Times the projector P,
@@ -1068,6 +1157,8 @@ def main():
                     help="Chebyshev filter of the local normal operator: [ORDER] [f32|f64]")
     ap.add_argument("--boundary", nargs="*", metavar="ARG",
                     help="boundary operator P, R^-1 and the boundary-action force: [f32|f64]")
+    ap.add_argument("--one-flavour", nargs="*", metavar="ARG",
+                    help="[f64|f32] [N]: the one-flavour DD-RHMC heat bath, action and force")
     ap.add_argument("--force", nargs="*", metavar="ARG",
                     help="link force of Re <X, D Y>: [f64|f32] [L] [Ls]")
     ap.add_argument("--hop", nargs="+", metavar="ARG",
@@ -1096,6 +1187,9 @@ def main():
         return
     if args.force is not None:
         run_force(args)
+        return
+    if args.one_flavour is not None:
+        run_one_flavour(args)
         return
     if args.boundary is not None:
         run_boundary(args)

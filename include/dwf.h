@@ -23,15 +23,18 @@
  * directions x, y, z), g_4 = [[0, 1], [1, 0]] (t), g_5 = diag(1, 1, -1, -1),
  * P_+ = spins {0, 1}, P_- = spins {2, 3}.  4D parity is (x + y + z + t) mod 2.
  *
- * Entry points, by group: handles and layouts (dwf_create ... dwf_unpack);
- * operators (dwf_dslash_eo, dwf_hop, dwf_mooee, dwf_mooee_inv, dwf_mpc,
- * dwf_apply_d, dwf_dirichlet_block); solvers (dwf_cgne_solve,
- * dwf_multishift_solve, dwf_rational_apply, dwf_gcr_solve with the learned
- * preconditioner dwf_nn_*); the DD-HMC boundary operator and forces of
- * Sec. 2.1 and 2.3 (dwf_boundary_project, dwf_boundary_r, dwf_boundary_rinv,
- * dwf_force, dwf_boundary_force, dwf_boundary_ratio_force); rational
- * approximation and multigrid set-up (dwf_zolotarev_inv_sqrt,
- * dwf_chebyshev_filter); kernel tuning (dwf_autotune, dwf_set_tile, ...).
+ * Entry points, by group: handles and layouts (dwf_create, dwf_create_cut
+ * ... dwf_unpack); operators (dwf_dslash_eo, dwf_hop, dwf_mooee,
+ * dwf_mooee_inv, dwf_mpc, dwf_apply_d, dwf_dirichlet_block); solvers
+ * (dwf_cgne_solve, dwf_multishift_solve, dwf_rational_apply, dwf_gcr_solve
+ * with the learned preconditioner dwf_nn_* or the multigrid dwf_mg_*); the
+ * DD-HMC boundary operator and forces of Sec. 2.1 and 2.3
+ * (dwf_boundary_project, dwf_boundary_r, dwf_boundary_rinv, dwf_force,
+ * dwf_boundary_force, dwf_boundary_ratio_force) and the one-flavour
+ * DD-RHMC term of Sec. 2.3.1 (dwf_one_flavour_action, _force, _heatbath);
+ * rational approximation and multigrid set-up (dwf_zolotarev_inv_sqrt,
+ * dwf_rational_power, dwf_chebyshev_filter); kernel tuning (dwf_autotune,
+ * dwf_set_tile, ...).
  *
  * ------------------------------------------------------------------------
  * DOMAINS.  A handle is bound to a domain: either the whole periodic
@@ -110,6 +113,16 @@ typedef struct {
     int extent[4];
 } dwf_box;
 
+/* A rational function in partial fractions,
+ *   r(x) = a0 + sum_{i<n} residues[i] / (x + shifts[i]),
+ * host arrays of n values (shifts >= 0), e.g. from dwf_rational_power. */
+typedef struct {
+    double a0;
+    const double* shifts;
+    const double* residues;
+    int n;
+} dwf_rational;
+
 typedef struct dwf_handle dwf_handle;
 typedef struct dwf_nn dwf_nn;
 typedef struct dwf_mg dwf_mg;
@@ -125,6 +138,18 @@ typedef struct dwf_mg dwf_mg;
 dwf_status dwf_create(dwf_handle** h, const dwf_params* p, const dwf_box* boxes,
                       int nbox, int nrhs_max);
 dwf_status dwf_destroy(dwf_handle* h);
+
+/* A whole-lattice handle of D_dirichlet (Sec. 2.3.1, eq. ddrhmc: det D /
+ * det D_dirichlet with D_dirichlet = D_Omega (+) D_Omega-bar): D with every
+ * link U_mu(x) left out whose ends x, x + mu lie in different domains, the
+ * domains being the `ncut` boxes and the rest of the lattice (Sec. 2.4's
+ * Dirichlet wrapper of the gauge field).  Site order, layouts and every call
+ * are those of a whole-lattice handle (dwf_create with boxes = NULL); only the
+ * link tables built by dwf_set_gauge differ (the left-out links are zero), so
+ * the same field serves D and D_dirichlet.  Errors as dwf_create, and
+ * DWF_ERR_ARG if ncut < 1, an extent is out of range or two boxes overlap. */
+dwf_status dwf_create_cut(dwf_handle** h, const dwf_params* p, const dwf_box* cut, int ncut,
+                          int nrhs_max);
 
 /* Number of sites of the handle's domain with parity `parity`. */
 dwf_status dwf_domain_sites(const dwf_handle* h, int parity, int64_t* nsites);
@@ -454,6 +479,25 @@ dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const
  * DWF_ERR_ARG unless 1 <= n <= 64 and 0 < lo < hi. */
 dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta);
 
+/* Best relative rational approximation of a fractional power, type (n, n),
+ * in partial fractions (host only, no GPU):
+ *   x^alpha ~ a0 + sum_{i<n} residues[i] / (x + shifts[i])   on [lo, hi],
+ * minimising max |r(x) / x^alpha - 1| =: *delta; the error equioscillates at
+ * 2n + 2 points (Chebyshev's characterisation of the unique best fit).
+ * These are the RHMC coefficients of the one-flavour DD-RHMC term of
+ * Sec. 2.3.1: alpha = 1/4 for (D_dir^+ D_dir)^(1/4), -1/2 for (D^+ D)^(-1/2),
+ * and -1/4, 1/4 for the heat bath (lo, hi bracketing the spectrum of
+ * M_pc^+ M_pc).  Shifts are > 0; residues > 0 for alpha < 0, < 0 for
+ * alpha > 0.  The Remez algorithm (Newton on the equioscillation equations,
+ * exchange of the reference points), started from Zolotarev's closed form at
+ * alpha = -1/2 and continued in alpha; alpha > 0 from the reciprocal of the
+ * fit of x^-alpha.  shifts, residues: caller arrays of n doubles; delta may
+ * be NULL.  DWF_ERR_ARG unless -1 < alpha < 1, alpha != 0, 1 <= n <= 48 and
+ * 0 < lo < hi <= 1e14 lo; DWF_ERR_NOT_CONVERGED if the iteration breaks down
+ * (an n whose error would fall below rounding). */
+dwf_status dwf_rational_power(double alpha, int n, double lo, double hi, double* a0, double* shifts,
+                              double* residues, double* delta);
+
 /* Rational function of the normal Schur operator in partial fractions,
  *   out = a0 in + sum_i residues[i] (M_pc^+ M_pc + shifts[i])^-1 in,
  * the form the DD-RHMC action of Sec. 2.3.1 takes for the powers of the
@@ -467,6 +511,46 @@ dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, d
 dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
                               const double* residues, int n, int nrhs, const dwf_solver_params* sp,
                               dwf_solver_stats* stats, void* stream);
+
+/* The one-flavour DD-RHMC boundary term of Sec. 2.3.1,
+ *   S = phi^+ r1(A_d) r2(A) r1(A_d) phi,  r1 ~ x^(1/4), r2 ~ x^(-1/2)
+ * (the paper's (D_dir^+ D_dir)^(1/4) (D^+ D)^(-1/2) (D_dir^+ D_dir)^(1/4) on
+ * the even-odd preconditioned operators: the site-local M_ee is common to D
+ * and D_dirichlet, so the Schur operators carry det D / det D_dirichlet),
+ * A = M_pc^+ M_pc of D on handle h (whole lattice), A_d that of D_dirichlet
+ * on handle hd (dwf_create_cut; same lattice, action and gauge field).
+ * phi: device odd cb FP64 field, nrhs pseudofermions.  Multi-shift solves
+ * with `sp` (FP64 or FP32 operator as in dwf_multishift_solve).
+ *
+ * dwf_one_flavour_action: S[r] per right-hand side (host array of nrhs);
+ *   stats: [r1->n][nrhs] (w = r1(A_d) phi) then [r2->n][nrhs] (r2(A) w).
+ * dwf_one_flavour_force: the link force of S summed over right-hand sides,
+ *   out[lex][mu] (canonical gauge layout, traceless anti-Hermitian) with
+ *   d/d eps S(exp(i eps H) U) |_0 = Re tr[i H F], from
+ *     F = 2 sum_i rho2_i F_M(M x_i, x_i) + 2 sum_j rho1_j (F_Md(M_d z_j, y_j) + F_Md(M_d y_j, z_j)),
+ *   x_i = (A + s2_i)^-1 w, z_j = (A_d + s1_j)^-1 phi, y_j = (A_d + s1_j)^-1 r2(A) w,
+ *   F_M(X_o, Y_o) the force of -Re <X_o, M_pc Y_o> (one dwf_force insertion
+ *   of the fields completed on the even sites by M_ee^-1 M_eo and its
+ *   adjoint); stats: the two above then [r1->n][nrhs] (y); `active` and
+ *   `accumulate` as in dwf_force.
+ * dwf_one_flavour_heatbath: phi = q1(A_d) q2(A) eta with q1 ~ x^(-1/4) and
+ *   q2 ~ x^(1/4), so that S(phi) = |eta|^2 up to the approximations (eta:
+ *   Gaussian noise, device odd cb FP64, distinct from phi); stats: [q2->n][nrhs]
+ *   then [q1->n][nrhs].
+ * Each call allocates its pole fields (n1 + n2, resp. 2 n1 + n2 + 7 odd cb
+ * FP64 fields for the force) for the call and returns the first non-OK
+ * status of its solves.  DWF_ERR_ARG on handles that do not form such a
+ * pair, a rational function with n < 1 or a negative shift, or null arrays. */
+dwf_status dwf_one_flavour_action(dwf_handle* h, dwf_handle* hd, const double* phi, int nrhs,
+                                  const dwf_rational* r1, const dwf_rational* r2, const dwf_solver_params* sp,
+                                  double* S, dwf_solver_stats* stats, void* stream);
+dwf_status dwf_one_flavour_force(dwf_handle* h, dwf_handle* hd, double* out, const double* phi, int nrhs,
+                                 const dwf_rational* r1, const dwf_rational* r2, const dwf_box* active,
+                                 int accumulate, const dwf_solver_params* sp, dwf_solver_stats* stats,
+                                 void* stream);
+dwf_status dwf_one_flavour_heatbath(dwf_handle* h, dwf_handle* hd, double* phi, const double* eta, int nrhs,
+                                    const dwf_rational* q1, const dwf_rational* q2, const dwf_solver_params* sp,
+                                    dwf_solver_stats* stats, void* stream);
 
 /* Chebyshev filter of the normal Schur operator: the recursively built
  * filter functions of Sec. 4 for a fast multigrid set-up of the local

@@ -65,3 +65,38 @@ def partial_fraction_eval(x, shifts, residues, a0=0.0):
     for s, r in zip(shifts, residues):
         out = out + r / (x + s)
     return out
+
+
+def zolotarev_inv_sqrt_nn(n: int, lo: float, hi: float, grid: int = 200001):
+    """(a0, shifts, residues, delta): the optimal relative approximation of
+    1/sqrt(x) on [lo, hi] of type (n, n), 1/sqrt(x) ~ a0 + sum residues /
+    (x + shifts).  Zolotarev's closed form with 2n + 1 in place of 2n: on
+    y = x / lo, c_l = sn^2/cn^2(l K' / (2n + 1) | m') for l = 1 .. 2n, poles
+    c_1, c_3, .., c_{2n-1}, zeros c_2, .., c_{2n}, and r(y) = D prod (y + zeros)
+    / prod (y + poles) with D centring the relative error (which then
+    equioscillates at 2n + 2 points)."""
+    if n < 1 or not (0 < lo < hi):
+        raise ValueError("n >= 1 and 0 < lo < hi")
+    b = hi / lo
+    mp = 1.0 - 1.0 / b
+    Kp = special.ellipk(mp)
+    c = []
+    for l in range(1, 2 * n + 1):
+        sn, cn, _, _ = special.ellipj(l * Kp / (2 * n + 1), mp)
+        c.append(sn * sn / (cn * cn))
+    poles = np.array(c[0::2])
+    zeros = np.array(c[1::2])
+    y = np.geomspace(1.0, b, grid)
+    prod = np.ones_like(y)
+    for z, p in zip(zeros, poles):
+        prod = prod * (y + z) / (y + p)
+    e = np.sqrt(y) * prod
+    D = 2.0 / (e.max() + e.min())
+    delta = (e.max() - e.min()) / (e.max() + e.min())
+    residues = []
+    for j, p in enumerate(poles):
+        R = D * np.prod(zeros - p) / np.prod([q - p for k, q in enumerate(poles) if k != j])
+        residues.append(R)
+    # back to x = lo y: r(x) = lo^(-1/2) (D + sum R / (x / lo + p))
+    s = lo ** -0.5
+    return s * D, lo * poles, s * lo * np.array(residues), float(delta)

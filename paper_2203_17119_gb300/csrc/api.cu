@@ -54,6 +54,10 @@ dwf_status dwf_create(dwf_handle** h, const dwf_params* p, const dwf_box* boxes,
     return dwf::create(h, p, boxes, nbox, nrhs_max);
 }
 
+dwf_status dwf_create_cut(dwf_handle** h, const dwf_params* p, const dwf_box* cut, int ncut, int nrhs_max) {
+    return dwf::create_cut(h, p, cut, ncut, nrhs_max);
+}
+
 dwf_status dwf_destroy(dwf_handle* h) { return dwf::destroy(h); }
 
 dwf_status dwf_domain_sites(const dwf_handle* h, int parity, int64_t* nsites) {
@@ -475,6 +479,39 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
 
 dwf_status dwf_zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta) {
     return zolotarev_inv_sqrt(n, lo, hi, shifts, residues, delta);
+}
+
+dwf_status dwf_rational_power(double alpha, int n, double lo, double hi, double* a0, double* shifts,
+                              double* residues, double* delta) {
+    return rational_power(alpha, n, lo, hi, a0, shifts, residues, delta);
+}
+
+dwf_status dwf_one_flavour_action(dwf_handle* h, dwf_handle* hd, const double* phi, int nrhs,
+                                  const dwf_rational* r1, const dwf_rational* r2, const dwf_solver_params* sp,
+                                  double* S, dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_one_flavour_action");
+    DWF_TRY(check_handle(h));
+    DWF_TRY(check_handle(hd));
+    return one_flavour_action(h, hd, phi, nrhs, r1, r2, sp, S, stats, (cudaStream_t)stream);
+}
+
+dwf_status dwf_one_flavour_force(dwf_handle* h, dwf_handle* hd, double* out, const double* phi, int nrhs,
+                                 const dwf_rational* r1, const dwf_rational* r2, const dwf_box* active,
+                                 int accumulate, const dwf_solver_params* sp, dwf_solver_stats* stats,
+                                 void* stream) {
+    DWF_RANGE("dwf_one_flavour_force");
+    DWF_TRY(check_handle(h));
+    DWF_TRY(check_handle(hd));
+    return one_flavour_force(h, hd, out, phi, nrhs, r1, r2, active, accumulate, sp, stats, (cudaStream_t)stream);
+}
+
+dwf_status dwf_one_flavour_heatbath(dwf_handle* h, dwf_handle* hd, double* phi, const double* eta, int nrhs,
+                                    const dwf_rational* q1, const dwf_rational* q2, const dwf_solver_params* sp,
+                                    dwf_solver_stats* stats, void* stream) {
+    DWF_RANGE("dwf_one_flavour_heatbath");
+    DWF_TRY(check_handle(h));
+    DWF_TRY(check_handle(hd));
+    return one_flavour_heatbath(h, hd, phi, eta, nrhs, q1, q2, sp, stats, (cudaStream_t)stream);
 }
 
 dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,

@@ -487,6 +487,76 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
     return DWF_OK;
 }
 
+// D_dirichlet of Sec. 2.3.1 in the whole-lattice layout: a whole-lattice
+// handle whose link tables leave out every link U_mu(x) with x and x + mu in
+// different domains -- the boxes of `cut` and the rest of the lattice -- the
+// Dirichlet wrapper of the gauge field of Sec. 2.4 (the edges of a domain are
+// where its mask differs from its shift by one).  Its operators are those of D
+// on the cut gauge field, i.e. D_Omega (+) D_Omega-bar on the common site order.
+dwf_status create_cut(dwf_handle** out, const dwf_params* p, const dwf_box* cut, int ncut, int nrhs_max) {
+    if (out == nullptr || p == nullptr || cut == nullptr || ncut < 1) {
+        set_error("dwf_create_cut: null argument or no box");
+        return DWF_ERR_ARG;
+    }
+    *out = nullptr;
+    dwf_handle* h = nullptr;
+    DWF_TRY(create(&h, p, nullptr, 0, nrhs_max));   // validates the lattice
+    const int* L = h->p.dims;
+    auto fail = [&](dwf_status st) {
+        destroy(h);
+        return st;
+    };
+    for (int i = 0; i < ncut; ++i)
+        for (int mu = 0; mu < 4; ++mu)
+            if (cut[i].extent[mu] < 1 || cut[i].extent[mu] > L[mu]) {
+                set_error("dwf_create_cut: box %d extent[%d] = %d outside [1, %d]", i, mu, cut[i].extent[mu], L[mu]);
+                return fail(DWF_ERR_ARG);
+            }
+    // domain of every site: the box holding it, -1 for the rest; boxes must not overlap
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    std::vector<int> dom(V, -1);
+    for (int64_t g = 0; g < V; ++g) {
+        const int x[4] = {(int)(g % L[0]), (int)((g / L[0]) % L[1]), (int)((g / ((int64_t)L[0] * L[1])) % L[2]),
+                          (int)(g / ((int64_t)L[0] * L[1] * L[2]))};
+        for (int i = 0; i < ncut; ++i) {
+            bool in = true;
+            for (int mu = 0; mu < 4 && in; ++mu) {
+                const int o = ((cut[i].origin[mu] % L[mu]) + L[mu]) % L[mu];
+                in = ((x[mu] - o + L[mu]) % L[mu]) < cut[i].extent[mu];
+            }
+            if (!in) continue;
+            if (dom[g] >= 0) {
+                set_error("dwf_create_cut: boxes %d and %d overlap", dom[g], i);
+                return fail(DWF_ERR_ARG);
+            }
+            dom[g] = i;
+        }
+    }
+    for (int q = 0; q < 2; ++q) {
+        const int64_t n = h->nsite[q] * 8;
+        std::vector<int64_t> lsrc(n);
+        if (cudaMemcpy(lsrc.data(), h->d_link_src[q], n * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("dwf_create_cut: reading the link table failed");
+            return fail(DWF_ERR_CUDA);
+        }
+        for (int64_t e = 0; e < n; ++e) {
+            if (lsrc[e] < 0) continue;
+            const int64_t g = lsrc[e] / 4;   // the link U_mu(g) joins g and g + mu
+            const int mu = (int)(lsrc[e] % 4);
+            int x[4] = {(int)(g % L[0]), (int)((g / L[0]) % L[1]), (int)((g / ((int64_t)L[0] * L[1])) % L[2]),
+                        (int)(g / ((int64_t)L[0] * L[1] * L[2]))};
+            x[mu] = (x[mu] + 1) % L[mu];
+            const int64_t gn = x[0] + (int64_t)L[0] * (x[1] + (int64_t)L[1] * (x[2] + (int64_t)L[2] * x[3]));
+            if (dom[g] != dom[gn]) lsrc[e] = -1;
+        }
+        const dwf_status st = h2d(h->d_link_src[q], lsrc.data(), n * sizeof(int64_t));
+        if (st != DWF_OK) return fail(st);
+    }
+    h->cut.assign(cut, cut + ncut);
+    *out = h;
+    return DWF_OK;
+}
+
 dwf_status destroy(dwf_handle* h) {
     if (h == nullptr) return DWF_OK;
     for (int q = 0; q < 2; ++q) {

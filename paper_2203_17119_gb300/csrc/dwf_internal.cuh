@@ -135,6 +135,9 @@ struct dwf_handle {
     int nbox = 1;                 // whole lattice = one box
     bool dirichlet = false;
     std::vector<dwf_box> boxes;
+    // whole-lattice handle of D_dirichlet: the links between different
+    // domains (each box, and the rest of the lattice) are left out
+    std::vector<dwf_box> cut;
     int nrhs_max = 1;
     int device = 0;
     int64_t nsite[2] = {0, 0};
@@ -258,9 +261,23 @@ dwf_status boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, const
 dwf_status force_bilinear(dwf_handle* h, double* out, const void* X, const void* Y, dwf_prec prec, int nrhs,
                           const dwf_box* active, int accumulate, cudaStream_t s);
 dwf_status zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, double* residues, double* delta);
+// Jacobi sn, cn (parameter m, complementary m1 = 1 - m passed exactly) and K(m)
+// by the arithmetic-geometric mean; any output may be null.
+void jacobi_sn_cn(double u, double m, double m1, double* sn, double* cn, double* K);
+dwf_status rational_power(double alpha, int n, double lo, double hi, double* a0, double* shifts,
+                          double* residues, double* delta);
 dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a0, const double* shifts,
                           const double* residues, int n, int nrhs, const dwf_solver_params* sp,
                           dwf_solver_stats* stats, cudaStream_t s);
+dwf_status one_flavour_action(dwf_handle* h, dwf_handle* hd, const double* phi, int nrhs, const dwf_rational* r1,
+                              const dwf_rational* r2, const dwf_solver_params* sp, double* S,
+                              dwf_solver_stats* stats, cudaStream_t s);
+dwf_status one_flavour_force(dwf_handle* h, dwf_handle* hd, double* out, const double* phi, int nrhs,
+                             const dwf_rational* r1, const dwf_rational* r2, const dwf_box* active, int accumulate,
+                             const dwf_solver_params* sp, dwf_solver_stats* stats, cudaStream_t s);
+dwf_status one_flavour_heatbath(dwf_handle* h, dwf_handle* hd, double* phi, const double* eta, int nrhs,
+                                const dwf_rational* q1, const dwf_rational* q2, const dwf_solver_params* sp,
+                                dwf_solver_stats* stats, cudaStream_t s);
 dwf_status multishift_solve(dwf_handle* h, double* x, const double* b, const double* shifts,
                             int nshift, int nrhs, const dwf_solver_params* sp,
                             dwf_solver_stats* stats, cudaStream_t s);
@@ -331,6 +348,7 @@ int tile_for(dwf_handle* h, int nrhs);
 dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, int nbox,
                   int nrhs_max);
 dwf_status destroy(dwf_handle* h);
+dwf_status create_cut(dwf_handle** out, const dwf_params* p, const dwf_box* cut, int ncut, int nrhs_max);
 dwf_status set_gauge(dwf_handle* h, const double* U, cudaStream_t s);
 dwf_status pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_prec prec,
                 cudaStream_t s);

@@ -411,7 +411,7 @@ dwf_status rational_apply(dwf_handle* h, double* out, const double* in, double a
 // geometric grid).  Jacobi sn, cn and K by the arithmetic-geometric-mean
 // (descending Landen) sequence, with the complementary parameter passed
 // exactly (m1 = 1/b) so nothing cancels as m' -> 1.
-static void jacobi_agm(double u, double m, double m1, double* sn, double* cn, double* K) {
+void jacobi_sn_cn(double u, double m, double m1, double* sn, double* cn, double* K) {
     double a[64], c[64];
     a[0] = 1.0;
     c[0] = std::sqrt(m);
@@ -438,11 +438,11 @@ dwf_status zolotarev_inv_sqrt(int n, double lo, double hi, double* shifts, doubl
     }
     const double b = hi / lo, m1 = 1.0 / b, m = 1.0 - m1;
     double Kp = 0.0;
-    jacobi_agm(0.0, m, m1, nullptr, nullptr, &Kp);
+    jacobi_sn_cn(0.0, m, m1, nullptr, nullptr, &Kp);
     std::vector<double> c(2 * n);   // c[l], l = 1 .. 2n - 1
     for (int l = 1; l < 2 * n; ++l) {
         double sn = 0.0, cn = 1.0;
-        jacobi_agm(l * Kp / (2.0 * n), m, m1, &sn, &cn, nullptr);
+        jacobi_sn_cn(l * Kp / (2.0 * n), m, m1, &sn, &cn, nullptr);
         c[l] = sn * sn / (cn * cn);
     }
     // d0: centre sqrt(y) r(y) between its extremes on [1, b]

@@ -172,6 +172,11 @@ std::string tuning_key(const dwf_handle* h, int nrhs, int prec) {
         }
     else
         k += "whole";
+    for (const dwf_box& b : h->cut) {
+        snprintf(buf, sizeof(buf), "%scut%d,%d,%d,%d:%d,%d,%d,%d", &b == &h->cut[0] ? "/" : ";", b.origin[0],
+                 b.origin[1], b.origin[2], b.origin[3], b.extent[0], b.extent[1], b.extent[2], b.extent[3]);
+        k += buf;
+    }
     snprintf(buf, sizeof(buf), "|p%d|n%d", prec, nrhs);
     return k + buf;
 }

@@ -41,6 +41,11 @@ class Box(C.Structure):
     _fields_ = [("origin", C.c_int * 4), ("extent", C.c_int * 4)]
 
 
+class Rational(C.Structure):
+    _fields_ = [("a0", C.c_double), ("shifts", C.POINTER(C.c_double)), ("residues", C.POINTER(C.c_double)),
+                ("n", C.c_int)]
+
+
 class SolverParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("delta", C.c_double),
                 ("restart", C.c_int), ("use_x0", C.c_int), ("inner_prec", C.c_int),
@@ -65,6 +70,13 @@ def signatures():
     vp, i, d = C.c_void_p, C.c_int, C.c_double
     return {
         "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
+        "dwf_create_cut": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
+        "dwf_one_flavour_action": [vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational), C.POINTER(SolverParams),
+                                   C.POINTER(C.c_double), C.POINTER(SolverStats), vp],
+        "dwf_one_flavour_force": [vp, vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational), C.POINTER(Box), i,
+                                  C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
+        "dwf_one_flavour_heatbath": [vp, vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational),
+                                     C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
         "dwf_destroy": [vp],
         "dwf_domain_sites": [vp, i, C.POINTER(C.c_int64)],
         "dwf_box_sites": [vp, i, i, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -96,6 +108,8 @@ def signatures():
         "dwf_force": [vp, vp, vp, vp, i, i, C.POINTER(Box), i, vp],
         "dwf_zolotarev_inv_sqrt": [i, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)],
+        "dwf_rational_power": [C.c_double, i, C.c_double, C.c_double, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "dwf_rational_apply": [vp, vp, vp, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), i, i,
                                C.POINTER(SolverParams), C.POINTER(SolverStats), vp],
         "dwf_chebyshev_filter": [vp, vp, vp, i, C.c_double, C.c_double, i, i, vp],
@@ -204,23 +218,45 @@ def zolotarev_inv_sqrt(n, lo, hi):
     return list(sh), list(rs), dl.value
 
 
+def rational_power(alpha, n, lo, hi):
+    """Best relative type (n, n) approximation of x**alpha on [lo, hi] in
+    partial fractions: (a0, shifts, residues, delta)."""
+    a0 = C.c_double()
+    sh = (C.c_double * n)()
+    rs = (C.c_double * n)()
+    dl = C.c_double()
+    _check(lib().dwf_rational_power(float(alpha), int(n), float(lo), float(hi), C.byref(a0), sh, rs,
+                                    C.byref(dl)))
+    return a0.value, list(sh), list(rs), dl.value
+
+
 class Handle:
     """A ``dwf_handle``: the whole lattice (``boxes=None``) or the Dirichlet
     blocks of a list of boxes ((origin[4], extent[4]) in x, y, z, t order)."""
 
-    def __init__(self, dims, Ls, action: Action, boxes=None, nrhs_max=1):
+    def __init__(self, dims, Ls, action: Action, boxes=None, nrhs_max=1, cut=None):
+        """``cut``: a list of boxes making this the whole-lattice handle of
+        D_dirichlet (the links between those domains and the rest left out,
+        ``dwf_create_cut``); not together with ``boxes``."""
         self.dims = tuple(int(d) for d in dims)
         self.Ls = int(Ls)
         self.action = action
         self.nrhs_max = int(nrhs_max)
         self.boxes = [tuple(map(tuple, b)) for b in boxes] if boxes else []
+        self.cut = [tuple(map(tuple, b)) for b in cut] if cut else []
+        if self.boxes and self.cut:
+            raise ValueError("a handle has either Dirichlet boxes or cut domains")
         p = Params((C.c_int * 4)(*self.dims), self.Ls, action.M5, action.mf, action.b5, action.c5)
-        nb = len(self.boxes)
+        lst = self.boxes or self.cut
+        nb = len(lst)
         arr = (Box * max(nb, 1))()
-        for k, (o, e) in enumerate(self.boxes):
+        for k, (o, e) in enumerate(lst):
             arr[k] = Box((C.c_int * 4)(*o), (C.c_int * 4)(*e))
         h = C.c_void_p()
-        _check(lib().dwf_create(C.byref(h), C.byref(p), arr if nb else None, nb, self.nrhs_max))
+        if self.cut:
+            _check(lib().dwf_create_cut(C.byref(h), C.byref(p), arr, nb, self.nrhs_max))
+        else:
+            _check(lib().dwf_create(C.byref(h), C.byref(p), arr if nb else None, nb, self.nrhs_max))
         self._h = h
         n0, n1 = C.c_int64(), C.c_int64()
         _check(lib().dwf_domain_sites(h, 0, C.byref(n0)))
@@ -461,6 +497,53 @@ class Handle:
                                       _stream(stream))
         _check(rc)
         return [[st[k * nsys + i].as_dict() for i in range(nsys)] for k in range(n)], rc
+
+    # ------------------------------------------- one-flavour DD-RHMC term
+    @staticmethod
+    def _rational(r):
+        a0, shifts, residues = r
+        n = len(shifts)
+        sh = (C.c_double * n)(*[float(v) for v in shifts])
+        rs = (C.c_double * n)(*[float(v) for v in residues])
+        return Rational(float(a0), sh, rs, n), (sh, rs)
+
+    def one_flavour_action(self, hd, phi, r1, r2, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64,
+                           stream=None):
+        """S[r] = phi_r^+ r1(A_d) r2(A) r1(A_d) phi_r with A of this handle (D)
+        and A_d of ``hd`` (the cut handle of D_dirichlet); r1, r2 = (a0,
+        shifts, residues).  Returns (list of S, stats dicts)."""
+        R1, keep1 = self._rational(r1)
+        R2, keep2 = self._rational(r2)
+        sp = SolverParams(tol, maxiter, 0.0, 0, 0, inner, 0.0, 0, None, 0, 0)
+        st = (SolverStats * ((R1.n + R2.n) * nrhs))()
+        S = (C.c_double * nrhs)()
+        _check(lib().dwf_one_flavour_action(self._h, hd._h, _ptr(phi), nrhs, C.byref(R1), C.byref(R2), C.byref(sp),
+                                            S, st, _stream(stream)))
+        return list(S), [s.as_dict() for s in st]
+
+    def one_flavour_force(self, hd, out, phi, r1, r2, nrhs=1, active=None, accumulate=False, tol=1e-10,
+                          maxiter=100000, inner=FP64, stream=None):
+        """out[lex, mu] = link force of the one-flavour term (summed over
+        right-hand sides); returns the stats dicts of the three multi-shift solves."""
+        R1, keep1 = self._rational(r1)
+        R2, keep2 = self._rational(r2)
+        sp = SolverParams(tol, maxiter, 0.0, 0, 0, inner, 0.0, 0, None, 0, 0)
+        st = (SolverStats * ((2 * R1.n + R2.n) * nrhs))()
+        box = C.byref(self._box(active)) if active is not None else None
+        _check(lib().dwf_one_flavour_force(self._h, hd._h, _ptr(out), _ptr(phi), nrhs, C.byref(R1), C.byref(R2),
+                                           box, int(accumulate), C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
+
+    def one_flavour_heatbath(self, hd, phi, eta, q1, q2, nrhs=1, tol=1e-10, maxiter=100000, inner=FP64,
+                             stream=None):
+        """phi = q1(A_d) q2(A) eta (q1 ~ x^-1/4, q2 ~ x^1/4); returns stats dicts."""
+        Q1, keep1 = self._rational(q1)
+        Q2, keep2 = self._rational(q2)
+        sp = SolverParams(tol, maxiter, 0.0, 0, 0, inner, 0.0, 0, None, 0, 0)
+        st = (SolverStats * ((Q1.n + Q2.n) * nrhs))()
+        _check(lib().dwf_one_flavour_heatbath(self._h, hd._h, _ptr(phi), _ptr(eta), nrhs, C.byref(Q1), C.byref(Q2),
+                                              C.byref(sp), st, _stream(stream)))
+        return [s.as_dict() for s in st]
 
     def chebyshev_filter(self, out, inp, order, lo, hi, prec=FP64, nrhs=1, stream=None):
         """out = T_order(z(A)) in, A = M_pc^+ M_pc, z(lam) = (hi + lo - 2 lam)/(hi - lo)."""

@@ -52,3 +52,22 @@ def test_bad_arguments():
         zolotarev_inv_sqrt(0, 1.0, 2.0)
     with pytest.raises(ValueError):
         zolotarev_inv_sqrt(4, 2.0, 1.0)
+
+
+@pytest.mark.parametrize("n,lo,hi", [(3, 1e-2, 10.0), (8, 1e-4, 50.0), (12, 1e-5, 1e2)])
+def test_type_nn_equioscillation(n, lo, hi):
+    """Type (n, n): 2n + 2 alternating extrema of equal size (Chebyshev's
+    characterisation of the best approximation), a0 > 0, positive residues
+    and shifts, and a smaller error than type (n - 1, n) with the same poles
+    count (one more free parameter)."""
+    from oracle.rational import zolotarev_inv_sqrt_nn
+    a0, shifts, res, delta = zolotarev_inv_sqrt_nn(n, lo, hi)
+    x = np.geomspace(lo, hi, 400001)
+    err = np.sqrt(x) * partial_fraction_eval(x, shifts, res, a0) - 1.0
+    ext = _extrema(err)
+    assert len(ext) == 2 * n + 2
+    assert np.all(np.sign(ext[1:]) == -np.sign(ext[:-1]))
+    assert np.allclose(np.abs(ext), delta, rtol=1e-3)
+    assert np.abs(err).max() <= delta * (1 + 1e-6)
+    assert a0 > 0 and np.all(shifts > 0) and np.all(res > 0)
+    assert delta < zolotarev_inv_sqrt(n, lo, hi)[2]

@@ -38,3 +38,83 @@ def test_bad_arguments():
         G.zolotarev_inv_sqrt(0, 1.0, 2.0)
     with pytest.raises(G.DWFError):
         G.zolotarev_inv_sqrt(4, 2.0, 1.0)
+
+
+def _alternation(err):
+    """Values at the alternating extrema of err on its grid (endpoints
+    included; runs of one sign reduced to their largest member)."""
+    d = np.diff(err)
+    idx = [0] + [i for i in range(1, len(err) - 1) if d[i - 1] * d[i] <= 0] + [len(err) - 1]
+    out = []
+    for v in err[idx]:
+        if out and np.sign(v) == np.sign(out[-1]):
+            out[-1] = v if abs(v) > abs(out[-1]) else out[-1]
+        else:
+            out.append(v)
+    return np.array(out)
+
+
+POWER_CASES = [(-0.25, 8, 1e-4, 1.0), (0.25, 8, 1e-4, 1.0), (-0.25, 16, 1e-6, 10.0), (0.25, 16, 1e-6, 10.0),
+               (-0.5, 12, 1e-5, 1e2), (-0.75, 10, 1e-3, 1.0), (0.25, 24, 1e-8, 1.0)]
+
+
+@pytest.mark.parametrize("alpha,n,lo,hi", POWER_CASES)
+def test_rational_power_is_the_best_approximation(alpha, n, lo, hi):
+    """dwf_rational_power against Chebyshev's characterisation: the relative
+    error r(x)/x^alpha - 1, evaluated here in numpy, stays within the returned
+    delta and reaches it with alternating signs at 2n + 2 points, which makes
+    r the unique best type (n, n) approximation (a plausible slip -- a wrong
+    residue, a dropped pole, a shift off by a factor -- breaks the equal
+    ripple); shifts > 0, residues of the sign of -alpha."""
+    G = _lib()
+    a0, sh, rs, delta = G.rational_power(alpha, n, lo, hi)
+    sh, rs = np.array(sh), np.array(rs)
+    x = np.geomspace(lo, hi, 400001)
+    err = partial_fraction_eval(x, sh, rs, a0) * x ** (-alpha) - 1.0
+    assert np.abs(err).max() <= delta * (1 + 1e-5)
+    alt = _alternation(err)
+    assert len(alt) >= 2 * n + 2
+    big = np.abs(alt) >= delta * (1 - 1e-3)
+    assert big.sum() >= 2 * n + 2, np.abs(alt) / delta
+    assert np.all(sh > 0)
+    assert np.all(np.sign(rs) == -np.sign(alpha)) and a0 > 0
+
+
+@pytest.mark.parametrize("n,lo,hi", [(6, 1e-3, 10.0), (12, 1e-5, 1e2)])
+def test_rational_power_inverse_sqrt_is_zolotarev(n, lo, hi):
+    """At alpha = -1/2 the best type (n, n) fit is Zolotarev's closed form
+    (the oracle's, scipy's elliptic functions): same coefficients."""
+    from oracle.rational import zolotarev_inv_sqrt_nn
+    G = _lib()
+    a0, sh, rs, delta = G.rational_power(-0.5, n, lo, hi)
+    oa0, osh, ors, odelta = zolotarev_inv_sqrt_nn(n, lo, hi)
+    order = np.argsort(sh)
+    assert a0 == pytest.approx(oa0, rel=1e-6)
+    assert np.allclose(np.array(sh)[order], np.sort(osh), rtol=1e-6, atol=0)
+    assert np.allclose(np.array(rs)[order], np.array(ors)[np.argsort(osh)], rtol=1e-5, atol=0)
+    assert delta == pytest.approx(odelta, rel=1e-3)
+
+
+def test_rational_power_scale_covariance_and_reciprocity():
+    """x -> c x maps the best fit on [lo, hi] to the one on [c lo, c hi]
+    (shifts * c, residues * c^(1 + alpha), a0 * c^alpha); the fits of x^(1/4)
+    and x^(-1/4) have the same error to first order (1/r of one is within
+    delta / (1 - delta) of the other power)."""
+    G = _lib()
+    a0, sh, rs, d = G.rational_power(0.25, 10, 1e-4, 1.0)
+    c = 37.0
+    b0, th, ts, e = G.rational_power(0.25, 10, c * 1e-4, c)
+    assert b0 == pytest.approx(a0 * c ** 0.25, rel=1e-6)
+    assert np.allclose(np.sort(th), c * np.sort(sh), rtol=1e-6)
+    assert np.allclose(np.array(ts)[np.argsort(th)], c ** 1.25 * np.array(rs)[np.argsort(sh)], rtol=1e-5)
+    assert e == pytest.approx(d, rel=1e-4)
+    dm = G.rational_power(-0.25, 10, 1e-4, 1.0)[3]
+    assert abs(dm - d) <= 4 * d * d + 1e-3 * d
+
+
+def test_rational_power_bad_arguments():
+    G = _lib()
+    for args in ((0.0, 4, 1.0, 2.0), (1.0, 4, 1.0, 2.0), (0.25, 0, 1.0, 2.0), (0.25, 4, 2.0, 1.0),
+                 (0.25, 4, 0.0, 1.0), (-0.5, 49, 1.0, 2.0)):
+        with pytest.raises(G.DWFError):
+            G.rational_power(*args)
