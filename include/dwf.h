@@ -337,6 +337,19 @@ dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk);
 dwf_status dwf_get_tuning(const dwf_handle* h, int nrhs, int* tile_sites, int* lanes_per_thread,
                           int* chunk, int* tensor_cores);
 
+/* The debug build (libdwf_debug.so, compiled with -DDWF_DEBUG): every entry
+ * point checks, on the host and before launching anything, that each caller
+ * buffer it reads or writes lies inside one device allocation of the current
+ * context (the allocation range the driver reports for the pointer, so with a
+ * caching allocator only overruns past its segment are seen), and the handle's
+ * neighbour and link tables are range-checked when built; a failure returns
+ * DWF_ERR_ARG naming the buffer.  *on = 1 in the debug build, 0 otherwise. */
+dwf_status dwf_debug_build(int* on);
+/* Debug build: DWF_OK if [p, p + bytes) lies inside one device allocation,
+ * DWF_ERR_ARG otherwise (or for host memory, NULL or bytes = 0).  The release
+ * build returns DWF_ERR_UNSUPPORTED. */
+dwf_status dwf_check_range(const void* p, size_t bytes);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);

@@ -88,6 +88,7 @@ dwf_status dwf_set_gauge(dwf_handle* h, const double* U, void* stream) {
         set_error("dwf_set_gauge: null gauge pointer");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_set_gauge", {U, link_field_bytes(h), "U"});
     return dwf::set_gauge(h, U, (cudaStream_t)stream);
 }
 
@@ -98,6 +99,8 @@ dwf_status dwf_pack(dwf_handle* h, void* dst, const double* src, int nrhs, dwf_p
         set_error("dwf_pack: bad argument");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_pack", {dst, field_bytes(h, 2, prec, nrhs), "dst"},
+                     {src, field_bytes(h, 2, DWF_FP64, nrhs), "src"});
     return dwf::pack(h, dst, src, nrhs, prec, (cudaStream_t)stream);
 }
 
@@ -108,6 +111,8 @@ dwf_status dwf_unpack(dwf_handle* h, double* dst, const void* src, int nrhs, dwf
         set_error("dwf_unpack: bad argument");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_unpack", {dst, field_bytes(h, 2, DWF_FP64, nrhs), "dst"},
+                     {src, field_bytes(h, 2, prec, nrhs), "src"});
     return dwf::unpack(h, dst, src, nrhs, prec, (cudaStream_t)stream);
 }
 
@@ -119,6 +124,8 @@ dwf_status dwf_dslash_eo(dwf_handle* h, void* out, const void* in, int out_parit
         set_error("dwf_dslash_eo: out_parity must be 0 or 1");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_dslash_eo", {out, field_bytes(h, out_parity, prec, nrhs), "out"},
+                     {in, field_bytes(h, 1 - out_parity, prec, nrhs), "in"});
     return op_dslash_eo(h, out, in, out_parity, dagger ? 1 : 0, prec, nrhs, h->d_tmp,
                         (cudaStream_t)stream);
 }
@@ -131,6 +138,8 @@ dwf_status dwf_hop(dwf_handle* h, void* out, const void* in, int out_parity, int
         set_error("dwf_hop: out_parity must be 0 or 1");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_hop", {out, field_bytes(h, out_parity, prec, nrhs), "out"},
+                     {in, field_bytes(h, 1 - out_parity, prec, nrhs), "in"});
     return op_hop(h, out, in, out_parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0, nullptr, nullptr,
                   (cudaStream_t)stream);
 }
@@ -342,6 +351,8 @@ dwf_status dwf_mooee(dwf_handle* h, void* out, const void* in, int parity, int d
         set_error("dwf_mooee: parity must be 0 or 1");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_mooee", {out, field_bytes(h, parity, prec, nrhs), "out"},
+                     {in, field_bytes(h, parity, prec, nrhs), "in"});
     return op_local(h, L_MOOEE, out, in, nullptr, parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0,
                     nullptr, (cudaStream_t)stream);
 }
@@ -354,6 +365,8 @@ dwf_status dwf_mooee_inv(dwf_handle* h, void* out, const void* in, int parity, i
         set_error("dwf_mooee_inv: parity must be 0 or 1");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_mooee_inv", {out, field_bytes(h, parity, prec, nrhs), "out"},
+                     {in, field_bytes(h, parity, prec, nrhs), "in"});
     return op_local(h, L_MINV, out, in, nullptr, parity, dagger ? 1 : 0, prec, prec, prec, nrhs, 1.0,
                     nullptr, (cudaStream_t)stream);
 }
@@ -362,6 +375,8 @@ dwf_status dwf_mpc(dwf_handle* h, void* out, const void* in, int dagger, dwf_pre
                    void* stream) {
     DWF_RANGE("dwf_mpc");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_mpc"));
+    DWF_CHECK_RANGES("dwf_mpc", {out, field_bytes(h, 1, prec, nrhs), "out"},
+                     {in, field_bytes(h, 1, prec, nrhs), "in"});
     return op_mpc(h, out, in, dagger ? 1 : 0, prec, prec, nrhs, h->d_tmp, h->d_tmp2, nullptr, nullptr,
                   (cudaStream_t)stream);
 }
@@ -370,6 +385,8 @@ dwf_status dwf_apply_d(dwf_handle* h, void* out, const void* in, int dagger, dwf
                        void* stream) {
     DWF_RANGE("dwf_apply_d");
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_apply_d"));
+    DWF_CHECK_RANGES("dwf_apply_d", {out, field_bytes(h, 2, prec, nrhs), "out"},
+                     {in, field_bytes(h, 2, prec, nrhs), "in"});
     return op_apply_d(h, out, in, dagger ? 1 : 0, prec, nrhs, h->d_tmp, (cudaStream_t)stream);
 }
 
@@ -382,6 +399,8 @@ dwf_status dwf_dirichlet_block(dwf_handle* h, void* out, const void* in, int dag
         return DWF_ERR_ARG;
     }
     DWF_TRY(check_op(h, out, in, prec, nrhs, "dwf_dirichlet_block"));
+    DWF_CHECK_RANGES("dwf_dirichlet_block", {out, field_bytes(h, 2, prec, nrhs), "out"},
+                     {in, field_bytes(h, 2, prec, nrhs), "in"});
     return op_apply_d(h, out, in, dagger ? 1 : 0, prec, nrhs, h->d_tmp, (cudaStream_t)stream);
 }
 
@@ -397,6 +416,8 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
         set_error("dwf_cgne_solve: x and b must not alias");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_cgne_solve", {x, field_bytes(h, 2, DWF_FP64, nrhs), "x"},
+                     {b, field_bytes(h, 2, DWF_FP64, nrhs), "b"});
     return cgne_solve(h, x, b, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
@@ -408,6 +429,8 @@ dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dw
         set_error("dwf_gcr_solve: x and b must not alias");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_gcr_solve", {x, field_bytes(h, 2, DWF_FP64, nrhs), "x"},
+                     {b, field_bytes(h, 2, DWF_FP64, nrhs), "b"});
     return gcr_solve(h, x, b, nrhs, K, nullptr, sp, stats, (cudaStream_t)stream);
 }
 
@@ -426,6 +449,8 @@ dwf_status dwf_gcr_solve_mg(dwf_handle* h, double* x, const double* b, dwf_mg* m
         set_error("dwf_gcr_solve_mg: x and b must not alias");
         return DWF_ERR_ARG;
     }
+    DWF_CHECK_RANGES("dwf_gcr_solve_mg", {x, field_bytes(h, 2, DWF_FP64, 1), "x"},
+                     {b, field_bytes(h, 2, DWF_FP64, 1), "b"});
     return gcr_solve(h, x, b, 1, nullptr, mg, sp, stats, (cudaStream_t)stream);
 }
 
@@ -434,6 +459,9 @@ dwf_status dwf_multishift_solve(dwf_handle* h, double* x, const double* b, const
                                 dwf_solver_stats* stats, void* stream) {
     DWF_RANGE("dwf_multishift_solve");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_multishift_solve",
+                     {x, nshift > 0 ? (size_t)nshift * field_bytes(h, 1, DWF_FP64, nrhs) : 0, "x"},
+                     {b, field_bytes(h, 1, DWF_FP64, nrhs), "b"});
     return multishift_solve(h, x, b, shifts, nshift, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
@@ -441,6 +469,8 @@ dwf_status dwf_boundary_project(dwf_handle* h, const dwf_box* omega, double* out
                                 int nrhs, void* stream) {
     DWF_RANGE("dwf_boundary_project");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_boundary_project", {out, field_bytes(h, 2, DWF_FP64, nrhs), "out"},
+                     {in, field_bytes(h, 2, DWF_FP64, nrhs), "in"});
     return boundary_project(h, omega, out, in, nrhs, (cudaStream_t)stream);
 }
 
@@ -449,6 +479,8 @@ dwf_status dwf_boundary_rinv(dwf_handle* h, const dwf_box* omega, double* out, c
                              void* stream) {
     DWF_RANGE("dwf_boundary_rinv");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_boundary_rinv", {out, field_bytes(h, 2, DWF_FP64, nrhs), "out"},
+                     {in, field_bytes(h, 2, DWF_FP64, nrhs), "in"});
     return boundary_rinv(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
@@ -456,6 +488,8 @@ dwf_status dwf_boundary_r(dwf_handle* h, const dwf_box* omega, double* out, cons
                           const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream) {
     DWF_RANGE("dwf_boundary_r");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_boundary_r", {out, field_bytes(h, 2, DWF_FP64, nrhs), "out"},
+                     {in, field_bytes(h, 2, DWF_FP64, nrhs), "in"});
     return boundary_r(h, omega, out, in, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
@@ -465,6 +499,8 @@ dwf_status dwf_boundary_ratio_force(dwf_handle* h_light, dwf_handle* h_pv, const
     DWF_RANGE("dwf_boundary_ratio_force");
     DWF_TRY(check_handle(h_light));
     DWF_TRY(check_handle(h_pv));
+    DWF_CHECK_RANGES("dwf_boundary_ratio_force", {out, link_field_bytes(h_light), "out"},
+                     {phi, field_bytes(h_light, 2, DWF_FP64, nrhs), "phi"});
     return boundary_ratio_force(h_light, h_pv, omega, out, phi, nrhs, active, accumulate, sp, stats,
                                 (cudaStream_t)stream);
 }
@@ -474,6 +510,8 @@ dwf_status dwf_boundary_force(dwf_handle* h, const dwf_box* omega, double* out, 
                               dwf_solver_stats* stats, void* stream) {
     DWF_RANGE("dwf_boundary_force");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_boundary_force", {out, link_field_bytes(h), "out"},
+                     {phi, field_bytes(h, 2, DWF_FP64, nrhs), "phi"});
     return boundary_force(h, omega, out, phi, nrhs, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
 
@@ -492,6 +530,7 @@ dwf_status dwf_one_flavour_action(dwf_handle* h, dwf_handle* hd, const double* p
     DWF_RANGE("dwf_one_flavour_action");
     DWF_TRY(check_handle(h));
     DWF_TRY(check_handle(hd));
+    DWF_CHECK_RANGES("dwf_one_flavour_action", {phi, field_bytes(h, 1, DWF_FP64, nrhs), "phi"});
     return one_flavour_action(h, hd, phi, nrhs, r1, r2, sp, S, stats, (cudaStream_t)stream);
 }
 
@@ -502,6 +541,8 @@ dwf_status dwf_one_flavour_force(dwf_handle* h, dwf_handle* hd, double* out, con
     DWF_RANGE("dwf_one_flavour_force");
     DWF_TRY(check_handle(h));
     DWF_TRY(check_handle(hd));
+    DWF_CHECK_RANGES("dwf_one_flavour_force", {out, link_field_bytes(h), "out"},
+                     {phi, field_bytes(h, 1, DWF_FP64, nrhs), "phi"});
     return one_flavour_force(h, hd, out, phi, nrhs, r1, r2, active, accumulate, sp, stats, (cudaStream_t)stream);
 }
 
@@ -511,6 +552,8 @@ dwf_status dwf_one_flavour_heatbath(dwf_handle* h, dwf_handle* hd, double* phi, 
     DWF_RANGE("dwf_one_flavour_heatbath");
     DWF_TRY(check_handle(h));
     DWF_TRY(check_handle(hd));
+    DWF_CHECK_RANGES("dwf_one_flavour_heatbath", {phi, field_bytes(h, 1, DWF_FP64, nrhs), "phi"},
+                     {eta, field_bytes(h, 1, DWF_FP64, nrhs), "eta"});
     return one_flavour_heatbath(h, hd, phi, eta, nrhs, q1, q2, sp, stats, (cudaStream_t)stream);
 }
 
@@ -519,6 +562,8 @@ dwf_status dwf_rational_apply(dwf_handle* h, double* out, const double* in, doub
                               dwf_solver_stats* stats, void* stream) {
     DWF_RANGE("dwf_rational_apply");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_rational_apply", {out, field_bytes(h, 1, DWF_FP64, nrhs), "out"},
+                     {in, field_bytes(h, 1, DWF_FP64, nrhs), "in"});
     return rational_apply(h, out, in, a0, shifts, residues, n, nrhs, sp, stats, (cudaStream_t)stream);
 }
 
@@ -526,6 +571,8 @@ dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int or
                                 dwf_prec prec, int nrhs, void* stream) {
     DWF_RANGE("dwf_chebyshev_filter");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_chebyshev_filter", {out, field_bytes(h, 1, prec, nrhs), "out"},
+                     {in, field_bytes(h, 1, prec, nrhs), "in"});
     return chebyshev_filter(h, out, in, order, lo, hi, prec, nrhs, (cudaStream_t)stream);
 }
 
@@ -533,6 +580,8 @@ dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, d
                      const dwf_box* active, int accumulate, void* stream) {
     DWF_RANGE("dwf_force");
     DWF_TRY(check_handle(h));
+    DWF_CHECK_RANGES("dwf_force", {out, link_field_bytes(h), "out"}, {X, field_bytes(h, 2, prec, nrhs), "X"},
+                     {Y, field_bytes(h, 2, prec, nrhs), "Y"});
     return force_bilinear(h, out, X, Y, prec, nrhs, active, accumulate, (cudaStream_t)stream);
 }
 

@@ -121,6 +121,15 @@ dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
             for (int64_t i = 0; i < cnt; i += T)
                 tl.push_back(make_int4(b, (int)(off + i), (int)std::min<int64_t>(T, cnt - i), 0));
         }
+#ifdef DWF_DEBUG
+        for (const int4& t : tl)
+            if (t.x < 0 || t.x >= h->nbox || t.y < 0 || t.z < 1 || (int64_t)t.y + t.z > h->nsite[p]) {
+                set_error("tile table (debug): tile {%d, %d, %d} outside parity %d's %lld sites", t.x, t.y, t.z, p,
+                          (long long)h->nsite[p]);
+                free_tiles(ts);
+                return DWF_ERR_ARG;
+            }
+#endif
         ts.box_tile_begin[p][h->nbox] = (int)tl.size();
         ts.ntiles[p] = (int)tl.size();
         cudaError_t e = cudaSuccess;
@@ -428,6 +437,18 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
                 lsrc[i * 8 + k] = g * 4 + mu;
             }
         }
+#ifdef DWF_DEBUG
+        // neighbours index the other parity's site list, links the canonical gauge field
+        const int64_t nopp = h->nsite[1 - q], nlink = (int64_t)L[0] * L[1] * L[2] * L[3] * 4;
+        for (int64_t e = 0; e < ns * 8 && st == DWF_OK; ++e)
+            if (nbr[e] < -1 || nbr[e] >= nopp || lsrc[e] < -1 || lsrc[e] >= nlink || (nbr[e] < 0) != (lsrc[e] < 0)) {
+                set_error("dwf_create (debug): table entry %lld of parity %d out of range (neighbour %d of %lld, "
+                          "link %lld of %lld)", (long long)e, q, nbr[e], (long long)nopp, (long long)lsrc[e],
+                          (long long)nlink);
+                st = DWF_ERR_ARG;
+            }
+        if (st != DWF_OK) break;
+#endif
         st = dalloc(&h->d_nbr[q], ns * 8);
         if (st == DWF_OK) st = dalloc(&h->d_link_src[q], ns * 8);
         if (st == DWF_OK) st = dalloc(&h->d_site_box[q], ns);
@@ -549,6 +570,13 @@ dwf_status create_cut(dwf_handle** out, const dwf_params* p, const dwf_box* cut,
             const int64_t gn = x[0] + (int64_t)L[0] * (x[1] + (int64_t)L[1] * (x[2] + (int64_t)L[2] * x[3]));
             if (dom[g] != dom[gn]) lsrc[e] = -1;
         }
+#ifdef DWF_DEBUG
+        for (int64_t e = 0; e < n; ++e)
+            if (lsrc[e] < -1 || lsrc[e] >= 4 * V) {
+                set_error("dwf_create_cut (debug): link table entry %lld out of range", (long long)e);
+                return fail(DWF_ERR_ARG);
+            }
+#endif
         const dwf_status st = h2d(h->d_link_src[q], lsrc.data(), n * sizeof(int64_t));
         if (st != DWF_OK) return fail(st);
     }

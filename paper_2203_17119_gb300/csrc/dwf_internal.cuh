@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <type_traits>
@@ -187,6 +188,28 @@ dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out);
 const TileSet* find_tiles(const dwf_handle* h, int T);
 // A handle is used on the device it was created on: DWF_ERR_ARG otherwise.
 dwf_status check_handle(const dwf_handle* h);
+
+// Byte sizes of the caller's fields: kind 0/1 a cb field of that parity, 2 a
+// full field; 0 for an invalid nrhs or precision.  link_field_bytes: the
+// canonical gauge (or force) array of the whole lattice.
+size_t field_bytes(const dwf_handle* h, int kind, dwf_prec prec, int nrhs);
+size_t link_field_bytes(const dwf_handle* h);
+struct FieldRange {
+    const void* p;
+    size_t bytes;
+    const char* what;
+};
+// DWF_CHECK_RANGES(who, {ptr, bytes, name}, ...): in the DWF_DEBUG build,
+// DWF_ERR_ARG unless every buffer lies inside one device allocation (null
+// pointers and zero sizes are left to the entry point's own checks); nothing
+// in the release build.
+#ifdef DWF_DEBUG
+dwf_status debug_range(const void* p, size_t bytes, const char* who, const char* what);
+dwf_status debug_ranges(const char* who, std::initializer_list<FieldRange> r);
+#define DWF_CHECK_RANGES(who, ...) DWF_TRY(::dwf::debug_ranges((who), {__VA_ARGS__}))
+#else
+#define DWF_CHECK_RANGES(who, ...) do { } while (0)
+#endif
 size_t prec_size(dwf_prec p);   // bytes per real
 // Persistent grid of a kernel: the blocks resident at once on the current
 // device (occupancy and SM count cached per device), at most one per tile.

@@ -16,7 +16,10 @@ from dataclasses import dataclass
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libdwf.so")
+# DWF_DEBUG=1 in the environment loads the debug build (host-side bounds checks
+# of every caller buffer, python -m paper_2203_17119_gb300.build --debug)
+LIB_PATH = (os.path.join(_PKG, "_build_debug", "libdwf_debug.so") if os.environ.get("DWF_DEBUG") == "1"
+            else os.path.join(_PKG, "_build", "libdwf.so"))
 
 FP64, FP32, BF16 = 0, 1, 2
 _DTYPE = {FP64: torch.float64, FP32: torch.float32, BF16: torch.bfloat16}
@@ -71,6 +74,8 @@ def signatures():
     return {
         "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
         "dwf_create_cut": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
+        "dwf_debug_build": [C.POINTER(C.c_int)],
+        "dwf_check_range": [vp, C.c_size_t],
         "dwf_one_flavour_action": [vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational), C.POINTER(SolverParams),
                                    C.POINTER(C.c_double), C.POINTER(SolverStats), vp],
         "dwf_one_flavour_force": [vp, vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational), C.POINTER(Box), i,

@@ -82,3 +82,13 @@ def test_binding_matches_every_prototype():
     assert not missing, missing
     wrong = {n: (len(a), arity[n]) for n, a in sig.items() if len(a) != arity.get(n, -1)}
     assert not wrong, wrong
+
+
+def test_release_build_has_no_debug_checks(libpath):
+    """The release library reports itself as such; dwf_check_range is the
+    debug build's alone."""
+    from paper_2203_17119_gb300 import dwf
+    L = dwf.lib()
+    on = ctypes.c_int(-1)
+    assert L.dwf_debug_build(ctypes.byref(on)) == 0 and on.value == 0
+    assert L.dwf_check_range(None, 8) == 6          # DWF_ERR_UNSUPPORTED
