@@ -388,7 +388,7 @@ def run_ours(args, rank, world):
     except (OSError, ValueError, KeyError):
         pass
     roof = {"bound": "hbm", "kernel": "k_hop<float> (bare Wilson hop, FP32, 32^4 x Ls=16)",
-            "config_tile_lanes_chunk": hop["f32"]["config"],
+            "config_tile_lanes_chunk": hop["f32"]["config"], "tile_order": list(hD.tile_order()),
             "achieved": hop["f32"]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": round(hop["f32"]["gbs"] / peak, 3), "traffic": traffic,
             "algorithmic_bytes_per_launch": hop["f32"]["bytes"],
@@ -579,6 +579,8 @@ def run_hop(args):
         h.set_hop_chunk(nrhs, args.chunk)
     else:
         T = h.autotune(nrhs, prec) if not args.no_autotune else None
+    if args.tile_order:
+        h.set_tile_order(1, *args.tile_order)
     inp = torch.randn(h.cb_shape(1, nrhs), device="cuda").to(G._DTYPE[prec])
     out = h.empty_cb(0, nrhs, prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -603,7 +605,7 @@ def run_hop(args):
     except (OSError, ValueError, KeyError):
         pass
     print(json.dumps({"kernel": "hop", "lattice": [L] * 4, "Ls": Ls, "nrhs": nrhs, "prec": prec_name,
-                      "tile_sites": T, "config": args.hop_config, "tensor_cores": bool(args.tc), "chunk": args.chunk or None, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
+                      "tile_sites": T, "config": args.hop_config, "tensor_cores": bool(args.tc), "chunk": args.chunk or None, "tile_order": args.tile_order, "ms": ms, "tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / peak,
                       "algorithmic_bytes": nbytes}))
 
@@ -1166,6 +1168,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tc", action="store_true", help="--hop bf16: the tensor-core kernel")
     ap.add_argument("--chunk", type=int, default=0, help="--hop: consecutive tiles per CTA")
+    ap.add_argument("--tile-order", nargs=2, type=int, metavar=("BZ", "BT"),
+                    help="--hop: tiles blocked in (z, t) by BZ x BT planes")
     ap.add_argument("--hop-config", nargs=2, type=int, metavar=("TILE", "VL"),
                     help="--hop: fixed sites per tile and lanes per thread instead of autotuning")
     ap.add_argument("--gpus", type=int, default=1)

@@ -277,15 +277,18 @@ dwf_status dwf_cgne_solve(dwf_handle* h, double* x, const double* b, int nrhs,
 /* Autotuner: time the hop kernel for nrhs right-hand sides in precision
  * `prec` over candidate tile sizes (sites per CTA tile: 8..128) and keep the
  * fastest for every later call on this handle with that nrhs (all kernels of
- * an operator chain share one tile table).  Synchronous; uses the handle's
- * scratch fields, so it must not overlap other calls on the handle.
- * tile_sites (nullable) receives the choice. */
+ * an operator chain share one tile table).  On a whole-lattice handle it then
+ * times the chosen configuration with the lexicographic and the 8 x 8 blocked
+ * tile order (dwf_set_tile_order) and keeps the faster for the handle.
+ * Synchronous; uses the handle's scratch fields, so it must not overlap other
+ * calls on the handle.  tile_sites (nullable) receives the choice. */
 dwf_status dwf_autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* tile_sites);
 
 /* Persisted autotuning.  dwf_autotune_save writes every choice dwf_autotune
  * made on this handle to the text file `path`, one line per key
  *   <device name>/<SMs>|<Lx>,<Ly>,<Lz>,<Lt>|<Ls>|<boxes or "whole">|p<prec>|n<nrhs>
- * followed by tile, lanes, tensor-core kernel, chunk and fusion; lines of other keys
+ * followed by tile, lanes, tensor-core kernel, chunk, fusion and the handle's tile
+ * order (order, bz, bt; lines without them load as lexicographic); lines of other keys
  * already in the file are kept.  dwf_autotune_load looks up this handle's key
  * for (nrhs, prec) and, if present (*found = 1), applies it as dwf_set_tile &
  * co. would (building the tile table); a missing file or key leaves the
@@ -330,6 +333,20 @@ dwf_status dwf_get_fusion(const dwf_handle* h, int nrhs, int* fuse);
  * load balance of the last round.  dwf_autotune picks 1 or 8.  Same results.
  * DWF_ERR_ARG unless 1 <= chunk <= 64. */
 dwf_status dwf_set_hop_chunk(dwf_handle* h, int nrhs, int chunk);
+
+/* Order in which every kernel on this handle walks the tiles of a box:
+ * order 0 lexicographic in the site order (the default); order 1 blocked in
+ * (z, t) -- by t / bt, z / bz, then t mod bt, z mod bz, y, x of a tile's first
+ * site -- so that the two uses of a z or t neighbour spinor (as the +mu
+ * neighbour of one plane and the -mu neighbour of the plane two steps on)
+ * are a block's planes apart rather than a whole time slice, for L2 reuse.
+ * Existing tile tables are rewritten in place (same tiles, so captured
+ * graphs stay valid); the call waits for the device and must not overlap
+ * other calls on the handle.  Same results up to the summation order of
+ * per-tile partial norms.  DWF_ERR_ARG unless order is 0 or 1 and bz, bt >= 1. */
+dwf_status dwf_set_tile_order(dwf_handle* h, int order, int bz, int bt);
+/* The handle's tile order (any output may be NULL). */
+dwf_status dwf_get_tile_order(const dwf_handle* h, int* order, int* bz, int* bt);
 
 /* The kernel configuration later calls with this nrhs use (set by
  * dwf_autotune or the dwf_set_* calls; defaults 32 sites, 2 lanes, chunk 1,

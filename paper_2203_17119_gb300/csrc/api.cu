@@ -207,9 +207,10 @@ dwf_status dwf_autotune_save(const dwf_handle* h, const char* path) {
             auto it = m.find(nrhs);
             return it == m.end() ? dflt : it->second;
         };
-        char buf[128];
-        snprintf(buf, sizeof(buf), " %d %d %d %d %d", get(h->tuned_T, 32), get(h->tuned_vl, 2), get(h->tuned_tc, 0),
-                 get(h->tuned_chunk, 1), get(h->tuned_fuse, 0));
+        char buf[160];
+        snprintf(buf, sizeof(buf), " %d %d %d %d %d %d %d %d", get(h->tuned_T, 32), get(h->tuned_vl, 2),
+                 get(h->tuned_tc, 0), get(h->tuned_chunk, 1), get(h->tuned_fuse, 0), h->tile_order, h->order_bz,
+                 h->order_bt);
         if (!lines.count(k)) order.push_back(k);
         lines[k] = k + buf;
     }
@@ -239,17 +240,25 @@ dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec
     if (!f) return DWF_OK;   // no file yet: nothing cached
     const std::string key = tuning_key(h, nrhs, (int)prec);
     char buf[1024];
-    int T = 0, vl = 0, tc = 0, ck = 0, fu = 0;
+    int T = 0, vl = 0, tc = 0, ck = 0, fu = 0, od = 0, bz = 8, bt = 8;
     while (fgets(buf, sizeof(buf), f)) {
         std::string l(buf);
         const size_t sp = l.find(' ');
         if (sp == std::string::npos || l.compare(0, sp, key) != 0 || sp != key.size()) continue;
-        if (sscanf(l.c_str() + sp, "%d %d %d %d %d", &T, &vl, &tc, &ck, &fu) == 5) *found = 1;
+        // tile, lanes, tensor cores, chunk, fusion [, tile order, bz, bt]
+        int o = 0, z = 8, t = 8;
+        const int n = sscanf(l.c_str() + sp, "%d %d %d %d %d %d %d %d", &T, &vl, &tc, &ck, &fu, &o, &z, &t);
+        if (n == 5 || n == 8) {
+            *found = 1;
+            od = n == 8 ? o : 0;
+            bz = n == 8 ? z : 8;
+            bt = n == 8 ? t : 8;
+        }
     }
     fclose(f);
     if (!*found) return DWF_OK;
     if (T < kMinTile || T > 256 || (vl != 1 && vl != 2) || (tc != 0 && tc != 1) || ck < 1 || ck > 64 ||
-        (fu != 0 && fu != 1) ||
+        (fu != 0 && fu != 1) || (od != 0 && od != 1) || bz < 1 || bt < 1 ||
         hop_smem(T, 8, 8, nrhs) > (size_t)kHopMaxSmem) {
         *found = 0;
         set_error("dwf_autotune_load: entry for this handle in %s is out of range", path);
@@ -263,6 +272,7 @@ dwf_status dwf_autotune_load(dwf_handle* h, const char* path, int nrhs, dwf_prec
     h->tuned_chunk[nrhs] = ck;
     h->tuned_fuse[nrhs] = fu;
     h->tuned_prec[nrhs] = (int)prec;
+    if (od != h->tile_order || bz != h->order_bz || bt != h->order_bt) DWF_TRY(set_tile_order(h, od, bz, bt));
     return DWF_OK;
 }
 
@@ -294,6 +304,19 @@ dwf_status dwf_get_fusion(const dwf_handle* h, int nrhs, int* fuse) {
     }
     auto it = h->tuned_fuse.find(nrhs);
     *fuse = it == h->tuned_fuse.end() ? 0 : it->second;
+    return DWF_OK;
+}
+
+dwf_status dwf_set_tile_order(dwf_handle* h, int order, int bz, int bt) {
+    DWF_TRY(check_handle(h));
+    return set_tile_order(h, order, bz, bt);
+}
+
+dwf_status dwf_get_tile_order(const dwf_handle* h, int* order, int* bz, int* bt) {
+    DWF_TRY(check_handle(h));
+    if (order) *order = h->tile_order;
+    if (bz) *bz = h->order_bz;
+    if (bt) *bt = h->order_bt;
     return DWF_OK;
 }
 

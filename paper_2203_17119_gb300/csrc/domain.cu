@@ -103,6 +103,36 @@ static void free_tiles(TileSet& ts) {
     }
 }
 
+// The tiles of parity p for T sites per tile, box by box, and where each box's
+// tiles begin.  Within a box the tiles run in lexicographic site order, or
+// (tile_order 1) blocked in (z, t): by t / bt, z / bz, then t % bt, z % bz, y,
+// x of a tile's first site, so that the two uses of a z or t neighbour row
+// (as the +mu neighbour of one plane, the -mu neighbour of the plane two
+// steps on) lie a block's planes apart instead of a whole time slice.
+static void tile_list(const dwf_handle* h, int T, int p, std::vector<int4>& tl, std::vector<int>& begin) {
+    tl.clear();
+    begin.assign(h->nbox + 1, 0);
+    for (int b = 0; b < h->nbox; ++b) {
+        begin[b] = (int)tl.size();
+        const int64_t off = h->box_off[p][b], cnt = h->box_cnt[p][b];
+        for (int64_t i = 0; i < cnt; i += T)
+            tl.push_back(make_int4(b, (int)(off + i), (int)std::min<int64_t>(T, cnt - i), 0));
+        if (h->tile_order == 1 && !h->site_local_host[p].empty()) {
+            const int* e = h->boxes[b].extent;
+            const int bz = h->order_bz, bt = h->order_bt;
+            auto key = [&](const int4& t) {
+                const int64_t l = h->site_local_host[p][t.y];
+                const int64_t x = l % e[0], y = (l / e[0]) % e[1], z = (l / ((int64_t)e[0] * e[1])) % e[2],
+                              tt = l / ((int64_t)e[0] * e[1] * e[2]);
+                return std::make_tuple(tt / bt, z / bz, tt % bt, z % bz, y, x);
+            };
+            std::stable_sort(tl.begin() + begin[b], tl.end(),
+                             [&](const int4& u, const int4& v) { return key(u) < key(v); });
+        }
+    }
+    begin[h->nbox] = (int)tl.size();
+}
+
 dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
     *out = find_tiles(h, T);
     if (*out != nullptr) return DWF_OK;
@@ -114,13 +144,7 @@ dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
     ts.T = T;
     for (int p = 0; p < 2; ++p) {
         std::vector<int4> tl;
-        ts.box_tile_begin[p].assign(h->nbox + 1, 0);
-        for (int b = 0; b < h->nbox; ++b) {
-            ts.box_tile_begin[p][b] = (int)tl.size();
-            const int64_t off = h->box_off[p][b], cnt = h->box_cnt[p][b];
-            for (int64_t i = 0; i < cnt; i += T)
-                tl.push_back(make_int4(b, (int)(off + i), (int)std::min<int64_t>(T, cnt - i), 0));
-        }
+        tile_list(h, T, p, tl, ts.box_tile_begin[p]);
 #ifdef DWF_DEBUG
         for (const int4& t : tl)
             if (t.x < 0 || t.x >= h->nbox || t.y < 0 || t.z < 1 || (int64_t)t.y + t.z > h->nsite[p]) {
@@ -130,7 +154,6 @@ dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
                 return DWF_ERR_ARG;
             }
 #endif
-        ts.box_tile_begin[p][h->nbox] = (int)tl.size();
         ts.ntiles[p] = (int)tl.size();
         cudaError_t e = cudaSuccess;
         if (!tl.empty()) {
@@ -149,6 +172,35 @@ dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out) {
         }
     }
     *out = &h->tiles.emplace(T, ts).first->second;
+    return DWF_OK;
+}
+
+// Reorder every existing tile table in place (same tiles, same device
+// buffers, so captured graphs and per-tile buffers stay valid) and build later
+// ones in the new order.  Waits for the device first.
+dwf_status set_tile_order(dwf_handle* h, int order, int bz, int bt) {
+    if ((order != 0 && order != 1) || bz < 1 || bt < 1) {
+        set_error("dwf_set_tile_order: order must be 0 or 1, block extents >= 1");
+        return DWF_ERR_ARG;
+    }
+    DWF_CUDA(cudaDeviceSynchronize());
+    h->tile_order = order;
+    h->order_bz = bz;
+    h->order_bt = bt;
+    for (auto& kv : h->tiles) {
+        TileSet& ts = kv.second;
+        for (int p = 0; p < 2; ++p) {
+            std::vector<int4> tl;
+            std::vector<int> begin;
+            tile_list(h, ts.T, p, tl, begin);
+            if ((int)tl.size() != ts.ntiles[p] || begin != ts.box_tile_begin[p]) {
+                set_error("dwf_set_tile_order: tile table changed shape");
+                return DWF_ERR_ARG;
+            }
+            if (!tl.empty())
+                DWF_CUDA(cudaMemcpy(ts.d_tiles[p], tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        }
+    }
     return DWF_OK;
 }
 
@@ -458,6 +510,7 @@ dwf_status create(dwf_handle** out, const dwf_params* p, const dwf_box* boxes, i
         if (st == DWF_OK) st = h2d(h->d_link_src[q], lsrc.data(), ns * 8 * sizeof(int64_t));
         if (st == DWF_OK) st = h2d(h->d_site_box[q], site_box[q].data(), ns * sizeof(int));
         if (st == DWF_OK) st = h2d(h->d_site_local[q], site_local[q].data(), ns * sizeof(int));
+        if (st == DWF_OK) h->site_local_host[q] = site_local[q];
         for (int pr = 0; pr < 3 && st == DWF_OK; ++pr)
             st = dalloc((char**)&h->d_links[pr][q], ns * 144 * prec_size((dwf_prec)pr));
     }

@@ -139,6 +139,11 @@ struct dwf_handle {
     // whole-lattice handle of D_dirichlet: the links between different
     // domains (each box, and the rest of the lattice) are left out
     std::vector<dwf_box> cut;
+    // host copy of every site's box-local lexicographic index (tile ordering)
+    std::vector<int> site_local_host[2];
+    // order of the tiles within each box: 0 lexicographic, 1 blocked in
+    // (z, t) by order_bz x order_bt planes (dwf_set_tile_order)
+    int tile_order = 0, order_bz = 8, order_bt = 8;
     int nrhs_max = 1;
     int device = 0;
     int64_t nsite[2] = {0, 0};
@@ -184,6 +189,7 @@ namespace dwf {
 inline int tile_or_default(int T) { return T > 0 ? T : 16; }
 // The tile table of T sites per tile, built (and allocated) on first use.
 dwf_status get_tiles(dwf_handle* h, int T, const TileSet** out);
+dwf_status set_tile_order(dwf_handle* h, int order, int bz, int bt);
 // The tile table if it exists already (never allocates), else nullptr.
 const TileSet* find_tiles(const dwf_handle* h, int T);
 // A handle is used on the device it was created on: DWF_ERR_ARG otherwise.

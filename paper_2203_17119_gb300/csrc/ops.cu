@@ -129,6 +129,51 @@ dwf_status autotune(dwf_handle* h, int nrhs, dwf_prec prec, int* best) {
         const float med = ts[ts.size() / 2];
         if (med < best_ms) { best_ms = med; best_T = T; best_vl = vl; best_chunk = ck; best_fuse = fu; }
     }
+    // the handle-wide tile order for the chosen configuration: lexicographic or
+    // blocked in (z, t) by 8 x 8 planes, whichever runs the chain faster
+    if (st == DWF_OK && h->nbox == 1 && !h->dirichlet) {
+        const int order0 = h->tile_order, bz0 = h->order_bz, bt0 = h->order_bt;
+        float ord_ms[2] = {0.f, 0.f};
+        h->tuned_T[nrhs] = best_T;
+        h->tuned_chunk[nrhs] = best_chunk;
+        h->tuned_fuse[nrhs] = best_fuse;
+        if (best_vl > 0) h->tuned_vl[nrhs] = best_vl;
+        if (prec == DWF_BF16) h->tuned_tc[nrhs] = best_vl < 0 ? 1 : 0;
+        for (int od = 0; od < 2 && st == DWF_OK; ++od) {
+            st = set_tile_order(h, od, 8, 8);
+            std::vector<float> ts;
+            for (int rep = 0; rep < 9 && st == DWF_OK; ++rep) {
+                cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
+                cudaEventRecord(e0, s);
+                if (chain) {
+                    st = op_mpc(h, t2 + bytes, t2, 0, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
+                    if (st == DWF_OK)
+                        st = op_mpc(h, t2, t2 + bytes, 1, prec, prec, nrhs, t1, t1 + bytes, nullptr, nullptr, s);
+                } else {
+                    HopCall c{};
+                    c.in = h->d_tmp2;
+                    c.out = h->d_tmp;
+                    c.prec_link = c.prec_in = c.prec_out = prec;
+                    c.nrhs = nrhs;
+                    c.scale = 1.0;
+                    c.T = best_T;
+                    c.chunk = best_chunk;
+                    st = launch_hop(h, c, s);
+                }
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep >= 2) ts.push_back(ms);
+            }
+            if (st == DWF_OK) {
+                std::sort(ts.begin(), ts.end());
+                ord_ms[od] = ts[ts.size() / 2];
+            }
+        }
+        if (st == DWF_OK) st = set_tile_order(h, ord_ms[1] < ord_ms[0] ? 1 : 0, 8, 8);
+        else set_tile_order(h, order0, bz0, bt0);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);

@@ -75,6 +75,8 @@ def signatures():
         "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
         "dwf_create_cut": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
         "dwf_debug_build": [C.POINTER(C.c_int)],
+        "dwf_set_tile_order": [vp, i, i, i],
+        "dwf_get_tile_order": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "dwf_check_range": [vp, C.c_size_t],
         "dwf_one_flavour_action": [vp, vp, vp, i, C.POINTER(Rational), C.POINTER(Rational), C.POINTER(SolverParams),
                                    C.POINTER(C.c_double), C.POINTER(SolverStats), vp],
@@ -581,6 +583,17 @@ class Handle:
         f = C.c_int()
         _check(lib().dwf_get_fusion(self._h, nrhs, C.byref(f)))
         return bool(f.value)
+
+    def set_tile_order(self, order=1, bz=8, bt=8):
+        """Tile order of every kernel on this handle: 0 lexicographic, 1
+        blocked in (z, t) by bz x bt planes."""
+        _check(lib().dwf_set_tile_order(self._h, int(order), int(bz), int(bt)))
+
+    def tile_order(self):
+        """(order, bz, bt) of this handle's tiles."""
+        o, z, t = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().dwf_get_tile_order(self._h, C.byref(o), C.byref(z), C.byref(t)))
+        return o.value, z.value, t.value
 
     def set_hop_chunk(self, nrhs=1, chunk=1):
         """Consecutive tiles per CTA of the hop before striding by the grid."""

@@ -158,17 +158,20 @@ def test_pack_unpack_layout(case, prec):
     assert LY.rel_l2(got, canon) <= TOL[prec]
 
 
-@pytest.mark.parametrize("tile,vl,chunk", [(4, 1, 1), (8, 2, 1), (48, 1, 1), (64, 2, 1),
-                                            (4, 2, 8), (8, 1, 3)])
-def test_tile_and_lane_variants(tile, vl, chunk):
+@pytest.mark.parametrize("tile,vl,chunk,order", [(4, 1, 1, None), (8, 2, 1, (2, 2)), (48, 1, 1, None),
+                                                  (64, 2, 1, (1, 3)), (4, 2, 8, (2, 2)), (8, 1, 3, None)])
+def test_tile_and_lane_variants(tile, vl, chunk, order):
     """Every (tile size, lanes per thread, tile order, epilogue fusion) choice
     the autotuner can make gives the same operator: hop-based dslash_eo and
     M_pc (both adjoints) in FP32 and FP64, with the site-local factor of M_pc
     in the hop epilogue (8 lanes x 2 rhs: the site groups divide a warp) and
-    without."""
+    without; tiles in lexicographic order or blocked in (z, t) inside each
+    (odd-sized, wrapping) box."""
     dims, Ls, prm, boxes, nrhs, U, masks, psi, h = _setup("mobius_boxes_odd_wrap")
     h.set_tile(nrhs, tile, vl)
     h.set_hop_chunk(nrhs, chunk)
+    if order:
+        h.set_tile_order(1, *order)
     po = [[O.parity_part(f, 1) for f in row] for row in psi]
     src = LY.to_cb(po, dims, boxes, 1)
     for dagger in (False, True):
@@ -205,6 +208,13 @@ def test_autotuned_solve_still_exact():
     st, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32)
     xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
     assert O.true_residual(U, xf, b, MOBIUS) <= 1e-10
+    # tiles reordered in place under the solver's captured graphs: same solve
+    h.set_tile_order(1, 2, 2)
+    x.zero_()
+    st2, rc = h.cgne_solve(x, bf, tol=1e-10, inner=G.FP32)
+    xf = LY.from_full(torch.view_as_complex(x.cpu()).numpy(), dims, None, Ls)[0][0]
+    assert O.true_residual(U, xf, b, MOBIUS) <= 1e-10
+    assert abs(st2[0]["iters"] - st[0]["iters"]) <= 2
 
 
 @pytest.mark.parametrize("dagger", [False, True])
@@ -247,12 +257,23 @@ def test_autotune_cache_round_trip(tmp_path):
     h = G.Handle(dims, Ls, act, nrhs_max=2)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     h.autotune(1, G.FP32)
+    h.set_tile_order(1, 2, 4)
     path = str(tmp_path / "tune.txt")
     h.autotune_save(path)
     h2 = G.Handle(dims, Ls, act, nrhs_max=2)
     h2.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
     assert h2.autotune_load(path, 1, G.FP32)
     assert h2.tuning(1) == h.tuning(1)
+    assert h2.tile_order() == (1, 2, 4)
+    # a line without the tile-order fields loads as lexicographic
+    old = str(tmp_path / "tune5.txt")
+    with open(path) as f, open(old, "w") as g:
+        for line in f:
+            g.write(" ".join(line.split()[:6]) + "\n")
+    h4 = G.Handle(dims, Ls, act, nrhs_max=2)
+    h4.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    assert h4.autotune_load(old, 1, G.FP32)
+    assert h4.tuning(1) == h.tuning(1) and h4.tile_order()[0] == 0
     assert not h2.autotune_load(path, 2, G.FP32)
     assert not h2.autotune_load(path, 1, G.BF16)
     h3 = G.Handle((4, 4, 4, 4), Ls, act)
