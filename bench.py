@@ -368,6 +368,8 @@ def run_ours(args, rank, world):
                      "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes}
     small = None if args.no_small else _small_workload(G, inputs, dev, stream, flush)
     del flush
+    # the batched workload (6 uneven Dirichlet boxes x 16 right-hand sides at 24^4 x 16), once
+    batched = None if args.no_batched else batched_result(16, "f32", args.steps)
 
     peaks = {}
     try:
@@ -377,18 +379,24 @@ def run_ours(args, rank, world):
     peak = peaks.get("hbm_gbs", 6800.0)
     for v in hop.values():
         v["frac_hbm"] = round(v["gbs"] / peak, 3)
+    # DRAM bytes per launch from the committed ncu capture of the same kernel
+    # configuration (tile, lanes, chunk, tile order), while hop.cu is unchanged
     traffic = None
+    order = list(hD.tile_order())
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "hop_f32_traffic.json")))
         src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2203_17119_gb300", "csrc", "hop.cu"),
                                        "rb").read()).hexdigest()[:16]
         if prof.get("hop_cu_sha256_16") == src_hash and prof.get("lattice") == list(DIMS) \
                 and prof.get("Ls") == LS:
-            traffic = prof["dram_bytes_per_launch_scaled"]
-    except (OSError, ValueError, KeyError):
+            for cap in prof["captures"]:
+                if cap["config_tile_lanes_chunk"] == list(hop["f32"]["config"]) and cap["tile_order"][0] == order[0] \
+                        and (order[0] == 0 or cap["tile_order"] == order):
+                    traffic = cap["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError, TypeError):
         pass
     roof = {"bound": "hbm", "kernel": "k_hop<float> (bare Wilson hop, FP32, 32^4 x Ls=16)",
-            "config_tile_lanes_chunk": hop["f32"]["config"], "tile_order": list(hD.tile_order()),
+            "config_tile_lanes_chunk": hop["f32"]["config"], "tile_order": order,
             "achieved": hop["f32"]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": round(hop["f32"]["gbs"] / peak, 3), "traffic": traffic,
             "algorithmic_bytes_per_launch": hop["f32"]["bytes"],
@@ -415,6 +423,7 @@ def run_ours(args, rank, world):
         "dslash": hop,
         "roofline": roof,
         "small_16x12": small,
+        "batched_24x16": batched,
         "e2e": {"value": round(world * e2e_flops / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
                 "steps": n_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -1084,19 +1093,18 @@ BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
 
 
-def run_batched(args):
+def batched_result(nrhs, prec_name="f32", steps=5, seed=1002):
     """Six standalone Dirichlet boxes of uneven extents (8^4 ... 16^4) inside a
     24^4 x Ls=16 Moebius lattice, nrhs right-hand sides each: the hop and a
     mixed-precision CGNE of all 6 * nrhs systems in one persistent launch per
-    kernel (--batched NRHS [f32|bf16])."""
+    kernel, autotuned; returns the result dict."""
     import numpy as np
     import torch
     from paper_2203_17119_gb300 import dwf as G
     from paper_2203_17119_gb300 import inputs
-    nrhs = int(args.batched[0])
-    prec = G.PREC[args.batched[1]] if len(args.batched) > 1 else G.FP32
+    prec = G.PREC[prec_name]
     dims, Ls = (24, 24, 24, 24), 16
-    rng = np.random.default_rng(1002)
+    rng = np.random.default_rng(seed)
     U = inputs.gauge_field(dims, "exp", eps=EPS, rng=rng)
     h = G.Handle(dims, Ls, G.Action(M5, SMALL_MF, B5, C5), boxes=BATCH_BOXES, nrhs_max=nrhs)
     h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
@@ -1115,7 +1123,7 @@ def run_batched(args):
     for _ in range(3):
         h.hop(out, inp, 0, prec=prec, nrhs=nrhs)
     ts = []
-    for _ in range(max(args.steps, 5)):
+    for _ in range(max(steps, 5)):
         flush.fill_(1.0)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -1133,14 +1141,22 @@ def run_batched(args):
     st, rc = h.cgne_solve(x, b, nrhs=nrhs, tol=1e-10, inner=prec, allow_fail=True)
     torch.cuda.synchronize()
     secs = time.time() - t0
-    print(json.dumps({
-        "workload": "6 Dirichlet boxes 8^4..16^4 in 24^4 x Ls=16, Moebius", "nrhs": nrhs,
-        "prec": args.batched[1] if len(args.batched) > 1 else "f32", "tile_sites": T,
-        "systems": len(st), "hop_ms": ms, "hop_tflops": FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12,
-        "hop_gbs": nbytes / (ms * 1e-3) / 1e9, "solve_seconds": secs,
-        "solve_status": rc, "max_iters": max(s["iters"] for s in st),
-        "max_true_resid": max(s["true_resid"] for s in st),
-        "seconds_per_system": secs / len(st)}))
+    res = {"workload": "6 Dirichlet boxes 8^4..16^4 in 24^4 x Ls=16, Moebius m_f=0.01", "nrhs": nrhs,
+           "prec": prec_name, "tile_sites": T, "systems": len(st), "hop_ms": round(ms, 4),
+           "hop_tflops": round(FLOPS_PER_SITE * sites / (ms * 1e-3) / 1e12, 3),
+           "hop_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "solve_seconds": round(secs, 3),
+           "solve_status": rc, "max_iters": max(s["iters"] for s in st),
+           "max_true_resid": max(s["true_resid"] for s in st),
+           "seconds_per_system": round(secs / len(st), 4)}
+    del h, b, x
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(args):
+    """--batched NRHS [f32|bf16]: batched_result as one JSON line."""
+    print(json.dumps(batched_result(int(args.batched[0]), args.batched[1] if len(args.batched) > 1 else "f32",
+                                    args.steps)))
 
 
 def main():
@@ -1179,6 +1195,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-cg", action="store_true", help="skip the plain FP64 CG solves")
     ap.add_argument("--no-small", action="store_true", help="skip the 16^4 x 12 extra keys")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 24^4 x 16 extra key")
     ap.add_argument("--config", nargs=3, type=int, metavar=("TILE", "VL", "CHUNK"),
                     help="default workload: fixed kernel configuration instead of autotuning")
     args = ap.parse_args()
