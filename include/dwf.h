@@ -532,8 +532,8 @@ dwf_status dwf_rational_power(double alpha, int n, double lo, double hi, double*
  *   out = a0 in + sum_i residues[i] (M_pc^+ M_pc + shifts[i])^-1 in,
  * the form the DD-RHMC action of Sec. 2.3.1 takes for the powers of the
  * normal operators of D (whole-lattice handle) and of D_Omega (box handle),
- * e.g. the (D_dir^+ D_dir)^(1/4) and (D^+ D)^(-1/2) factors with the
- * caller's (Remez) coefficients.  One dwf_multishift_solve (same sp, stats
+ * e.g. the (D_dir^+ D_dir)^(1/4) and (D^+ D)^(-1/2) factors with
+ * coefficients from dwf_rational_power.  One dwf_multishift_solve (same sp, stats
  * [n][nbox * nrhs]) and n + 1 axpby passes.  in, out: distinct odd cb FP64
  * fields; shifts, residues: host arrays of n values (shifts >= 0).  Returns
  * the multi-shift status (out is formed from the last iterates on
