@@ -12,7 +12,7 @@
 // once), deterministic FP64 reductions per system, the scalar recurrences on
 // the host (a few doubles per (shift, system)), and per shift two
 // per-system axpby launches (x_s += a p_s, p_s = zeta r + b p_s) on FP64
-// vectors.  Converged (shift, system) pairs get zero updates.
+// vectors; shifts whose systems have all converged are no longer updated.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -191,9 +191,17 @@ static dwf_status multishift_core(dwf_handle* h, double* x, const double* b, con
         }
         for (int i = 0; i < nsys; ++i) hs(3, 0, i) = -alpha[i];
         DWF_CUDA(cudaMemcpyAsync(dS, h_sc.data(), h_sc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        // shifts whose every system has converged are left alone (their updates
+        // would be x += 0 p, p = 0 r + 1 p: whole fields streamed for nothing)
+        auto shift_active = [&](int k) {
+            for (int i = 0; i < nsys; ++i)
+                if (act[(size_t)k * nsys + i]) return true;
+            return false;
+        };
         for (int k = 0; k < nshift; ++k)
-            DWF_TRY(launch_axpby(h, 1, nrhs, ds(0, k), 0.0, pk(k), DWF_FP64, nullptr, 1.0, xs(k),
-                                 DWF_FP64, nullptr, T, s));
+            if (shift_active(k))
+                DWF_TRY(launch_axpby(h, 1, nrhs, ds(0, k), 0.0, pk(k), DWF_FP64, nullptr, 1.0, xs(k),
+                                     DWF_FP64, nullptr, T, s));
         // r -= alpha A p
         DWF_TRY(launch_axpby(h, 1, nrhs, ds(3, 0), 0.0, dAp, DWF_FP64, nullptr, 1.0, dR, DWF_FP64,
                              nullptr, T, s));
@@ -212,8 +220,9 @@ static dwf_status multishift_core(dwf_handle* h, double* x, const double* b, con
             }
         DWF_CUDA(cudaMemcpyAsync(dS, h_sc.data(), h_sc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         for (int k = 0; k < nshift; ++k)
-            DWF_TRY(launch_axpby(h, 1, nrhs, ds(1, k), 0.0, dR, DWF_FP64, ds(2, k), 0.0, pk(k),
-                                 DWF_FP64, nullptr, T, s));
+            if (shift_active(k))
+                DWF_TRY(launch_axpby(h, 1, nrhs, ds(1, k), 0.0, dR, DWF_FP64, ds(2, k), 0.0, pk(k),
+                                     DWF_FP64, nullptr, T, s));
         // convergence of every (shift, system): |r^(s)| = |zeta_new| |r|; a system
         // whose base shift converged stops all its shifts (they are better
         // conditioned and have converged already in exact arithmetic)
