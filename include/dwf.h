@@ -367,6 +367,16 @@ dwf_status dwf_debug_build(int* on);
  * build returns DWF_ERR_UNSUPPORTED. */
 dwf_status dwf_check_range(const void* p, size_t bytes);
 
+/* Copy `bytes` from src to dst, each device memory or page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister, e.g. a pinned PyTorch tensor), with the
+ * GPU's own 16-byte loads and stores (a grid-stride kernel) instead of a copy
+ * engine: the host <-> device transfers of a solve's source and solution where
+ * the CPU-GPU link gives the SMs coherent access to host memory (NVLink-C2C).
+ * Asynchronous on `stream`.  DWF_ERR_ARG, before anything is launched, for
+ * NULL or pageable (unregistered) pointers, pointers not 16-byte aligned or a
+ * size that is not a multiple of 16. */
+dwf_status dwf_copy(void* dst, const void* src, size_t bytes, void* stream);
+
 /* Number of kernels the library has launched in this process so far (a
  * captured CUDA graph counts its kernels on every replay). */
 dwf_status dwf_launch_count(uint64_t* n);

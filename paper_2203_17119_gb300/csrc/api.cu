@@ -608,6 +608,11 @@ dwf_status dwf_force(dwf_handle* h, double* out, const void* X, const void* Y, d
     return force_bilinear(h, out, X, Y, prec, nrhs, active, accumulate, (cudaStream_t)stream);
 }
 
+dwf_status dwf_copy(void* dst, const void* src, size_t bytes, void* stream) {
+    DWF_RANGE("dwf_copy");
+    return copy_sm(dst, src, bytes, (cudaStream_t)stream);
+}
+
 dwf_status dwf_check_device(dwf_handle* h) {
     DWF_TRY(check_handle(h));
     int e = 0;

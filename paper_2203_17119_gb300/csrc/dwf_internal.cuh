@@ -332,6 +332,8 @@ struct LocalCall {
 dwf_status launch_local(dwf_handle* h, const LocalCall& c, cudaStream_t s);
 
 // elementwise / reduction kernels (blas.cu)
+// copy between device and page-locked host memory with SM loads and stores
+dwf_status copy_sm(void* dst, const void* src, size_t bytes, cudaStream_t s);
 dwf_status launch_convert(void* dst, dwf_prec pd, const void* src, dwf_prec ps,
                           size_t n_complex, cudaStream_t s);
 // partial sums per tile and rhs: q0 = Re<a,b> (a == b: |a|^2)

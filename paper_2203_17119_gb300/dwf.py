@@ -75,6 +75,7 @@ def signatures():
         "dwf_create": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
         "dwf_create_cut": [C.POINTER(vp), C.POINTER(Params), C.POINTER(Box), i, i],
         "dwf_debug_build": [C.POINTER(C.c_int)],
+        "dwf_copy": [vp, vp, C.c_size_t, vp],
         "dwf_set_tile_order": [vp, i, i, i],
         "dwf_get_tile_order": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "dwf_check_range": [vp, C.c_size_t],
@@ -223,6 +224,16 @@ def zolotarev_inv_sqrt(n, lo, hi):
     dl = C.c_double()
     _check(lib().dwf_zolotarev_inv_sqrt(int(n), float(lo), float(hi), sh, rs, C.byref(dl)))
     return list(sh), list(rs), dl.value
+
+
+def copy(dst: torch.Tensor, src: torch.Tensor, stream=None):
+    """dst <- src (same byte size; device or pinned host tensors) with the GPU's
+    own loads and stores (dwf_copy)."""
+    nb = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nb or not dst.is_contiguous() or not src.is_contiguous():
+        raise DWFError(1, "copy: contiguous tensors of the same byte size")
+    _check(lib().dwf_copy(C.c_void_p(dst.data_ptr()), C.c_void_p(src.data_ptr()), nb, _stream(stream)))
+    return dst
 
 
 def rational_power(alpha, n, lo, hi):
