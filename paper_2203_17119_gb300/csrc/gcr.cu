@@ -69,36 +69,57 @@ __global__ void k_caxpy(const int4* __restrict__ tiles, int nrhs, int Ls, const 
     }
 }
 
-// Partial sums per (i, tile, rhs) of <Q_i, v>, i = blockIdx.y: the inner
-// products of classical Gram-Schmidt against all previous directions at once.
+// Partial sums per (i, tile, rhs) of <Q_i, v>: the inner products of
+// classical Gram-Schmidt against all previous directions at once.  A CTA
+// takes one tile and up to kDotGroup directions i = kDotGroup * blockIdx.y + g,
+// so v is read once per group instead of once per direction; each thread
+// walks rows (one (site, colour-spin, rhs) row holds Ls contiguous complex
+// lanes) in 16-byte steps of two lanes.
+constexpr int kDotGroup = 8;
 __global__ void __launch_bounds__(512) k_multi_cdot_partial(const int4* __restrict__ tiles, int ntiles, int nrhs,
-                                                            int Ls, const float* __restrict__ Q, size_t fstride,
-                                                            const float* __restrict__ v, double* pre,
-                                                            double* pim) {
+                                                            int Ls, int nq, const float* __restrict__ Q,
+                                                            size_t fstride, const float* __restrict__ v,
+                                                            double* pre, double* pim) {
     __shared__ double s_red[512];
-    const int i = blockIdx.y;
-    const float* a = Q + (size_t)i * fstride;
+    const int i0 = blockIdx.y * kDotGroup;
+    const int ng = min(kDotGroup, nq - i0);
     const int4 tl = tiles[blockIdx.x];
     const int rows = tl.z * 12 * nrhs;
     const int64_t off = (int64_t)tl.y * 12 * nrhs * Ls;
-    double accr = 0.0, acci = 0.0;
+    double accr[kDotGroup], acci[kDotGroup];
+#pragma unroll
+    for (int g = 0; g < kDotGroup; ++g) accr[g] = acci[g] = 0.0;
     for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-        const float* pa = a + 2 * (off + (int64_t)row * Ls);
-        const float* pb = v + 2 * (off + (int64_t)row * Ls);
-        float sr = 0.f, si = 0.f;
-        for (int s = 0; s < Ls; ++s) {
-            const float ar = pa[2 * s], ai = pa[2 * s + 1], br = pb[2 * s], bi = pb[2 * s + 1];
-            sr += ar * br + ai * bi;
-            si += ar * bi - ai * br;
+        const int64_t base = 2 * (off + (int64_t)row * Ls);
+        float sr[kDotGroup], si[kDotGroup];
+#pragma unroll
+        for (int g = 0; g < kDotGroup; ++g) sr[g] = si[g] = 0.f;
+        for (int s2 = 0; s2 < Ls; s2 += 2) {
+            const float4 b = *reinterpret_cast<const float4*>(v + base + 2 * s2);
+#pragma unroll
+            for (int g = 0; g < kDotGroup; ++g) {
+                if (g < ng) {
+                    const float4 a =
+                        *reinterpret_cast<const float4*>(Q + (size_t)(i0 + g) * fstride + base + 2 * s2);
+                    // conj(a) b for the two lanes
+                    sr[g] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+                    si[g] += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
+                }
+            }
         }
-        accr += sr;
-        acci += si;
+#pragma unroll
+        for (int g = 0; g < kDotGroup; ++g) {
+            accr[g] += sr[g];
+            acci[g] += si[g];
+        }
     }
     const int nr = nrhs;
     auto rhs = [&](int t) { return t < rows ? t % nr : -1; };
-    const size_t o = ((size_t)i * ntiles + blockIdx.x) * nrhs;
-    block_rhs_reduce(accr, s_red, nrhs, rhs, pre + o);
-    block_rhs_reduce(acci, s_red, nrhs, rhs, pim + o);
+    for (int g = 0; g < ng; ++g) {
+        const size_t o = ((size_t)(i0 + g) * ntiles + blockIdx.x) * nrhs;
+        block_rhs_reduce(accr[g], s_red, nrhs, rhs, pre + o);
+        block_rhs_reduce(acci[g], s_red, nrhs, rhs, pim + o);
+    }
 }
 
 // c[i][sys] = sgn * sum over the box's tiles of the partials (0 for systems
@@ -380,8 +401,8 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
         double* an_im = w.scal + 7 * (size_t)nsys;
         // one classical Gram-Schmidt pass of (q_j, z_j) against the j previous pairs
         auto project = [&](int j, float* qj, float* zj) -> dwf_status {
-            k_multi_cdot_partial<<<dim3(ntl, j), cdot_threads, 0, s>>>(ts.d_tiles[1], ntl, nrhs, h->p.Ls, w.q, fs, qj,
-                                                                      ppre, ppim);
+            k_multi_cdot_partial<<<dim3(ntl, (j + kDotGroup - 1) / kDotGroup), cdot_threads, 0, s>>>(
+                ts.d_tiles[1], ntl, nrhs, h->p.Ls, j, w.q, fs, qj, ppre, ppim);
             note_launch();
             k_multi_reduce<<<dim3(nsys, j), 256, 0, s>>>(ppre, ppim, box_tb, ntl, nrhs, w.act, 1.0, mre, mim);
             note_launch();
@@ -412,8 +433,8 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
             DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, 0.0, nullptr, DWF_FP32, s_c2, 0.0, qj, DWF_FP32, nullptr, T, s));
             DWF_TRY(launch_axpby(h, 1, nrhs, nullptr, 0.0, nullptr, DWF_FP32, s_c2, 0.0, zj, DWF_FP32, nullptr, T, s));
             // a = <q_j, r>: x += a z_j, r -= a q_j
-            k_multi_cdot_partial<<<dim3(ntl, 1), cdot_threads, 0, s>>>(ts.d_tiles[1], ntl, nrhs, h->p.Ls, qj, fs, w.r,
-                                                                      ppre, ppim);
+            k_multi_cdot_partial<<<dim3(ntl, 1), cdot_threads, 0, s>>>(ts.d_tiles[1], ntl, nrhs, h->p.Ls, 1, qj, fs,
+                                                                      w.r, ppre, ppim);
             note_launch();
             k_multi_reduce<<<dim3(nsys, 1), 256, 0, s>>>(ppre, ppim, box_tb, ntl, nrhs, w.act, 1.0, a_re, a_im);
             note_launch();

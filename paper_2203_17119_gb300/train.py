@@ -161,11 +161,13 @@ def multigrid(h, nvec, block, order, seed=5):
     return mg, hi
 
 
-def evaluate(K, dims, Ls, act, seed=1004, nvec=12, block=(8, 8, 8, 8), order=30):
+def evaluate(K, dims, Ls, act, seed=1004, nvec=12, block=(8, 8, 8, 8), order=30, restart=64):
     """Time to 1e-10 on one Gaussian source: GCR with K, GCR without K, GCR
     with the two-level multigrid (Chebyshev smoother, and K as smoother; the
-    multigrid set-up timed separately), mixed CG and FP64 CG.  `fallback`
-    marks a GCR that handed over to CG."""
+    multigrid set-up timed separately), mixed CG and FP64 CG.  `restart`: the
+    GCR restart length (short restarts stall on these normal equations: at
+    24^4 x 16, GCR(16) + K needs over 2900 iterations where GCR(64) + K needs
+    320).  `fallback` marks a GCR that handed over to CG."""
     rng = np.random.default_rng(seed + 10)
     U = inputs.gauge_field(dims, "exp", eps=0.3, rng=rng)
     h = G.Handle(dims, Ls, act, nrhs_max=nvec)
@@ -187,10 +189,12 @@ def evaluate(K, dims, Ls, act, seed=1004, nvec=12, block=(8, 8, 8, 8), order=30)
             mg.set_smoother("chebyshev", 3, hi / 10, hi)
         return mg
 
-    for name, fn in (("gcr_K", lambda x: h.gcr_solve(x, b, K=K, tol=1e-10)),
-                     ("gcr", lambda x: h.gcr_solve(x, b, K=None, tol=1e-10)),
-                     ("gcr_mg_chebyshev", lambda x: h.gcr_solve_mg(x, b, with_smoother("chebyshev"), tol=1e-10)),
-                     ("gcr_mg_K", lambda x: h.gcr_solve_mg(x, b, with_smoother("nn"), tol=1e-10)),
+    out["restart"] = restart
+    for name, fn in (("gcr_K", lambda x: h.gcr_solve(x, b, K=K, tol=1e-10, restart=restart)),
+                     ("gcr", lambda x: h.gcr_solve(x, b, K=None, tol=1e-10, restart=restart)),
+                     ("gcr_mg_chebyshev", lambda x: h.gcr_solve_mg(x, b, with_smoother("chebyshev"), tol=1e-10,
+                                                                  restart=restart)),
+                     ("gcr_mg_K", lambda x: h.gcr_solve_mg(x, b, with_smoother("nn"), tol=1e-10, restart=restart)),
                      ("cg_mixed_fp32", lambda x: h.cgne_solve(x, b, tol=1e-10, inner=G.FP32)),
                      ("cg_fp64", lambda x: h.cgne_solve(x, b, tol=1e-10, inner=G.FP64))):
         x = torch.zeros_like(b)
