@@ -9,7 +9,7 @@
 //   P           the near-null vectors restricted to each block and
 //               orthonormalised there in vector order (classical Gram-Schmidt
 //               with reorthogonalisation, P^+ P = 1)
-//   A_c         P^+ A P (Galerkin), dense, inverted once on the host
+//   A_c         P^+ A P (Galerkin), dense, inverted once (Gauss-Jordan on the device)
 //   M^-1 r      V(1,1) cycle: z = S r; z += P A_c^-1 P^+ (r - A z);
 //               z += S (r - A z), smoother S none, a Chebyshev iteration on
 //               [lo, hi] or the learned network K
@@ -332,37 +332,133 @@ dwf_status mg_apply(dwf_mg* mg, float* z, const float* r, cudaStream_t s) {
 }
 
 // In-place inverse of a dense complex matrix (Gauss-Jordan, partial pivoting).
-static bool invert(std::vector<std::complex<double>>& a, int n) {
-    std::vector<std::complex<double>> inv((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
-    for (int c = 0; c < n; ++c) {
-        int p = c;
-        double best = std::abs(a[(size_t)c * n + c]);
-        for (int r = c + 1; r < n; ++r)
-            if (std::abs(a[(size_t)r * n + c]) > best) { best = std::abs(a[(size_t)r * n + c]); p = r; }
-        if (!(best > 0.0)) return false;
-        if (p != c)
-            for (int j = 0; j < n; ++j) {
-                std::swap(a[(size_t)p * n + j], a[(size_t)c * n + j]);
-                std::swap(inv[(size_t)p * n + j], inv[(size_t)c * n + j]);
-            }
-        const std::complex<double> piv = 1.0 / a[(size_t)c * n + c];
-        for (int j = 0; j < n; ++j) {
-            a[(size_t)c * n + j] *= piv;
-            inv[(size_t)c * n + j] *= piv;
-        }
-        for (int r = 0; r < n; ++r) {
-            if (r == c) continue;
-            const std::complex<double> f = a[(size_t)r * n + c];
-            if (f == 0.0) continue;
-            for (int j = 0; j < n; ++j) {
-                a[(size_t)r * n + j] -= f * a[(size_t)c * n + j];
-                inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
-            }
-        }
+// Gauss-Jordan inversion with partial pivoting of the dense coarse operator on
+// the device, FP64: the augmented rows [A | 1] (n x 2n, row-major), per
+// column c the pivot (largest |a_rc|, r >= c, the smallest such r), the row
+// swap and scaling, the column's factors, then every other row minus its
+// factor times the pivot row.  n <= 4096.
+__global__ void k_gj_identity(double2* M, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        M[(size_t)i * 2 * n + n + i] = make_double2(1.0, 0.0);
+}
+
+// the pivot row index and the pivot value (read here, before any row changes)
+__global__ void k_gj_pivot(const double2* __restrict__ M, int n, int c, int* piv, double2* pval) {
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    double best = -1.0;
+    int bi = n;
+    for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+        const double2 v = M[(size_t)r * 2 * n + c];
+        const double m = v.x * v.x + v.y * v.y;
+        if (m > best) { best = m; bi = r; }
     }
-    a.swap(inv);
-    return true;
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const double o = sv[threadIdx.x + w];
+            const int oi = si[threadIdx.x + w];
+            if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = o;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool ok = sv[0] > 0.0 && si[0] < n;
+        piv[0] = ok ? si[0] : -1;
+        pval[0] = ok ? M[(size_t)si[0] * 2 * n + c] : make_double2(1.0, 0.0);
+    }
+}
+
+// swap rows c and piv, scale row c by 1 / a_cc, and keep the column-c factors
+// of every row (read before the elimination writes them)
+__global__ void k_gj_swap_scale(double2* M, int n, int c, const int* __restrict__ piv,
+                                const double2* __restrict__ pval, int* err) {
+    const int p = piv[0];
+    if (p < 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *err = 1;
+        return;
+    }
+    const size_t ld = 2 * (size_t)n;
+    const double2 d = pval[0];
+    const double den = d.x * d.x + d.y * d.y;
+    const double2 inv = make_double2(d.x / den, -d.y / den);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += gridDim.x * blockDim.x) {
+        const double2 vp = M[(size_t)p * ld + j], vc = M[(size_t)c * ld + j];
+        M[(size_t)c * ld + j] = make_double2(vp.x * inv.x - vp.y * inv.y, vp.x * inv.y + vp.y * inv.x);
+        if (p != c) M[(size_t)p * ld + j] = vc;
+    }
+}
+
+__global__ void k_gj_factors(const double2* __restrict__ M, int n, int c, const int* __restrict__ piv,
+                             double2* fac) {
+    if (piv[0] < 0) return;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        fac[r] = r == c ? make_double2(0.0, 0.0) : M[(size_t)r * 2 * n + c];
+}
+
+__global__ void k_gj_eliminate(double2* M, int n, int c, const int* __restrict__ piv,
+                               const double2* __restrict__ fac) {
+    if (piv[0] < 0) return;
+    const size_t ld = 2 * (size_t)n;
+    const int r = blockIdx.y;
+    const double2 f = fac[r];
+    if (f.x == 0.0 && f.y == 0.0) return;
+    for (int j = c + blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += gridDim.x * blockDim.x) {
+        const double2 pc = M[(size_t)c * ld + j];
+        double2 v = M[(size_t)r * ld + j];
+        v.x -= f.x * pc.x - f.y * pc.y;
+        v.y -= f.x * pc.y + f.y * pc.x;
+        M[(size_t)r * ld + j] = v;
+    }
+}
+
+// d_out = A^-1 for the n x n complex matrix at A (device); false if singular.
+static dwf_status invert_device(const double2* A, int n, double2* d_out, int* singular, cudaStream_t s) {
+    double2* M = nullptr;
+    double2* fac = nullptr;   // n factors, then the pivot value
+    int* iw = nullptr;        // [0] pivot, [1] singular flag
+    dwf_status st = DWF_OK;
+    auto fail = [&](cudaError_t e) {
+        if (e != cudaSuccess) {
+            set_error("dwf_mg_setup: coarse inversion: %s", cudaGetErrorString(e));
+            st = DWF_ERR_CUDA;
+        }
+        return e != cudaSuccess;
+    };
+    if (!fail(dev_malloc(&M, (size_t)n * 2 * n * sizeof(double2))) && !fail(dev_malloc(&fac, (size_t)(n + 1) * sizeof(double2))) &&
+        !fail(dev_malloc(&iw, 2 * sizeof(int))) && !fail(cudaMemsetAsync(iw, 0, 2 * sizeof(int), s)) &&
+        !fail(cudaMemsetAsync(M, 0, (size_t)n * 2 * n * sizeof(double2), s)) &&
+        !fail(cudaMemcpy2DAsync(M, 2 * n * sizeof(double2), A, n * sizeof(double2), n * sizeof(double2), n,
+                                cudaMemcpyDeviceToDevice, s))) {
+        k_gj_identity<<<(n + 255) / 256, 256, 0, s>>>(M, n);   // the right half: element (i, n + i)
+        note_launch();
+        for (int c = 0; c < n && st == DWF_OK; ++c) {
+            k_gj_pivot<<<1, 256, 0, s>>>(M, n, c, iw, fac + n);
+            k_gj_swap_scale<<<(2 * n + 255) / 256, 256, 0, s>>>(M, n, c, iw, fac + n, iw + 1);
+            k_gj_factors<<<(n + 255) / 256, 256, 0, s>>>(M, n, c, iw, fac);
+            k_gj_eliminate<<<dim3((2 * n - c + 255) / 256, n), 256, 0, s>>>(M, n, c, iw, fac);
+            note_launch();
+            note_launch();
+            note_launch();
+            note_launch();
+            fail(cudaGetLastError());
+        }
+        if (st == DWF_OK)
+            fail(cudaMemcpy2DAsync(d_out, n * sizeof(double2), M + n, 2 * n * sizeof(double2), n * sizeof(double2), n,
+                                   cudaMemcpyDeviceToDevice, s));
+        if (st == DWF_OK) fail(cudaMemcpyAsync(singular, iw + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (st == DWF_OK) fail(cudaStreamSynchronize(s));
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(M);
+    cudaFree(fac);
+    cudaFree(iw);
+    return st;
 }
 
 void free_mg(dwf_mg* mg) {
@@ -556,14 +652,12 @@ dwf_status dwf_mg_setup(dwf_mg* mg, const float* V, void* stream) {
         return DWF_ERR_ARG;
     }
     DWF_CUDA(cudaMemcpy(mg->d_ac, hac.data(), hac.size() * sizeof(double2), cudaMemcpyHostToDevice));
-    std::vector<std::complex<double>> a((size_t)nc * nc);
-    for (size_t i = 0; i < a.size(); ++i) a[i] = {hac[i].x, hac[i].y};
-    if (!invert(a, nc)) {
+    int singular = 0;
+    DWF_TRY(invert_device(mg->d_ac, nc, mg->d_cinv, &singular, s));
+    if (singular) {
         set_error("dwf_mg_setup: the coarse operator is singular");
         return DWF_ERR_ARG;
     }
-    for (size_t i = 0; i < a.size(); ++i) hac[i] = make_double2(a[i].real(), a[i].imag());
-    DWF_CUDA(cudaMemcpy(mg->d_cinv, hac.data(), hac.size() * sizeof(double2), cudaMemcpyHostToDevice));
     mg->ready = true;
     return DWF_OK;
 }
