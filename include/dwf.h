@@ -629,7 +629,8 @@ dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dw
  * each block and orthonormalised there by Gram-Schmidt in vector order
  * (classical, twice; P^+ P = 1); the coarse operator A_c = P^+ A P (Galerkin) is dense,
  * built by nblocks applications of A with nvec lanes and inverted once on the
- * host (at most 4096 coarse unknowns = blocks x nvec).  The preconditioner
+ * device by pivoted Gauss-Jordan in FP64 (at most 4096 coarse unknowns =
+ * blocks x nvec).  The preconditioner
  * is the V(1,1) cycle z = S r; z += P A_c^-1 P^+ (r - A z); z += S (r - A z)
  * with a smoother S: none, the Chebyshev iteration for A z = r on [lo, hi]
  * (steps - 1 applications of A), or the learned network K.  FP32 fields and
