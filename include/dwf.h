@@ -613,7 +613,10 @@ dwf_status dwf_chebyshev_filter(dwf_handle* h, void* out, const void* in, int or
  * stops decreasing for two restarts (a poor K), the solve falls back to
  * mixed-precision CGNE from the current x; stats.recorded = -1 marks that. 
  * Inner vectors and operator FP32, solution and restarted residual FP64,
- * FP64 inner products.  reliable_updates in stats counts restarts. */
+ * FP64 inner products.  Each new direction is orthogonalised by classical
+ * Gram-Schmidt, repeated once where the first pass shrank its norm by more
+ * than 1/sqrt(2) in any active system.  reliable_updates in stats counts
+ * restarts. */
 dwf_status dwf_gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn* K,
                          const dwf_solver_params* sp, dwf_solver_stats* stats, void* stream);
 

@@ -420,10 +420,18 @@ dwf_status gcr_solve(dwf_handle* h, double* x, const double* b, int nrhs, dwf_nn
             DWF_TRY(op_mpc(h, w.t32, zj, 0, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));
             DWF_TRY(op_mpc(h, qj, w.t32, 1, DWF_FP32, DWF_FP32, nrhs, w.tA, w.tB, nullptr, nullptr, s));
             if (j > 0) {
-                // twice (classical Gram-Schmidt with reorthogonalisation): as
-                // stable as the modified form, with all inner products at once
+                // classical Gram-Schmidt with all inner products at once, and a
+                // second pass where the first lost orthogonality: the criterion of
+                // Daniel, Gragg, Kaufman and Stewart (1976), repeat when the pass
+                // shrank |q_j| by more than 1/sqrt(2) (any active system decides)
+                std::vector<double> n0(nsys), n1(nsys);
+                DWF_TRY(norm2(1, qj, DWF_FP32, n0));
                 DWF_TRY(project(j, qj, zj));
-                DWF_TRY(project(j, qj, zj));
+                DWF_TRY(norm2(1, qj, DWF_FP32, n1));
+                bool again = false;
+                for (int m = 0; m < nsys; ++m)
+                    if (active[m] && !(n1[m] >= 0.5 * n0[m])) again = true;
+                if (again) DWF_TRY(project(j, qj, zj));
             }
             // q_j, z_j /= |q_j|
             DWF_TRY(launch_dot_partial(h, 1, qj, qj, DWF_FP32, DWF_FP32, nrhs, pre, T, s));
