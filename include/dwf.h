@@ -696,7 +696,12 @@ dwf_status dwf_nn_get_weights(const dwf_nn* K, double* w, size_t n_complex);
 dwf_status dwf_nn_save(const dwf_nn* K, const char* path);
 dwf_status dwf_nn_load(dwf_nn* K, const char* path);
 /* out = K in, odd cb FP32 fields with nrhs lanes (host workspace grows on
- * first use per handle and nrhs). */
+ * first use per handle and nrhs).  The two layers are linear, so this call
+ * applies their product W2 W1 (formed in FP64 from the BF16 weights, stored
+ * FP32) to the transported input, only on the directions that are nonzero on
+ * each checkerboard (the link transports on even sites, the identity and the
+ * s-shifts on odd sites); the training step runs the two layers through the
+ * channels.  Both give the same K up to FP32 rounding. */
 dwf_status dwf_nn_apply(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs,
                         void* stream);
 /* One Adam step on nrhs (r, e) pairs (odd cb FP32, one pair per lane,

@@ -309,6 +309,7 @@ struct dwf_nn {
     float* d_mix1 = nullptr; // BF16-rounded mixing matrices, kernel layouts
     float* d_mix2 = nullptr;
     float* d_mix2h = nullptr;    // adjoint of layer-2 mixing
+    float* d_fold[2] = {nullptr, nullptr};   // W2 W1 on even / odd sites (inference)
     int adam_t = 0;
     bool dirty = true;           // mixing matrices need a refresh
 };
@@ -317,6 +318,13 @@ namespace dwf {
 
 static size_t w1_len(int C) { return (size_t)kNDir * C * 16 * 2; }
 static size_t w2_len(int C) { return (size_t)kNDir * C * 16 * 2; }
+
+// Directions whose R_d = T_d x0 can be nonzero on each parity when x0 vanishes
+// on even sites: the link transports reach even sites from odd neighbours, the
+// identity and the two s-shifts stay on odd sites.
+constexpr int kNFold[2] = {8, 3};
+constexpr int kFoldDirs[2][8] = {{1, 2, 3, 4, 5, 6, 7, 8}, {0, 9, 10, 0, 0, 0, 0, 0}};
+static size_t fold_len(int p) { return (size_t)kNFold[p] * 4 * kNFold[p] * 4 * 2; }
 
 static float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -352,6 +360,33 @@ static dwf_status refresh_mix(dwf_nn* K) {
     DWF_CUDA(cudaMemcpy(K->d_mix1, m1.data(), m1.size() * 4, cudaMemcpyHostToDevice));
     DWF_CUDA(cudaMemcpy(K->d_mix2, m2.data(), m2.size() * 4, cudaMemcpyHostToDevice));
     DWF_CUDA(cudaMemcpy(K->d_mix2h, m2h.data(), m2h.size() * 4, cudaMemcpyHostToDevice));
+    // folded layers for inference: M[d][d'] = sum_b W2[d][b] W1[d'][b] (4x4 complex
+    // spin blocks, FP64 products of the BF16-rounded weights, stored FP32) in the
+    // mixing layout [o = d][so][i = d'][si], restricted to each parity's directions
+    for (int p = 0; p < 2; ++p) {
+        const int n = kNFold[p];
+        std::vector<float> fm(fold_len(p));
+        for (int o = 0; o < n; ++o)
+            for (int i = 0; i < n; ++i)
+                for (int so = 0; so < 4; ++so)
+                    for (int si = 0; si < 4; ++si) {
+                        const int d = kFoldDirs[p][o], dp = kFoldDirs[p][i];
+                        double mr = 0.0, mi = 0.0;
+                        for (int b = 0; b < C; ++b)
+                            for (int t = 0; t < 4; ++t) {
+                                const size_t i2 = (((size_t)d * C + b) * 4 + so) * 4 + t;
+                                const size_t i1 = (((size_t)dp * C + b) * 4 + t) * 4 + si;
+                                const double ar = bf16_round(w2[2 * i2]), ai = bf16_round(w2[2 * i2 + 1]);
+                                const double br = bf16_round(w1[2 * i1]), bi = bf16_round(w1[2 * i1 + 1]);
+                                mr += ar * br - ai * bi;
+                                mi += ar * bi + ai * br;
+                            }
+                        const size_t dst = (((size_t)o * 4 + so) * n + i) * 4 + si;
+                        fm[2 * dst] = (float)mr;
+                        fm[2 * dst + 1] = (float)mi;
+                    }
+        DWF_CUDA(cudaMemcpy(K->d_fold[p], fm.data(), fm.size() * 4, cudaMemcpyHostToDevice));
+    }
     K->dirty = false;
     return DWF_OK;
 }
@@ -431,12 +466,12 @@ static TransArgs trans_args(dwf_handle* h, int nrhs, int p) {
 
 static dwf_status launch_transport(dwf_handle* h, int nrhs, const float* in, float* out,
                                    const int* dirs, int ndir, bool sum, const float* const* ins,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int only_parity = -1) {
     const TileSet* tsp = nullptr;
     DWF_TRY(get_tiles(h, tile_for(h, nrhs), &tsp));
     const TileSet& ts = *tsp;
     for (int p = 0; p < 2; ++p) {
-        if (ts.ntiles[p] == 0) continue;
+        if (ts.ntiles[p] == 0 || (only_parity >= 0 && p != only_parity)) continue;
         TransArgs a = trans_args(h, nrhs, p);
         a.in = in;
         a.out = out;
@@ -452,9 +487,13 @@ static dwf_status launch_transport(dwf_handle* h, int nrhs, const float* in, flo
     return DWF_OK;
 }
 
+// Mixing on a full field, or (parity 0 / 1) on that parity's block only: `in`
+// and `out` then point at the block, fields keep the full-field stride.
 static dwf_status launch_mix(dwf_handle* h, int nrhs, const float* in, int nin, float* out, int nout,
-                             const float* W, cudaStream_t s) {
-    const int64_t npix = (h->nsite[0] + h->nsite[1]) * 3 * (int64_t)h->p.Ls * nrhs;
+                             const float* W, cudaStream_t s, int only_parity = -1) {
+    const int64_t nsites = only_parity < 0 ? h->nsite[0] + h->nsite[1] : h->nsite[only_parity];
+    const int64_t npix = nsites * 3 * (int64_t)h->p.Ls * nrhs;
+    if (npix == 0) return DWF_OK;
     const int64_t fstride = full_floats(h, nrhs);
     const size_t smem = (size_t)nout * 4 * nin * 4 * 2 * sizeof(float);
     int64_t blocks = (npix + 127) / 128;
@@ -464,6 +503,10 @@ static dwf_status launch_mix(dwf_handle* h, int nrhs, const float* in, int nin, 
         k_mix<16><<<(int)blocks, 128, smem, s>>>(in, nin, out, W, npix, N5, fstride);
     else if (nout == 11)
         k_mix<11><<<(int)blocks, 128, smem, s>>>(in, nin, out, W, npix, N5, fstride);
+    else if (nout == 8)
+        k_mix<8><<<(int)blocks, 128, smem, s>>>(in, nin, out, W, npix, N5, fstride);
+    else if (nout == 3)
+        k_mix<3><<<(int)blocks, 128, smem, s>>>(in, nin, out, W, npix, N5, fstride);
     else {
         set_error("nn: unsupported channel count %d", nout);
         return DWF_ERR_UNSUPPORTED;
@@ -518,15 +561,41 @@ static dwf_status nn_forward(dwf_nn* K, dwf_handle* h, NNWS& w, int nrhs, cudaSt
     return launch_transport(h, nrhs, nullptr, w.z, kDirsFwd, kNDir, true, d_ins, s);
 }
 
+// Inference z = K x on the odd checkerboard.  The same function as
+// nn_forward up to rounding, with the work that is exactly zero left out: x0
+// vanishes on even sites, so R_d = T_d x0 is zero on odd sites for the link
+// directions 1..8 and on even sites for 0, 9 and 10; only odd z is read, which
+// takes psi_d on even sites for d = 1..8 and on odd sites for 0, 9, 10; and
+// with no nonlinearity between the layers psi = (W2 W1) R.  Per parity the
+// folded 4x4-block matrix over that parity's directions (8 x 8 blocks even,
+// 3 x 3 odd) replaces the two mixes through the C channels.
 dwf_status nn_apply_internal(dwf_nn* K, dwf_handle* h, float* out, const float* in, int nrhs,
                              cudaStream_t s) {
     NNWS* w;
     DWF_TRY(nn_ws(h, nrhs, K->C, false, &w));
+    DWF_TRY(refresh_mix(K));
     const int64_t c0 = h->nsite[0] * 12 * (int64_t)h->p.Ls * nrhs * 2;
     const int64_t c1 = h->nsite[1] * 12 * (int64_t)h->p.Ls * nrhs * 2;
-    DWF_CUDA(cudaMemsetAsync(w->x0, 0, c0 * 4, s));
+    const int64_t f = full_floats(h, nrhs);
+    // the even block of x0 is never read below
     DWF_CUDA(cudaMemcpyAsync(w->x0 + c0, in, c1 * 4, cudaMemcpyDeviceToDevice, s));
-    DWF_TRY(nn_forward(K, h, *w, nrhs, s));
+    for (int p = 0; p < 2; ++p)
+        DWF_TRY(launch_transport(h, nrhs, w->x0, w->R, kFoldDirs[p], kNFold[p], false, nullptr, s, p));
+    DWF_TRY(launch_mix(h, nrhs, w->R, kNFold[0], w->psi, kNFold[0], K->d_fold[0], s, 0));
+    DWF_TRY(launch_mix(h, nrhs, w->R + c0, kNFold[1], w->psi + c0, kNFold[1], K->d_fold[1], s, 1));
+    // z on odd sites: psi field j holds direction kFoldDirs[p][j] on parity p
+    int dirs[kNDir];
+    const float* ins[kNDir];
+    int nd = 0;
+    for (int p = 1; p >= 0; --p)
+        for (int j = 0; j < kNFold[p]; ++j) {
+            dirs[nd] = kFoldDirs[p][j];
+            ins[nd++] = w->psi + j * f;
+        }
+    static thread_local const float** d_ins = nullptr;
+    if (d_ins == nullptr) DWF_CUDA(dev_malloc(&d_ins, kNDir * sizeof(float*)));
+    DWF_CUDA(cudaMemcpyAsync(d_ins, ins, sizeof(ins), cudaMemcpyHostToDevice, s));
+    DWF_TRY(launch_transport(h, nrhs, nullptr, w->z, dirs, kNDir, true, d_ins, s, 1));
     DWF_CUDA(cudaMemcpyAsync(out, w->z + c0, c1 * 4, cudaMemcpyDeviceToDevice, s));
     return DWF_OK;
 }
@@ -554,7 +623,9 @@ dwf_status dwf_nn_create(dwf_nn** out, int channels) {
         dev_malloc(&K->d_m, (n1 + n2) * 4) != cudaSuccess ||
         dev_malloc(&K->d_v, (n1 + n2) * 4) != cudaSuccess ||
         dev_malloc(&K->d_mix1, n1 * 4) != cudaSuccess || dev_malloc(&K->d_mix2, n2 * 4) != cudaSuccess ||
-        dev_malloc(&K->d_mix2h, n2 * 4) != cudaSuccess) {
+        dev_malloc(&K->d_mix2h, n2 * 4) != cudaSuccess ||
+        dev_malloc(&K->d_fold[0], fold_len(0) * 4) != cudaSuccess ||
+        dev_malloc(&K->d_fold[1], fold_len(1) * 4) != cudaSuccess) {
         set_error("dwf_nn_create: cudaMalloc failed");
         return DWF_ERR_CUDA;
     }
@@ -571,6 +642,7 @@ dwf_status dwf_nn_destroy(dwf_nn* K) {
     if (!K) return DWF_OK;
     cudaFree(K->d_w1); cudaFree(K->d_w2); cudaFree(K->d_m); cudaFree(K->d_v);
     cudaFree(K->d_mix1); cudaFree(K->d_mix2); cudaFree(K->d_mix2h);
+    cudaFree(K->d_fold[0]); cudaFree(K->d_fold[1]);
     delete K;
     return DWF_OK;
 }
