@@ -1133,6 +1133,52 @@ def run_learned(args):
                       "train_loss_first_last": [loss0, loss1], "eval": ev}))
 
 
+def run_nn(args):
+    """One application of the learned preconditioner K (dwf_nn_apply, the form
+    GCR and the multigrid smoother use): --nn L Ls [nrhs], random BF16-exact
+    weights, CUDA events around each application on the launching stream.  The
+    network's intermediate fields (11 transported and 11 mixed fields of the
+    whole lattice) are larger than L2 at the sizes it is timed on, so no flush.
+    mix_tflops counts the folded mixes' multiply-adds: per (site, colour, lane)
+    32 x 32 complex on even sites and 12 x 12 on odd sites."""
+    import numpy as np
+    import torch
+    from paper_2203_17119_gb300 import dwf as G
+    from paper_2203_17119_gb300 import inputs
+    L, Ls = int(args.nn[0]), int(args.nn[1])
+    nrhs = int(args.nn[2]) if len(args.nn) > 2 else 1
+    dims = (L, L, L, L)
+    U = inputs.gauge_field(dims, "exp", eps=EPS, seed=SMALL_SEED)
+    h = G.Handle(dims, Ls, G.Action(M5, MF, B5, C5), nrhs_max=nrhs)
+    h.set_gauge(torch.from_numpy(U.reshape(-1)).cuda())
+    del U
+    rng = np.random.default_rng(1005)
+
+    def bf16(a):
+        return torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).double().numpy()
+
+    W1 = bf16(rng.standard_normal((11, 16, 1, 4, 4)) * 0.1) + 1j * bf16(rng.standard_normal((11, 16, 1, 4, 4)) * 0.1)
+    W2 = bf16(rng.standard_normal((11, 1, 16, 4, 4)) * 0.1) + 1j * bf16(rng.standard_normal((11, 1, 16, 4, 4)) * 0.1)
+    K = G.NN()
+    K.set_weights(W1, W2)
+    x = torch.randn(h.cb_shape(1, nrhs), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        K.apply(h, out, x, nrhs, stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(1, args.steps)):
+        _, ms = _event_ms(lambda: K.apply(h, out, x, nrhs, stream), stream)
+        times.append(ms)
+    ms = float(np.median(times))
+    half = L ** 4 // 2
+    flops = 8.0 * (32 * 32 + 12 * 12) * half * 3 * Ls * nrhs
+    print(json.dumps({"workload": f"learned preconditioner K applied on {L}^4 x Ls={Ls}, nrhs={nrhs}",
+                      "ms": ms, "ms_all": times, "mix_gflop": flops / 1e9,
+                      "mix_tflops": flops / (ms * 1e-3) / 1e12, "l2_flush": "none (fields > L2)"}))
+
+
 BATCH_BOXES = [((0, 0, 0, 0), (8, 8, 8, 8)), ((0, 0, 0, 0), (8, 8, 12, 12)),
                ((0, 0, 0, 0), (12, 12, 12, 12)), ((0, 0, 0, 0), (12, 12, 16, 16)),
                ((0, 0, 0, 0), (16, 16, 16, 12)), ((0, 0, 0, 0), (16, 16, 16, 16))]
@@ -1224,6 +1270,8 @@ def main():
                     help="[f64|f32] [N]: the one-flavour DD-RHMC heat bath, action and force")
     ap.add_argument("--force", nargs="*", metavar="ARG",
                     help="link force of Re <X, D Y>: [f64|f32] [L] [Ls]")
+    ap.add_argument("--nn", nargs="+", metavar="ARG",
+                    help="L Ls [nrhs]: time one application of the learned preconditioner K")
     ap.add_argument("--hop", nargs="+", metavar="ARG",
                     help="bare hop only: L Ls prec(f64|f32|bf16) [nrhs]")
     ap.add_argument("--no-autotune", action="store_true")
@@ -1271,6 +1319,9 @@ def main():
         return
     if args.learned is not None:
         run_learned(args)
+        return
+    if args.nn:
+        run_nn(args)
         return
     if args.hop:
         run_hop(args)

@@ -156,6 +156,7 @@ __global__ void k_multi_reduce(const double* __restrict__ pre, const double* __r
 }
 
 // y -= sum_{i<j} c_i Q_i and z -= sum_{i<j} c_i Z_i (complex c per system).
+constexpr int kAxpyGroup = 8;
 __global__ void k_multi_caxpy(const int4* __restrict__ tiles, int nrhs, int Ls, int nsys, int j,
                               const double* __restrict__ cre, const double* __restrict__ cim,
                               const float* __restrict__ Q, const float* __restrict__ Z, size_t fstride,
@@ -167,7 +168,29 @@ __global__ void k_multi_caxpy(const int4* __restrict__ tiles, int nrhs, int Ls, 
         const int sys = tl.x * nrhs + (e / Ls) % nrhs;
         float2 yv = reinterpret_cast<float2*>(y)[off + e];
         float2 zv = reinterpret_cast<float2*>(z)[off + e];
-        for (int i = 0; i < j; ++i) {
+        // directions in groups of 8 with all their loads issued before the
+        // updates (more loads in flight per thread); the updates keep the
+        // order i = 0, 1, ..., so the result does not depend on the grouping
+        int i = 0;
+        for (; i + kAxpyGroup <= j; i += kAxpyGroup) {
+            float2 q[kAxpyGroup], w[kAxpyGroup];
+            float cr[kAxpyGroup], ci[kAxpyGroup];
+#pragma unroll
+            for (int u = 0; u < kAxpyGroup; ++u) {
+                cr[u] = (float)cre[(size_t)(i + u) * nsys + sys];
+                ci[u] = (float)cim[(size_t)(i + u) * nsys + sys];
+                q[u] = reinterpret_cast<const float2*>(Q + (size_t)(i + u) * fstride)[off + e];
+                w[u] = reinterpret_cast<const float2*>(Z + (size_t)(i + u) * fstride)[off + e];
+            }
+#pragma unroll
+            for (int u = 0; u < kAxpyGroup; ++u) {
+                yv.x -= cr[u] * q[u].x - ci[u] * q[u].y;
+                yv.y -= cr[u] * q[u].y + ci[u] * q[u].x;
+                zv.x -= cr[u] * w[u].x - ci[u] * w[u].y;
+                zv.y -= cr[u] * w[u].y + ci[u] * w[u].x;
+            }
+        }
+        for (; i < j; ++i) {
             const float cr = (float)cre[(size_t)i * nsys + sys], ci = (float)cim[(size_t)i * nsys + sys];
             const float2 q = reinterpret_cast<const float2*>(Q + (size_t)i * fstride)[off + e];
             const float2 w = reinterpret_cast<const float2*>(Z + (size_t)i * fstride)[off + e];
