@@ -1,7 +1,8 @@
 """Pins of the oracle's parallel-transport preconditioner and GCR: identity
 weights give K = 1, gauge equivariance, adjoint transports, central finite
 differences for the analytic gradient, the closed form of Adam's first step,
-and GCR against a dense LU solve."""
+GCR against a dense LU solve, and the folded checkerboard form of K that
+inference uses."""
 
 import numpy as np
 import pytest
@@ -27,6 +28,32 @@ def test_identity_weights_give_identity():
     r = inputs.gaussian_source(dims, Ls, rng=rng)
     W1, W2 = N.identity_weights(16)
     assert np.allclose(N.apply_K(U, r, W1, W2), O.parity_part(r, 1), atol=1e-15)
+
+
+def test_folded_checkerboard_form_equals_two_layers():
+    """The inference form the GPU applies: for an input on odd sites,
+    R_d = T_d r vanishes on odd sites for the link directions 1..8 and on even
+    sites for 0, 9, 10 (exactly), and with the layers linear K r on odd sites
+    is sum_d T_d (sum_d' M[d][d'] R_d') with M = W2 W1 over each
+    checkerboard's own directions."""
+    dims, Ls, C = (4, 2, 4, 2), 4, 5
+    rng = np.random.default_rng(8)
+    U = inputs.gauge_field(dims, "haar", rng=rng)
+    r = O.parity_part(inputs.gaussian_source(dims, Ls, rng=rng), 1)
+    W1, W2 = rand_w(rng, C)
+    links, local = list(range(1, 9)), [0, 9, 10]
+    for d in range(N.NDIR):
+        T = N.transport(U, r, d)
+        assert np.max(np.abs(O.parity_part(T, 1 if d in links else 0))) == 0.0, d
+    M = np.einsum("dbot,ebti->deoi", W2[:, 0], W1[:, :, 0])
+    z = np.zeros_like(r)
+    for p, ds in ((0, links), (1, local)):
+        R = {e: O.parity_part(N.transport(U, r, e), p) for e in ds}
+        for d in ds:
+            psi = sum(np.einsum("ij,tzyxsja->tzyxsia", M[d, e], R[e]) for e in ds)
+            z += N.transport(U, psi, d)
+    want = N.apply_K(U, r, W1, W2)
+    assert np.linalg.norm(O.parity_part(z, 1) - want) <= 1e-13 * np.linalg.norm(want)
 
 
 def test_transport_adjoints():
