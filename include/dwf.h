@@ -357,7 +357,7 @@ dwf_status dwf_get_tuning(const dwf_handle* h, int nrhs, int* tile_sites, int* l
 /* The debug build (libdwf_debug.so, compiled with -DDWF_DEBUG): every entry
  * point checks, on the host and before launching anything, that each caller
  * buffer it reads or writes lies inside one device allocation of the current
- * context (the allocation range the driver reports for the pointer, so with a
+ * context (the allocation range the CUDA driver reports for the pointer, so with a
  * caching allocator only overruns past its segment are seen), and the handle's
  * neighbour and link tables are range-checked when built; a failure returns
  * DWF_ERR_ARG naming the buffer.  *on = 1 in the debug build, 0 otherwise. */

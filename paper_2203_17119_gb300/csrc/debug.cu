@@ -1,7 +1,7 @@
 // The debug build (-DDWF_DEBUG, libdwf_debug.so): host-side bounds checks in
 // the entry points.  Every caller buffer an entry point reads or writes is
 // checked, before anything is launched, to lie inside one device allocation
-// of the current context ([p, p + bytes) within the range the driver reports
+// of the current context ([p, p + bytes) within the range the CUDA driver reports
 // for p); the handle's neighbour and link tables are checked when they are
 // built.  Failures return DWF_ERR_ARG with the buffer's name.  With a caching
 // allocator (PyTorch's) the allocation is the allocator's segment, so only
